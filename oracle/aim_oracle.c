@@ -1,0 +1,212 @@
+/*
+ * ORACLE -- test infrastructure only.  Plain, slow, obviously correct CPU
+ * implementation of what the alignment hot path computes.  Only the tests,
+ * the smoke check and the benchmark's CPU-baseline leg may call it; the CUDA
+ * product path never does.  It shares no code with the CUDA library.
+ *
+ * What it computes (per pair of read P[0..n) and target T[0..m)):
+ *
+ *   Exact global alignment under gap-affine costs (Section 2.4.2, SWG with
+ *   three tables M, I, D, "resembles NW but uses an affine gap model"); NW
+ *   edit distance (Section 2.4.1) is the same DP with mismatch 1, open 0,
+ *   extend 1.  The recurrences are the textbook Gotoh ones (the paper names
+ *   the method but does not print them), written out over the full matrix:
+ *
+ *     M(v,h) = min(M,I,D)(v-1,h-1) + (P[v-1]==T[h-1] ? 0 : x)
+ *     I(v,h) = min(M(v-1,h)+o+e, D(v-1,h)+o+e, I(v-1,h)+e)      (consumes a read base)
+ *     D(v,h) = min(M(v,h-1)+o+e, I(v,h-1)+o+e, D(v,h-1)+e)      (consumes a target base)
+ *     M(0,0) = 0, I(v,0) = o+e*v, D(0,h) = o+e*h, every other border entry infinite.
+ *     Cells with |h-v| > band are infinite when a band is given.
+ *     score = min(M,I,D)(n,m)
+ *
+ *   Threshold (Section 1, "edit distance threshold"): the pair is rejected
+ *   iff score > limit (or |n-m| > band); a rejected pair reports score -1,
+ *   flag 1 and no CIGAR.
+ *
+ *   Canonical CIGAR (the paper fixes no tie-break): among all optimal
+ *   alignments, the one whose op string read backward from the end is
+ *   lexicographically smallest under X < I < D < M.  Computed by a backward
+ *   greedy over the set of states whose DP value equals the cost the suffix
+ *   requires of them ("tight" states), taking at each cell the op of the
+ *   highest-priority tight state.
+ *
+ * Pinned by: brute-force enumeration of every op string on tiny pairs,
+ * closed forms, hand-worked examples and invariants (tests/test_oracle_*.py).
+ *
+ * Build: gcc -O2 -fPIC -shared aim_oracle.c -o liboracle.so -lpthread
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <pthread.h>
+
+#define INF ((int32_t)1 << 29)
+
+static int32_t min2(int32_t a, int32_t b) { return a < b ? a : b; }
+static int32_t min3(int32_t a, int32_t b, int32_t c) { return min2(min2(a, b), c); }
+static int32_t cap_inf(int32_t a) { return a >= INF ? INF : a; }
+
+/* BAM op codes used in the CIGAR runs: '=' 7, 'X' 8, 'I' 1, 'D' 2; a run is len << 4 | code. */
+static uint32_t bam_code(char op) {
+    switch (op) { case 'M': return 7; case 'X': return 8; case 'I': return 1; default: return 2; }
+}
+
+/*
+ * Align one pair.  Returns 0 on success, -3 if memory could not be allocated.
+ * cigar may be NULL (score only).  *ncig receives the number of runs even when
+ * it exceeds cap; runs beyond cap are not written and flag 2 is set.
+ */
+int oracle_align(const char *P, uint32_t n, const char *T, uint32_t m, int32_t x, int32_t o, int32_t e,
+                 int32_t band, int64_t limit, int32_t *score, uint8_t *flags, uint32_t *cigar, uint32_t cap,
+                 uint32_t *ncig) {
+    *score = -1; *flags = 0; *ncig = 0;
+    int64_t dnm = (int64_t)m - (int64_t)n;
+    if (band >= 0 && (dnm > band || -dnm > band)) { *flags = 1; return 0; }
+    size_t W = (size_t)m + 1, cells = ((size_t)n + 1) * W;
+    int32_t *Mt = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *It = (int32_t *)malloc(cells * sizeof(int32_t));
+    int32_t *Dt = (int32_t *)malloc(cells * sizeof(int32_t));
+    char *ops = (char *)malloc((size_t)n + m + 1);
+    if (!Mt || !It || !Dt || !ops) { free(Mt); free(It); free(Dt); free(ops); return -3; }
+#define AT(t, v, h) (t)[(size_t)(v) * W + (size_t)(h)]
+    for (uint32_t v = 0; v <= n; ++v) {
+        for (uint32_t h = 0; h <= m; ++h) {
+            int32_t Mv = INF, Iv = INF, Dv = INF;
+            int64_t k = (int64_t)h - (int64_t)v;
+            int inband = band < 0 || (k <= band && -k <= band);
+            if (inband) {
+                if (v == 0 && h == 0) {
+                    Mv = 0;
+                } else {
+                    if (v >= 1 && h >= 1) {
+                        int32_t d = (P[v - 1] == T[h - 1]) ? 0 : x;
+                        Mv = cap_inf(min3(AT(Mt, v - 1, h - 1), AT(It, v - 1, h - 1), AT(Dt, v - 1, h - 1)) + d);
+                    }
+                    if (v >= 1)
+                        Iv = cap_inf(min3(AT(Mt, v - 1, h) + o + e, AT(Dt, v - 1, h) + o + e, AT(It, v - 1, h) + e));
+                    if (h >= 1)
+                        Dv = cap_inf(min3(AT(Mt, v, h - 1) + o + e, AT(It, v, h - 1) + o + e, AT(Dt, v, h - 1) + e));
+                }
+            }
+            AT(Mt, v, h) = Mv; AT(It, v, h) = Iv; AT(Dt, v, h) = Dv;
+        }
+    }
+    int32_t s = min3(AT(Mt, n, m), AT(It, n, m), AT(Dt, n, m));
+    if (s >= INF || (int64_t)s > limit) {
+        *flags = 1;
+        free(Mt); free(It); free(Dt); free(ops);
+        return 0;
+    }
+    *score = s;
+    /* state-set backward greedy; req* < 0 means the state is not required */
+    int64_t reqM = s, reqI = s, reqD = s;
+    uint32_t v = n, h = m, nops = 0;
+    while (v > 0 || h > 0) {
+        int tM = reqM >= 0 && AT(Mt, v, h) == reqM;
+        int tI = reqI >= 0 && AT(It, v, h) == reqI;
+        int tD = reqD >= 0 && AT(Dt, v, h) == reqD;
+        int match = (v > 0 && h > 0) && P[v - 1] == T[h - 1];
+        char op;
+        if (tM && v > 0 && h > 0 && !match) op = 'X';
+        else if (tI) op = 'I';
+        else if (tD) op = 'D';
+        else if (tM && match) op = 'M';
+        else { free(Mt); free(It); free(Dt); free(ops); return -5; /* cannot happen: no tight state */ }
+        ops[nops++] = op;
+        if (op == 'X' || op == 'M') {
+            int64_t c = reqM - (op == 'X' ? x : 0);
+            reqM = reqI = reqD = c; --v; --h;
+        } else if (op == 'I') {
+            int64_t c = reqI;
+            reqM = c - o - e; reqD = c - o - e; reqI = c - e; --v;
+        } else {
+            int64_t c = reqD;
+            reqM = c - o - e; reqI = c - o - e; reqD = c - e; --h;
+        }
+    }
+    /* ops were produced end-first; run-length encode them start-first */
+    uint32_t runs = 0;
+    for (int64_t i = (int64_t)nops - 1; i >= 0;) {
+        char op = ops[i]; uint32_t len = 0;
+        while (i >= 0 && ops[i] == op) { ++len; --i; }
+        if (cigar && runs < cap) cigar[runs] = (len << 4) | bam_code(op);
+        ++runs;
+    }
+    *ncig = runs;
+    if (cigar && runs > cap) *flags |= 2;
+#undef AT
+    free(Mt); free(It); free(Dt); free(ops);
+    return 0;
+}
+
+/* Textbook one-state Levenshtein distance (two rows), an independent cross-check for the unit-cost case. */
+int32_t oracle_levenshtein(const char *P, uint32_t n, const char *T, uint32_t m) {
+    int32_t *prev = (int32_t *)malloc(((size_t)m + 1) * sizeof(int32_t));
+    int32_t *cur = (int32_t *)malloc(((size_t)m + 1) * sizeof(int32_t));
+    if (!prev || !cur) { free(prev); free(cur); return -3; }
+    for (uint32_t h = 0; h <= m; ++h) prev[h] = (int32_t)h;
+    for (uint32_t v = 1; v <= n; ++v) {
+        cur[0] = (int32_t)v;
+        for (uint32_t h = 1; h <= m; ++h) {
+            int32_t sub = prev[h - 1] + (P[v - 1] != T[h - 1]);
+            int32_t del = prev[h] + 1, ins = cur[h - 1] + 1;
+            cur[h] = sub < del ? (sub < ins ? sub : ins) : (del < ins ? del : ins);
+        }
+        int32_t *t = prev; prev = cur; cur = t;
+    }
+    int32_t r = prev[m];
+    free(prev); free(cur);
+    return r;
+}
+
+/* ---- batch driver: one pair per task over plain pthreads ---- */
+
+typedef struct {
+    const char *reads, *targets;
+    const uint64_t *read_off, *target_off;
+    const uint32_t *read_len, *target_len;
+    uint64_t num_pairs;
+    int32_t x, o, e, band;
+    const int64_t *limit;          /* per pair */
+    int32_t *scores; uint8_t *flags;
+    uint32_t *cigars; const uint64_t *cigar_off; uint32_t *cigar_lens;
+    volatile int64_t next;
+    volatile int err;
+} batch_job;
+
+static void *batch_worker(void *arg) {
+    batch_job *j = (batch_job *)arg;
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&j->next, 1, __ATOMIC_RELAXED);
+        if (i >= (int64_t)j->num_pairs) break;
+        uint32_t *cig = NULL, cap = 0;
+        if (j->cigars) { cig = j->cigars + j->cigar_off[i]; cap = (uint32_t)(j->cigar_off[i + 1] - j->cigar_off[i]); }
+        int r = oracle_align(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
+                             j->target_len[i], j->x, j->o, j->e, j->band, j->limit[i], &j->scores[i], &j->flags[i],
+                             cig, cap, &j->cigar_lens[i]);
+        if (r) j->err = r;
+    }
+    return NULL;
+}
+
+/*
+ * Align num_pairs pairs on `threads` host threads.  cigars/cigar_off may be
+ * NULL (scores only); cigar_off has num_pairs + 1 entries when given.
+ */
+int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len, const char *targets,
+                       const uint64_t *target_off, const uint32_t *target_len, uint64_t num_pairs, int32_t x,
+                       int32_t o, int32_t e, int32_t band, const int64_t *limit, int32_t *scores, uint8_t *flags,
+                       uint32_t *cigars, const uint64_t *cigar_off, uint32_t *cigar_lens, int threads) {
+    batch_job j = {reads, targets, read_off, target_off, read_len, target_len, num_pairs, x, o, e, band, limit,
+                   scores, flags, cigars, cigar_off, cigar_lens, 0, 0};
+    if (threads < 1) threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    if (!th) return -3;
+    int started = 0;
+    for (int t = 0; t < threads; ++t)
+        if (pthread_create(&th[t], NULL, batch_worker, &j) == 0) ++started;
+    if (started == 0) batch_worker(&j);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    return j.err;
+}
