@@ -1,0 +1,386 @@
+"""Throughput benchmark: alignments/s of the GPU aligner on a seeded synthetic workload.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+A step aligns one whole batch: 2-bit packing of the ASCII pairs, the
+alignment kernel (threshold early exit, traceback, CIGAR and result writes),
+all through the C ABI (aim_align_batch_ascii) on inputs already in device
+memory.  `e2e` repeats the step with the inputs in pinned host memory and
+the host<->device copies inside the timed region.  Multi-GPU (torchrun): every
+rank aligns its own slice of the pair stream (weak scaling, no collective on
+the data path); timing is bracketed by barriers and the slowest rank counts.
+`--impl reference` times the CPU oracle on a bounded sample of the workload.
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+WORKLOADS = {"wfa_150bp": gen.WFA_150BP, "edit_nw_100bp": gen.EDIT_NW_100BP,
+             "gotoh_250bp": gen.GOTOH_WFA_250BP, "wfa_250bp": gen.GOTOH_WFA_250BP, "wfa_uneven": gen.WFA_UNEVEN}
+ALGO_OF = {"wfa_150bp": "wfa", "edit_nw_100bp": "edit", "gotoh_250bp": "gotoh", "wfa_250bp": "wfa",
+           "wfa_uneven": "wfa"}
+
+# Algorithmic integer operations per unit of counted work (the roofline numerator):
+#   WFA wavefront entry: I~ one max, D~ one max + one add, mismatch candidate one add, f0 two max = 6
+#   WFA extend window (32 bases): two 2-word funnel shifts (3 ops each), xor, clz, halve, cap, advance v and h = 12
+#   Gotoh DP cell: 7 adds + 6 mins + 1 compare = 14;  unit-cost DP cell: 3 adds + 2 mins = 5
+OPS_WF_ENTRY, OPS_EXT_WINDOW, OPS_GOTOH_CELL, OPS_UNIT_CELL = 6, 12, 14, 5
+INT32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="wfa_150bp", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count (0: as defined)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def max_edits_args(w, p):
+    if w.max_edits is not None:
+        return w.max_edits, None
+    me = gen.per_pair_max_edits(w, p)
+    return int(me.max()), me
+
+
+def runs_capacity(w, p, algo):
+    """CIGAR run capacity per pair: every edit run costs at least min(x, o+e) (unit: 1), runs alternate."""
+    _, x, o, e = w.penalties
+    me = gen.per_pair_max_edits(w, p).astype(np.int64)
+    if algo == "edit":
+        lim = me; minc = 1
+    else:
+        lim = me * max(x, o + e); minc = min(x, o + e)
+    cap = 2 * (lim // minc) + 1
+    return np.minimum(cap, p.read_len.astype(np.int64) + p.target_len.astype(np.int64) + 1)
+
+
+def config_of(name, w, n_pairs, algo):
+    c = {"workload": w.name, "pairs_per_gpu": n_pairs, "algo": algo,
+         "read_len": w.len_min if w.len_min == w.len_max else [w.len_min, w.len_max],
+         "edit_rate": w.rate_min if w.rate_min == w.rate_max else [w.rate_min, w.rate_max],
+         "unrelated_frac": w.unrelated_frac, "penalties": {"match": 0, "mismatch": w.penalties[1],
+                                                          "gap_open": w.penalties[2], "gap_extend": w.penalties[3]},
+         "max_edits": w.max_edits if w.max_edits is not None else f"ceil({w.max_edits_frac}*read_len)",
+         "band": w.band if algo != "wfa" or name == "wfa_250bp" else -1,
+         "input": "ASCII pairs, 2-bit packed on device inside the step",
+         "l2": "inputs larger than L2 (no flush needed)"}
+    return c
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.flush(); self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if "Active" in r[5 + j] and "Not" not in r[5 + j]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def traffic_record(kernel: str, workload: str):
+    """dram bytes per launch from a committed ncu summary, if it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        rec = json.load(open(path)).get(f"{kernel}:{workload}")
+    except (OSError, ValueError):
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_2208_01243_gb300", "csrc", rec["source"])
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+        return None
+    return rec
+
+
+# ---------------------------------------------------------------- reference arm (CPU oracle)
+
+def run_reference(args, w, algo):
+    import oracle
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000}[algo]
+    if w is gen.WFA_UNEVEN:
+        sample = 2_000
+    pen = oracle.UNIT if algo == "edit" else w.penalties
+    band = w.band if algo != "wfa" or args.workload == "wfa_250bp" else -1
+    times = []
+    for step in range(args.warmup + args.steps):
+        p = gen.generate(w, sample, first=step * sample)
+        me = gen.per_pair_max_edits(w, p)
+        lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
+        t0 = time.perf_counter()
+        oracle.align_batch(p, pen, lim, band=band, threads=cores)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    ms = 1e3 * float(np.mean(times))
+    value = sample / (ms / 1e3)
+    line = {"impl": "reference", "metric": "alignments/s", "value": value, "unit": "alignments/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_of(args.workload, w, sample, algo),
+            "cpu_baseline": {"value": value, "unit": "alignments/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} pairs per step (pairs drawn from the workload's seeded stream), "
+                                       f"full-matrix DP with canonical traceback on {cores} host threads"},
+            "e2e": {"value": value, "unit": "alignments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline(w, algo):
+    """The oracle as it stands on this host's cores, on a bounded sample (~10-30 s of CPU work)."""
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000}[algo]
+    if w is gen.WFA_UNEVEN:
+        sample = 10_000
+    p = gen.generate(w, sample)
+    me = gen.per_pair_max_edits(w, p)
+    lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
+    pen = oracle.UNIT if algo == "edit" else w.penalties
+    t0 = time.perf_counter()
+    oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": "alignments/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} pairs of the workload, full-matrix DP + canonical traceback, "
+                      f"{dt:.1f} s wall on {cores} threads"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, w, algo):
+    import torch
+    import __graft_entry__
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    __graft_entry__.build()
+    import paper_2208_01243_gb300 as aim
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    n_pairs = args.pairs or w.pairs
+    p = gen.generate(w, n_pairs, first=rank * n_pairs)     # each rank: its own slice of the pair stream
+    max_edits, per_pair = max_edits_args(w, p)
+    band = w.band if algo != "wfa" or args.workload == "wfa_250bp" else -1
+    pen_t = (0, 1, 0, 1) if algo == "edit" else w.penalties
+    pen = aim.penalties(pen_t[1], pen_t[2], pen_t[3], band=band)
+    max_len = int(max(p.read_len.max(), p.target_len.max()))
+    cap = runs_capacity(w, p, algo)
+    coff = np.zeros(n_pairs + 1, np.int64); coff[1:] = np.cumsum(cap)
+
+    host = {"reads": p.reads, "targets": p.targets, "ro": p.read_off, "to": p.target_off, "rl": p.read_len,
+            "tl": p.target_len}
+    if per_pair is not None:
+        host["pp"] = per_pair.astype(np.int32)
+    d = dict(zip(host, aim.upload(*host.values(), device=local)))
+    coff_d = aim.upload(coff, device=local)[0]
+    al = aim.Aligner(local, 8 << 30)
+    out = {"scores": torch.empty(n_pairs, dtype=torch.int32, device=dev),
+           "flags": torch.empty(n_pairs, dtype=torch.uint8, device=dev),
+           "lens": torch.empty(n_pairs, dtype=torch.int32, device=dev),
+           "cigars": torch.empty(int(coff[-1]), dtype=torch.int32, device=dev)}
+
+    def step(src):
+        aim.aim_align_batch_ascii(al.ctx, src["reads"], src["targets"], src["ro"], src["to"], src["rl"], src["tl"],
+                                  max_len, algo, pen, max_edits, src.get("pp"), out["scores"], out["cigars"], coff_d,
+                                  out["lens"], out["flags"])
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step(d)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(); torch.cuda.synchronize()
+    aim.aim_timing_enable(al.ctx, True)
+    aim.aim_timing_read(al.ctx, 0); aim.aim_timing_read(al.ctx, 1)
+    aim.aim_stats_reset(al.ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(d)
+    ev1.record(stream)
+    torch.cuda.synchronize(); barrier(); torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    align_ms, align_n = aim.aim_timing_read(al.ctx, 1)
+    pack_ms, pack_n = aim.aim_timing_read(al.ctx, 0)
+    aim.aim_timing_enable(al.ctx, False)
+    stats = aim.aim_stats_read(al.ctx)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_pairs / (ms / 1e3)
+
+    # ---- end to end through the same call: pinned host inputs in, results out, copies timed
+    hp = {k: torch.from_numpy(np.ascontiguousarray(v).view(
+        {np.dtype(np.uint64): np.int64, np.dtype(np.uint32): np.int32}.get(np.asarray(v).dtype, np.asarray(v).dtype)))
+        .pin_memory() for k, v in host.items()}
+    dd = {k: torch.empty_like(v, device=dev) for k, v in hp.items()}
+    ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
+    h2d = sum(v.numel() * v.element_size() for v in hp.values())
+    d2h = sum(v.numel() * v.element_size() for v in ho.values())
+
+    def e2e_step():
+        for k in hp:
+            dd[k].copy_(hp[k], non_blocking=True)
+        step(dd)
+        for k in out:
+            ho[k].copy_(out[k], non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(); barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(); barrier()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    # the e2e results must equal the device-resident ones
+    assert torch.equal(ho["scores"], out["scores"].cpu())
+
+    if rank != 0:
+        al.close()
+        return 0
+
+    # ---- roofline of the alignment kernel: algorithmic integer ops per launch / its mean launch time
+    props = torch.cuda.get_device_properties(local)
+    peaks = measured_peaks()
+    sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
+    peak_ops = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6
+    launches = max(align_n, 1)
+    if algo == "wfa":
+        ops = stats["wf_entries"] * OPS_WF_ENTRY + stats["extend_windows"] * OPS_EXT_WINDOW
+        kernel = "wfa_kernel"; src_file = "wfa.cu"
+    else:
+        ops = stats["dp_cells"] * (OPS_UNIT_CELL if algo == "edit" else OPS_GOTOH_CELL)
+        kernel = "dp_kernel"; src_file = "dp_banded.cu"
+    ops_per_launch = ops / launches
+    kern_s = align_ms / launches / 1e3
+    achieved = ops_per_launch / kern_s / 1e12
+    tr = traffic_record(kernel, w.name)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops / 1e12, "unit": "Tops/s",
+            "frac": achieved / (peak_ops / 1e12), "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+            "kernel": kernel, "kernel_ms": kern_s * 1e3, "ops_per_launch": ops_per_launch,
+            "peak_note": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz "
+                         "(derived from unit counts and the max SM clock)",
+            "work": {k: v // launches for k, v in stats.items()},
+            "pack_ms_per_launch": pack_ms / max(pack_n, 1)}
+    # input ASCII + offsets + lengths, 2-bit words written and read back, results and the CIGAR runs written
+    packed_words = int(((p.read_len.astype(np.int64) + 31) // 32).sum() + ((p.target_len.astype(np.int64) + 31) // 32).sum())
+    hbm_bytes = (int(p.read_len.sum()) + int(p.target_len.sum()) + n_pairs * 2 * (8 + 4) + 2 * 8 * packed_words
+                 + n_pairs * (4 + 1 + 4 + 8) + 4 * int(out["lens"].cpu().numpy().astype(np.int64).sum()))
+    roof["hbm_note"] = {"algorithmic_bytes_per_step": hbm_bytes,
+                        "achieved_gbs": hbm_bytes / (ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs")}
+
+    line = {"metric": "alignments/s", "value": value, "unit": "alignments/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": config_of(args.workload, w, n_pairs, algo),
+            "cells_per_s": (stats["wf_entries"] if algo == "wfa" else stats["dp_cells"]) / launches / (ms / 1e3),
+            "rejected_frac": float((out["flags"].cpu().numpy() & 1).mean()),
+            "roofline": roof,
+            "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": args.steps * 3,
+            "clocks": clk}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, algo)
+    print(json.dumps(line))
+    al.close()
+    return 0
+
+
+def main():
+    args = parse()
+    w = WORKLOADS[args.workload]
+    algo = ALGO_OF[args.workload]
+    if args.impl == "reference":
+        return run_reference(args, w, algo)
+    return run_ours(args, w, algo)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

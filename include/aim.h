@@ -1,0 +1,198 @@
+/*
+ * aim.h -- C ABI of the GB300 batched pairwise aligner.
+ *
+ * The library aligns very many independent read/target pairs, each under an
+ * edit threshold, and returns for every pair a score and a CIGAR or a reject
+ * flag.  This is the data-parallel core of the Alignment-in-Memory framework
+ * (Section 2.2, Fig. 2, Steps 3-5: fetch a pair, align it and trace back the
+ * alignment operations, write the score and operations back), with the
+ * dispatch over DPUs replaced by one GPU.
+ *
+ * Algorithms (Section 2.4):
+ *   AIM_ALGO_EDIT_NW       Needleman-Wunsch edit distance (Section 2.4.1), unit costs
+ *                          (mismatch 1, gap open 0, gap extend 1); a banded DP.
+ *   AIM_ALGO_GOTOH_BANDED  gap-affine global DP with three tables M, I, D
+ *                          (Section 2.4.2, "SWG"; read as global alignment), banded.
+ *   AIM_ALGO_WFA_AFFINE    gap-affine wavefront algorithm (Section 2.4.4), exact.
+ * All three compute the same exact optimum for the same costs; the CIGAR is
+ * the canonical one (below), so they agree bit for bit.
+ *
+ * Conventions (the paper fixes none of these; they are this library's):
+ *   - Read P[0..n) is the query, target T[0..m) the reference.  Op M/'='
+ *     is a match (cost 0), X a mismatch (cost x), I consumes a read base, D a
+ *     target base.  A maximal run of L I's (or D's) costs o + L*e.
+ *   - CIGAR runs are uint32 len << 4 | BAM code: '=' 7, X 8, I 1, D 2.
+ *   - Canonical CIGAR: among all optimal alignments, the one whose op
+ *     string read backward from the end is lexicographically smallest under
+ *     X < I < D < M (gaps and mismatches as late as possible).
+ *   - Threshold: limit = pen->max_score if >= 0; else max_edits for
+ *     EDIT_NW; else max_edits * max(x, o + e).  A pair whose optimum
+ *     (inside the band, if one is given) exceeds limit, or whose |n - m|
+ *     exceeds the band, is rejected: score -1, flag AIM_F_REJECTED, 0 runs.
+ *     max_edits < 0 and max_score < 0 means no threshold.
+ *   - Sequences are 2-bit packed (aim_pack_2bit): A,C,G,T = 0,1,2,3, base j
+ *     in word j/32 at bits [63-2(j%32)-1, 63-2(j%32)], every sequence starting
+ *     on a word boundary, unused bits zero.
+ *
+ * Memory and streams: every data pointer is device memory owned by the
+ * caller, unless a comment says "host".  The library owns only its context
+ * workspace.  Calls are asynchronous on `stream` (a cudaStream_t, NULL = the
+ * legacy default stream); argument errors are returned synchronously and
+ * per-pair problems come back as flags, never as faults.  Calls that share
+ * one context must not run concurrently (they share its workspace).
+ * Outputs do not depend on batch composition, order or launch form.
+ */
+#ifndef AIM_H
+#define AIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define AIM_API __attribute__((visibility("default")))
+#else
+#define AIM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aim_ctx aim_ctx;
+typedef void *aim_stream_t; /* cudaStream_t */
+
+/* call status */
+enum {
+    AIM_OK = 0,
+    AIM_ERR_ARG = -1,         /* bad argument (null pointer, bad penalties, size out of range) */
+    AIM_ERR_INPUT = -2,       /* bad input data detected synchronously */
+    AIM_ERR_NOMEM = -3,       /* workspace too small even for one pair in flight */
+    AIM_ERR_CUDA = -4,        /* a CUDA call failed; aim_last_cuda_error() has the code */
+    AIM_ERR_UNSUPPORTED = -5  /* valid but not supported (e.g. a band wider than 127 for the DP) */
+};
+
+/* per-pair flags (out_flags) */
+enum {
+    AIM_F_REJECTED = 1,        /* optimum above the limit, or |n - m| above the band */
+    AIM_F_CIGAR_OVERFLOW = 2,  /* score valid; CIGAR needed more runs than its capacity (length still reported) */
+    AIM_F_BAD_PAIR = 4,        /* non-ACGT byte, length above max_length, or per-pair max_edits above max_edits */
+    AIM_F_STEP_CAP = 8         /* internal bound hit (scratch exhausted); no result */
+};
+
+typedef enum { AIM_ALGO_EDIT_NW = 0, AIM_ALGO_GOTOH_BANDED = 1, AIM_ALGO_WFA_AFFINE = 2 } aim_algo_t;
+
+typedef struct {
+    int32_t match;      /* must be 0 (the wavefront algorithm needs it; Section 2.4.4 uses a=0) */
+    int32_t mismatch;   /* x >= 1 */
+    int32_t gap_open;   /* o >= 0 */
+    int32_t gap_extend; /* e >= 1 */
+    int32_t max_score;  /* >= 0: score limit; < 0: derive it from max_edits */
+    int32_t band;       /* >= 0: only alignments with |h - v| <= band; < 0: none */
+} aim_penalties_t;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+AIM_API int aim_version(void);
+
+/* Static text for a status code. */
+AIM_API const char *aim_status_string(int status);
+
+/* cudaError_t of the last failing CUDA call in this thread (0 if none). */
+AIM_API int aim_last_cuda_error(void);
+
+/*
+ * Create a context on CUDA device `device` with a device workspace of
+ * workspace_bytes (0: 1 GiB).  The workspace holds per-warp scratch
+ * (wavefront history, DP trace bits, CIGAR staging) and, for the ASCII entry
+ * point, the packed copies of the sequences.  A call that needs more scratch
+ * than fits runs fewer pairs at once; it fails with AIM_ERR_NOMEM only when
+ * not even one pair's scratch fits.  *out is NULL on failure.
+ */
+AIM_API int aim_create(aim_ctx **out, int device, size_t workspace_bytes);
+
+/* Destroy a context (synchronises the device first).  NULL is accepted. */
+AIM_API int aim_destroy(aim_ctx *ctx);
+
+/*
+ * 2-bit packer (one of the hot-path steps: sequences are moved to device
+ * memory compactly before alignment; the paper transfers pairs to the memory
+ * banks first, Section 2.2 Step 2).
+ *   ascii        count sequences, sequence i at byte ascii + char_offsets[i], lengths[i] bytes
+ *   packed       output words; sequence i written at packed + word_offsets[i], ceil(lengths[i]/32) words
+ *   bad          optional (NULL): bad[i] = 1 if sequence i holds a byte other than A/C/G/T, else 0;
+ *                such a sequence's words are written with the offending bases as 0
+ * Returns AIM_ERR_ARG for null required pointers.
+ */
+AIM_API int aim_pack_2bit(aim_ctx *ctx, const uint8_t *ascii, const uint64_t *char_offsets, const uint32_t *lengths,
+                  uint32_t count, uint64_t *packed, const uint64_t *word_offsets, uint8_t *bad,
+                  aim_stream_t stream);
+
+/*
+ * Align num_pairs packed pairs (Section 2.2 Steps 3-5 for every pair at once).
+ *   packed_reads/_targets      2-bit words (see aim_pack_2bit)
+ *   read_offsets/target_offsets  word offset of each sequence (uint64, num_pairs entries)
+ *   read_lengths/target_lengths  bases (uint32, num_pairs entries)
+ *   max_length                 host value: upper bound on every read and target length in the call;
+ *                              longer pairs are flagged AIM_F_BAD_PAIR.  Sizes the scratch.
+ *   algo, pen                  algorithm and costs (pen is a host pointer)
+ *   max_edits                  edit threshold (see the threshold rule above); when max_edits_per_pair
+ *                              is given it must bound every entry, and pairs above it are flagged BAD_PAIR
+ *   max_edits_per_pair         optional (NULL): per-pair thresholds (int32, device)
+ *   out_scores                 int32 per pair: optimum, or -1 if rejected / bad
+ *   out_cigars, cigar_offsets  optional (both NULL: scores only).  Pair i's runs go to
+ *                              out_cigars + cigar_offsets[i], capacity cigar_offsets[i+1] - cigar_offsets[i]
+ *                              (cigar_offsets has num_pairs + 1 entries)
+ *   out_cigar_lens             optional: runs per pair (the full count even on overflow)
+ *   out_flags                  uint8 per pair (AIM_F_*)
+ * Limits: AIM_ALGO_WFA_AFFINE needs max_length <= 32000; the DP algorithms
+ * need an effective band <= 127 (edit distance: min(band, limit); Gotoh:
+ * min(band, (limit - o) / e)), else AIM_ERR_UNSUPPORTED.
+ */
+AIM_API int aim_align_batch(aim_ctx *ctx, const uint64_t *packed_reads, const uint64_t *packed_targets,
+                    const uint64_t *read_offsets, const uint64_t *target_offsets, const uint32_t *read_lengths,
+                    const uint32_t *target_lengths, uint32_t num_pairs, uint32_t max_length, int algo,
+                    const aim_penalties_t *pen, int32_t max_edits, const int32_t *max_edits_per_pair,
+                    int32_t *out_scores, uint32_t *out_cigars, const uint64_t *cigar_offsets,
+                    uint32_t *out_cigar_lens, uint8_t *out_flags, aim_stream_t stream);
+
+/*
+ * Same as aim_align_batch on ASCII input: packs reads and targets into the
+ * context workspace (ceil(max_length/32) words per sequence), then aligns.
+ * Pairs with a non-ACGT byte get AIM_F_BAD_PAIR and score -1.
+ *   reads/targets          bytes (device); sequence i at reads + read_char_offsets[i]
+ */
+AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint8_t *targets,
+                          const uint64_t *read_char_offsets, const uint64_t *target_char_offsets,
+                          const uint32_t *read_lengths, const uint32_t *target_lengths, uint32_t num_pairs,
+                          uint32_t max_length, int algo, const aim_penalties_t *pen, int32_t max_edits,
+                          const int32_t *max_edits_per_pair, int32_t *out_scores, uint32_t *out_cigars,
+                          const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
+                          aim_stream_t stream);
+
+/*
+ * Work counters, accumulated by the kernels of every call since the last
+ * reset (the figures behind cells/s and the roofline report):
+ *   [0] wavefront entries computed by the WFA (each holds M~, I~, D~)
+ *   [1] 32-base windows compared by the WFA extend
+ *   [2] DP cells computed (in-band cells actually swept, up to early exit)
+ *   [3] pairs aligned (every pair a kernel finished, any flag)
+ * aim_stats_reset is asynchronous on `stream`; aim_stats_read synchronises
+ * the device and copies the four counters to host memory `out`.
+ */
+AIM_API int aim_stats_reset(aim_ctx *ctx, aim_stream_t stream);
+AIM_API int aim_stats_read(aim_ctx *ctx, uint64_t *out /* host, 4 entries */);
+
+/*
+ * Kernel timing.  While enabled, every call records a CUDA event pair on its
+ * stream around each kernel it launches.  aim_timing_read synchronises on the
+ * recorded events, returns the summed device time (ms) and the number of
+ * launches of one kernel kind (0: 2-bit packer, 1: alignment kernels) since
+ * the last read, then clears them.  Up to 4096 launches are kept per kind;
+ * later ones are counted but not timed (*launches still counts them).
+ */
+AIM_API int aim_timing_enable(aim_ctx *ctx, int on);
+AIM_API int aim_timing_read(aim_ctx *ctx, int kind, double *total_ms /* host */, int *launches /* host */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AIM_H */

@@ -1,0 +1,245 @@
+"""GB300 batched pairwise aligner: a thin Python binding over libaim.so.
+
+The functions below carry the C names of include/aim.h and only marshal
+arguments (torch CUDA tensors -> device pointers, the current torch stream
+-> cudaStream_t).  Every step of the alignment runs in the library's CUDA
+kernels; there is no CPU path, and importing a function whose library is not
+built raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import LIB
+
+AIM_OK, AIM_ERR_ARG, AIM_ERR_INPUT, AIM_ERR_NOMEM, AIM_ERR_CUDA, AIM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+AIM_F_REJECTED, AIM_F_CIGAR_OVERFLOW, AIM_F_BAD_PAIR, AIM_F_STEP_CAP = 1, 2, 4, 8
+AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE = 0, 1, 2
+ALGO = {"edit": AIM_ALGO_EDIT_NW, "gotoh": AIM_ALGO_GOTOH_BANDED, "wfa": AIM_ALGO_WFA_AFFINE}
+
+
+class aim_penalties_t(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32), ("max_score", ctypes.c_int32), ("band", ctypes.c_int32)]
+
+
+class AimError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {_lib().aim_status_string(status).decode()} ({status})"
+                         + (f", cudaError {_lib().aim_last_cuda_error()}" if status == AIM_ERR_CUDA else ""))
+
+
+_LIB = None
+EXPORTS = ["aim_version", "aim_status_string", "aim_last_cuda_error", "aim_create", "aim_destroy",
+           "aim_pack_2bit", "aim_align_batch", "aim_align_batch_ascii", "aim_stats_reset", "aim_stats_read",
+           "aim_timing_enable", "aim_timing_read"]
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is not built (run __graft_entry__.build()); the aligner has no CPU path")
+        lib = ctypes.CDLL(LIB)
+        p, u32, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int32
+        lib.aim_version.restype = ctypes.c_int
+        lib.aim_status_string.restype = ctypes.c_char_p
+        lib.aim_status_string.argtypes = [ctypes.c_int]
+        lib.aim_create.argtypes = [ctypes.POINTER(p), ctypes.c_int, ctypes.c_size_t]
+        lib.aim_destroy.argtypes = [p]
+        lib.aim_pack_2bit.argtypes = [p, p, p, p, u32, p, p, p, p]
+        lib.aim_align_batch.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.c_int, ctypes.POINTER(aim_penalties_t),
+                                        i32, p, p, p, p, p, p, p]
+        lib.aim_align_batch_ascii.argtypes = lib.aim_align_batch.argtypes
+        lib.aim_stats_reset.argtypes = [p, p]
+        lib.aim_stats_read.argtypes = [p, p]
+        lib.aim_timing_enable.argtypes = [p, ctypes.c_int]
+        lib.aim_timing_read.argtypes = [p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc: int, what: str):
+    if rc != AIM_OK:
+        raise AimError(rc, what)
+
+
+# a C uint64/uint32 array may be passed as the signed torch type of the same width
+_SAME_WIDTH = {torch.uint64: (torch.uint64, torch.int64), torch.uint32: (torch.uint32, torch.int32),
+               torch.int32: (torch.int32, torch.uint32), torch.uint8: (torch.uint8, torch.int8)}
+
+
+def _ptr(t, dtype=None, name="tensor", optional=False):
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype not in _SAME_WIDTH.get(dtype, (dtype,)):
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def penalties(mismatch=4, gap_open=6, gap_extend=2, max_score=-1, band=-1, match=0) -> aim_penalties_t:
+    return aim_penalties_t(match, mismatch, gap_open, gap_extend, max_score, band)
+
+
+def aim_version() -> int:
+    return int(_lib().aim_version())
+
+
+def aim_create(device: int = 0, workspace_bytes: int = 0) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(_lib().aim_create(ctypes.byref(ctx), device, workspace_bytes), "aim_create")
+    return ctx
+
+
+def aim_destroy(ctx) -> None:
+    _check(_lib().aim_destroy(ctx), "aim_destroy")
+
+
+def aim_pack_2bit(ctx, ascii, char_offsets, lengths, packed, word_offsets, bad=None, stream=None) -> None:
+    u8, u64, u32 = torch.uint8, torch.uint64, torch.uint32
+    _check(_lib().aim_pack_2bit(ctx, _ptr(ascii, u8, "ascii"), _ptr(char_offsets, u64, "char_offsets"),
+                                _ptr(lengths, u32, "lengths"), int(lengths.numel()), _ptr(packed, u64, "packed"),
+                                _ptr(word_offsets, u64, "word_offsets"), _ptr(bad, u8, "bad", True),
+                                _stream(stream)), "aim_pack_2bit")
+
+
+def aim_stats_reset(ctx, stream=None) -> None:
+    _check(_lib().aim_stats_reset(ctx, _stream(stream)), "aim_stats_reset")
+
+
+def aim_stats_read(ctx) -> dict:
+    import numpy as np
+    out = np.zeros(4, np.uint64)
+    _check(_lib().aim_stats_read(ctx, ctypes.c_void_p(out.ctypes.data)), "aim_stats_read")
+    return {"wf_entries": int(out[0]), "extend_windows": int(out[1]), "dp_cells": int(out[2]), "pairs": int(out[3])}
+
+
+def aim_timing_enable(ctx, on: bool = True) -> None:
+    _check(_lib().aim_timing_enable(ctx, int(bool(on))), "aim_timing_enable")
+
+
+def aim_timing_read(ctx, kind: int) -> tuple[float, int]:
+    """(total device ms, launches) of kernel kind 0 (packer) or 1 (alignment) since the last read."""
+    ms = ctypes.c_double(); n = ctypes.c_int()
+    _check(_lib().aim_timing_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)), "aim_timing_read")
+    return ms.value, n.value
+
+
+def _align_args(num_pairs, max_length, algo, pen, max_edits, max_edits_per_pair, out_scores, out_cigars,
+                cigar_offsets, out_cigar_lens, out_flags, stream):
+    a = ALGO[algo] if isinstance(algo, str) else int(algo)
+    return [ctypes.c_uint32(num_pairs), ctypes.c_uint32(max_length), ctypes.c_int(a), ctypes.byref(pen),
+            ctypes.c_int32(max_edits), _ptr(max_edits_per_pair, torch.int32, "max_edits_per_pair", True),
+            _ptr(out_scores, torch.int32, "out_scores"), _ptr(out_cigars, torch.uint32, "out_cigars", True),
+            _ptr(cigar_offsets, torch.uint64, "cigar_offsets", True),
+            _ptr(out_cigar_lens, torch.uint32, "out_cigar_lens", True), _ptr(out_flags, torch.uint8, "out_flags"),
+            _stream(stream)]
+
+
+def aim_align_batch(ctx, packed_reads, packed_targets, read_offsets, target_offsets, read_lengths, target_lengths,
+                    max_length, algo, pen, max_edits, max_edits_per_pair, out_scores, out_cigars, cigar_offsets,
+                    out_cigar_lens, out_flags, stream=None) -> None:
+    u64, u32 = torch.uint64, torch.uint32
+    n = int(read_lengths.numel())
+    _check(_lib().aim_align_batch(ctx, _ptr(packed_reads, u64, "packed_reads"),
+                                  _ptr(packed_targets, u64, "packed_targets"), _ptr(read_offsets, u64, "read_offsets"),
+                                  _ptr(target_offsets, u64, "target_offsets"), _ptr(read_lengths, u32, "read_lengths"),
+                                  _ptr(target_lengths, u32, "target_lengths"),
+                                  *_align_args(n, max_length, algo, pen, max_edits, max_edits_per_pair, out_scores,
+                                               out_cigars, cigar_offsets, out_cigar_lens, out_flags, stream)),
+           "aim_align_batch")
+
+
+def aim_align_batch_ascii(ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths,
+                          target_lengths, max_length, algo, pen, max_edits, max_edits_per_pair, out_scores,
+                          out_cigars, cigar_offsets, out_cigar_lens, out_flags, stream=None) -> None:
+    u8, u64, u32 = torch.uint8, torch.uint64, torch.uint32
+    n = int(read_lengths.numel())
+    _check(_lib().aim_align_batch_ascii(ctx, _ptr(reads, u8, "reads"), _ptr(targets, u8, "targets"),
+                                        _ptr(read_char_offsets, u64, "read_char_offsets"),
+                                        _ptr(target_char_offsets, u64, "target_char_offsets"),
+                                        _ptr(read_lengths, u32, "read_lengths"),
+                                        _ptr(target_lengths, u32, "target_lengths"),
+                                        *_align_args(n, max_length, algo, pen, max_edits, max_edits_per_pair,
+                                                     out_scores, out_cigars, cigar_offsets, out_cigar_lens, out_flags,
+                                                     stream)),
+           "aim_align_batch_ascii")
+
+
+class Aligner:
+    """Owns a context; allocates outputs as torch tensors on its device."""
+
+    def __init__(self, device: int = 0, workspace_bytes: int = 0):
+        self.device = device
+        self.ctx = aim_create(device, workspace_bytes)
+
+    def close(self):
+        if self.ctx is not None:
+            aim_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, num_pairs: int, cigar_capacity=None):
+        """Output tensors; cigar_capacity: per-pair run capacity (tensor/int) or None for scores only."""
+        dev = torch.device("cuda", self.device)
+        out = {"scores": torch.empty(num_pairs, dtype=torch.int32, device=dev),
+               "flags": torch.empty(num_pairs, dtype=torch.uint8, device=dev),
+               "cigar_lens": torch.empty(num_pairs, dtype=torch.int32, device=dev),
+               "cigars": None, "cigar_offsets": None}
+        if cigar_capacity is not None:
+            cap = (torch.full((num_pairs,), int(cigar_capacity), dtype=torch.int64, device=dev)
+                   if isinstance(cigar_capacity, int) else cigar_capacity.to(dev, torch.int64))
+            off = torch.zeros(num_pairs + 1, dtype=torch.int64, device=dev)
+            off[1:] = torch.cumsum(cap, 0)
+            out["cigar_offsets"] = off
+            out["cigars"] = torch.empty(int(off[-1].item()), dtype=torch.int32, device=dev)
+        return out
+
+    def align_ascii(self, reads, targets, read_char_offsets, target_char_offsets, read_lengths, target_lengths,
+                    max_length, algo, pen, max_edits, max_edits_per_pair=None, out=None, stream=None):
+        n = int(read_lengths.numel())
+        out = out or self.outputs(n, None)
+        return self._run_ascii(out, reads, targets, read_char_offsets, target_char_offsets, read_lengths,
+                               target_lengths, max_length, algo, pen, max_edits, max_edits_per_pair, stream)
+
+    def _run_ascii(self, out, reads, targets, read_char_offsets, target_char_offsets, read_lengths, target_lengths,
+                   max_length, algo, pen, max_edits, max_edits_per_pair, stream):
+        aim_align_batch_ascii(self.ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths,
+                              target_lengths, max_length, algo, pen, max_edits, max_edits_per_pair, out["scores"],
+                              out["cigars"], out["cigar_offsets"], out["cigar_lens"], out["flags"], stream)
+        return out
+
+
+def upload(*arrays, device: int = 0):
+    """numpy arrays -> CUDA tensors (uint64 as int64, uint32 as int32: same bits)."""
+    import numpy as np
+    out = []
+    for a in arrays:
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint64:
+            a = a.view(np.int64)
+        elif a.dtype == np.uint32:
+            a = a.view(np.int32)
+        out.append(torch.from_numpy(a).to(torch.device("cuda", device)))
+    return out

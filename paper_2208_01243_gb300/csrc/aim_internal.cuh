@@ -1,0 +1,193 @@
+// Internal declarations shared by the CUDA translation units of the aligner.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/aim.h"
+
+namespace aim {
+
+constexpr int kWarp = 32;
+constexpr int16_t kNeg16 = -16384;           // invalid wavefront offset (any value < 0 is invalid)
+constexpr int32_t kInf = 1 << 28;            // DP infinity
+constexpr uint32_t kMaxWfaLength = 32000;    // offsets are stored as int16
+constexpr int kMaxDpBand = 127;              // DP kernels: 2*band+1 diagonals over R <= 4 lane blocks
+
+// BAM CIGAR op codes
+constexpr uint32_t kOpMatch = 7, kOpMismatch = 8, kOpIns = 1, kOpDel = 2;
+
+// ---- packed sequence access (2 bits per base, first base in the top bits) ----
+
+__device__ __forceinline__ uint32_t base_at(const uint64_t* __restrict__ w, uint32_t i) {
+    return (uint32_t)(__ldg(w + (i >> 5)) >> (62 - 2 * (i & 31))) & 3u;
+}
+
+// 32 bases starting at base `pos` of a sequence of `nwords` words, first base in the top bits.
+// Bases past the last word read as 0; callers cap comparisons by the remaining length.
+__device__ __forceinline__ uint64_t window32(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
+    uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
+    uint64_t hi = wi < nwords ? __ldg(w + wi) : 0ull;
+    if (sh == 0) return hi;
+    uint64_t lo = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0ull;
+    return (hi << sh) | (lo >> (64 - sh));
+}
+
+// ---- per-call description handed to the kernels ----
+
+struct Costs {
+    int32_t x, o, e;   // mismatch, gap open, gap extend (match is 0)
+};
+
+struct PairsView {
+    const uint64_t* reads;
+    const uint64_t* targets;
+    const uint64_t* read_off;
+    const uint64_t* target_off;
+    const uint32_t* read_len;
+    const uint32_t* target_len;
+    const uint8_t* bad_r;        // optional per-read input-error flags (ASCII path), may be null
+    const uint8_t* bad_t;        // optional per-target input-error flags, may be null
+    uint32_t num_pairs;
+    uint32_t max_length;
+    uint64_t stride;             // words per sequence when the offset arrays are null
+};
+
+__device__ __forceinline__ const uint64_t* read_words(const PairsView& P, uint32_t i) {
+    return P.reads + (P.read_off ? __ldg(P.read_off + i) : (uint64_t)i * P.stride);
+}
+__device__ __forceinline__ const uint64_t* target_words(const PairsView& P, uint32_t i) {
+    return P.targets + (P.target_off ? __ldg(P.target_off + i) : (uint64_t)i * P.stride);
+}
+
+struct OutView {
+    int32_t* scores;
+    uint32_t* cigars;            // may be null
+    const uint64_t* cigar_off;   // may be null
+    uint32_t* cigar_lens;        // may be null
+    uint8_t* flags;
+    unsigned long long* stats;   // work counters (see aim_stats_read), may be null
+};
+
+struct LimitView {
+    int64_t limit;               // limit for every pair when per_pair is null (kUnbounded: none)
+    const int32_t* per_pair;     // per-pair max_edits, or null
+    int32_t max_edits_bound;     // upper bound for per_pair entries
+    int32_t edit_cost;           // limit = per_pair * edit_cost (unit: 1, affine: max(x, o+e))
+};
+
+constexpr int64_t kUnbounded = (int64_t)1 << 40;
+
+// limit of pair i; -2 if its per-pair threshold exceeds the stated bound
+__device__ __forceinline__ bool pair_bad(const PairsView& P, uint32_t i) {
+    return (P.bad_r && P.bad_r[i]) || (P.bad_t && P.bad_t[i]);
+}
+
+__device__ __forceinline__ int64_t pair_limit(const LimitView& L, uint32_t i) {
+    if (L.per_pair == nullptr) return L.limit;
+    int32_t me = __ldg(L.per_pair + i);
+    if (me > L.max_edits_bound) return -2;
+    if (me < 0) return kUnbounded;
+    return (int64_t)me * L.edit_cost;
+}
+
+// ---- launchers (each returns a cudaError_t) ----
+
+cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const uint32_t* len, uint32_t count,
+                        uint64_t* packed, const uint64_t* word_off, uint64_t word_stride, uint8_t* bad,
+                        cudaStream_t st);
+
+struct DpPlan {
+    int band;            // effective band b (2b+1 diagonals)
+    int blocks;          // lane blocks R (1, 2 or 4)
+    bool unit;
+    size_t slot_bytes;   // per-warp scratch
+};
+DpPlan plan_dp(bool unit, int band, uint32_t max_length, int64_t max_limit_hint);
+cudaError_t launch_dp(const DpPlan& plan, const Costs& c, const PairsView& P, const LimitView& L, const OutView& O,
+                      int64_t max_limit, uint8_t* scratch, size_t scratch_bytes, uint32_t* counter,
+                      int num_sms, cudaStream_t st, int* warps_used);
+
+struct WfaPlan {
+    int g;               // gcd of the costs; scores run in units of g
+    int x, oe, e;        // scaled mismatch, open+extend, extend
+    int64_t smax;        // largest scaled score any pair may reach
+    int band;            // < 0: none
+    size_t slot_bytes;   // per-warp scratch
+    size_t hist_elems;   // int16 entries of wavefront history per warp
+    int runs_cap;        // CIGAR runs staged per warp
+};
+WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
+cudaError_t launch_wfa(const WfaPlan& plan, const Costs& c, const PairsView& P, const LimitView& L,
+                       const OutView& O, uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms,
+                       cudaStream_t st, int* warps_used);
+
+}  // namespace aim
+
+namespace aim {
+
+constexpr uint32_t kFull = 0xffffffffu;
+
+__host__ __device__ __forceinline__ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Run-length encoder for ops produced end-first (one thread).  Runs land in
+// `runs` in end-first order; `n` counts every run, even past `cap`.
+struct RunWriter {
+    uint32_t* runs;
+    uint32_t cap;
+    uint32_t n;
+    uint32_t op;
+    uint32_t len;
+    __device__ __forceinline__ void init(uint32_t* r, uint32_t c) { runs = r; cap = c; n = 0; op = 0; len = 0; }
+    __device__ __forceinline__ void flush() {
+        if (len) {
+            if (n < cap) runs[n] = (len << 4) | op;
+            ++n;
+        }
+    }
+    __device__ __forceinline__ void put(uint32_t o, uint32_t l) {
+        if (o == op) { len += l; return; }
+        flush();
+        op = o; len = l;
+    }
+    __device__ __forceinline__ void finish() { flush(); len = 0; }
+};
+
+// Lane 0 only: score/flags/run count of pair i.
+__device__ __forceinline__ void write_header(const OutView& O, uint32_t i, int32_t score, uint8_t flags,
+                                             uint32_t nruns) {
+    O.scores[i] = score;
+    O.flags[i] = flags;
+    if (O.cigar_lens) O.cigar_lens[i] = nruns;
+}
+
+// Whole warp: copy end-first staged runs into pair i's CIGAR in start-first
+// order, or flag an overflow.  `nruns` and `staged_ok` must be warp-uniform.
+__device__ __forceinline__ void write_cigar(const OutView& O, uint32_t i, int32_t score, const uint32_t* staged,
+                                            uint32_t nruns, bool staged_ok, uint32_t lane) {
+    uint8_t flags = staged_ok ? 0 : AIM_F_STEP_CAP;
+    if (O.cigars && O.cigar_off && staged_ok) {
+        const uint64_t off = O.cigar_off[i];
+        const uint64_t cap = O.cigar_off[i + 1] - off;
+        if (nruns <= cap) {
+            for (uint32_t j = lane; j < nruns; j += 32) O.cigars[off + j] = staged[nruns - 1 - j];
+        } else {
+            flags |= AIM_F_CIGAR_OVERFLOW;
+        }
+    }
+    if (lane == 0) write_header(O, i, staged_ok ? score : -1, flags, nruns);
+}
+
+}  // namespace aim
+
+namespace aim {
+
+// Whole warp: add each lane's counter into stats[slot] with one atomic per warp.
+__device__ __forceinline__ void warp_stat_add(unsigned long long* stats, int slot, unsigned long long v,
+                                              uint32_t lane) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (stats && lane == 0 && v) atomicAdd(stats + slot, v);
+}
+
+}  // namespace aim

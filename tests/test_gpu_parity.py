@@ -1,0 +1,197 @@
+"""CUDA path vs the oracle, element by element (scores, flags, CIGAR runs).
+
+Sizes the oracle finishes in seconds span many warps and a ragged tail
+(counts not a multiple of the 8 warps of a block or of the grid); the full
+sizes of the large workloads are run on the device in full and checked on a
+seeded sample against the oracle plus whole-batch properties.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from devutil import assert_same, device_results, limits, oracle_results
+from oracle.cigar import cost, decode
+
+pytestmark = pytest.mark.gpu
+
+AFF = (0, 4, 6, 2)
+
+
+@pytest.fixture(scope="module")
+def aligner():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2208_01243_gb300 as aim
+    a = aim.Aligner(0, 4 << 30)
+    yield a
+    a.close()
+
+
+@pytest.mark.parametrize("path", ["ascii", "packed"])
+def test_edit_nw_100bp_all_pairs(aligner, oracle_lib, gen_lib, path):
+    w = gen.EDIT_NW_100BP
+    p = gen.generate(w)                       # all 10,000 pairs
+    orc = oracle_results(p, oracle.UNIT, limits(w, p))
+    dev = device_results(p, "edit", oracle.UNIT, 10, path=path, aligner=aligner)
+    assert_same(dev, orc, what=f"edit nw {path}")
+    # the textbook Levenshtein agrees with the scores on a sample
+    for i in range(0, len(p), 997):
+        assert dev[0][i] == oracle.levenshtein(p.read(i), p.target(i))
+
+
+def test_wfa_150bp_parity_small(aligner, oracle_lib, gen_lib):
+    w = gen.WFA_150BP
+    p = gen.generate(w, 20_011)
+    orc = oracle_results(p, AFF, limits(w, p))
+    dev = device_results(p, "wfa", AFF, 6, aligner=aligner)
+    assert_same(dev, orc, what="wfa 150bp")
+    rej = (dev[1] & oracle.F_REJECTED) > 0
+    assert rej.sum() > 0 and (rej <= p.unrelated.astype(bool)).all()   # only unrelated pairs are rejected
+
+
+@pytest.mark.parametrize("algo", ["gotoh", "wfa"])
+def test_gotoh_wfa_250bp_band25_parity_small(aligner, oracle_lib, gen_lib, algo):
+    w = gen.GOTOH_WFA_250BP
+    p = gen.generate(w, 3_001)
+    orc = oracle_results(p, AFF, limits(w, p), band=25)
+    dev = device_results(p, algo, AFF, 25, band=25, aligner=aligner)
+    assert_same(dev, orc, what=f"{algo} band 25")
+
+
+def test_wfa_uneven_parity_sample(aligner, oracle_lib, gen_lib):
+    w = gen.WFA_UNEVEN
+    p = gen.generate(w, 1_500)
+    me = gen.per_pair_max_edits(w, p)
+    orc = oracle_results(p, AFF, limits(w, p))
+    dev = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    assert_same(dev, orc, what="wfa uneven")
+
+
+def test_unbanded_gotoh_equals_wfa(aligner, gen_lib):
+    """Gotoh with the band derived from the limit (exact) == WFA, CIGAR included."""
+    p = gen.generate(gen.WFA_150BP, 10_007)
+    a = device_results(p, "gotoh", AFF, 6, aligner=aligner)
+    b = device_results(p, "wfa", AFF, 6, aligner=aligner)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert all(np.array_equal(x, y) for x, y in zip(a[2], b[2]))
+
+
+def test_wfa_150bp_full_size(aligner, oracle_lib, gen_lib):
+    """All 1,000,000 pairs on the device; a seeded sample against the oracle; properties on the rest."""
+    w = gen.WFA_150BP
+    p = gen.generate(w)
+    dev = device_results(p, "wfa", AFF, 6, aligner=aligner)
+    s, f = dev[0], dev[1]
+    rej = (f & oracle.F_REJECTED) > 0
+    assert not (f & ~np.uint8(oracle.F_REJECTED)).any()
+    related = ~p.unrelated.astype(bool)
+    assert not rej[related].any()                      # <= 6 edits never exceed 6 * 8
+    bound = gen.script_cost_bound(p, 4, 6, 2)
+    assert (s[related] <= bound[related]).all() and (s[related] >= 0).all()
+    idx = np.random.default_rng(2).choice(len(p), 3000, replace=False)
+    sub = gen.generate(w, index=idx)
+    orc = oracle_results(sub, AFF, limits(w, sub))
+    assert_same(dev, orc, idx=idx, what="wfa 150bp full-size sample")
+    for i in idx[:500]:
+        if not rej[i]:
+            assert cost(decode(dev[2][i]), p.read(i), p.target(i), AFF) == s[i]
+
+
+def test_gotoh_wfa_250bp_full_size_cross_check(aligner, oracle_lib, gen_lib):
+    """1,000,000 pairs: banded Gotoh and banded WFA agree bit for bit; a sample matches the oracle."""
+    w = gen.GOTOH_WFA_250BP
+    p = gen.generate(w)
+    a = device_results(p, "gotoh", AFF, 25, band=25, aligner=aligner)
+    b = device_results(p, "wfa", AFF, 25, band=25, aligner=aligner)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[3], b[3])
+    assert all(np.array_equal(x, y) for x, y in zip(a[2], b[2]))
+    idx = np.random.default_rng(3).choice(len(p), 1000, replace=False)
+    sub = gen.generate(w, index=idx)
+    assert_same(a, oracle_results(sub, AFF, limits(w, sub), band=25), idx=idx, what="gotoh 250bp sample")
+
+
+# ---------------- edge cases ----------------
+
+EDGE_READS = ["", "", "A", "ACGT", "A" * 31, "C" * 32, "G" * 33, "ACGT" * 16, "ACGT" * 16 + "A", "T" * 65,
+              "AAAA", "GATTACA", "ACGTACGT", "ACGTTGCA", "A" * 40]
+EDGE_TARGS = ["", "ACG", "", "ACGT", "A" * 32, "C" * 31, "G" * 33, "ACGT" * 16 + "A", "ACGT" * 16, "T" * 64,
+              "CCCC", "GCATTAC", "ACTTACGGT", "ACGTTGCA", "C" * 40]
+
+
+@pytest.mark.parametrize("algo,pen", [("edit", oracle.UNIT), ("gotoh", AFF), ("wfa", AFF), ("wfa", (0, 3, 4, 1)),
+                                      ("gotoh", (0, 2, 1, 1))])
+def test_edge_cases(aligner, oracle_lib, algo, pen):
+    p = gen.from_strings(EDGE_READS, EDGE_TARGS)
+    for max_edits in (-1, 0, 3):
+        if algo != "wfa" and max_edits < 0:
+            continue          # the DP needs a band; unbounded below is covered by the WFA
+        unit = algo == "edit"
+        lim = np.full(len(p), oracle.limit_for(pen, max_edits, unit=unit), np.int64)
+        orc = oracle_results(p, pen, lim)
+        dev = device_results(p, algo, pen, max_edits, aligner=aligner)
+        assert_same(dev, orc, what=f"edges {algo} {pen} max_edits={max_edits}")
+
+
+def test_max_score_overrides_and_bands(aligner, oracle_lib, gen_lib):
+    p = gen.generate(gen.WFA_150BP, 500)
+    for band in (-1, 3, 10):
+        for algo in ("wfa", "gotoh"):
+            if algo == "gotoh" and band < 0:
+                continue
+            lim = np.full(len(p), 30, np.int64)
+            orc = oracle_results(p, AFF, lim, band=band)
+            dev = device_results(p, algo, AFF, 6, band=band, max_score=30, aligner=aligner)
+            assert_same(dev, orc, what=f"{algo} band {band} max_score 30")
+
+
+def test_bad_inputs_flagged(aligner, oracle_lib):
+    p = gen.from_strings(["ACGT", "ACNT", "ACGT", "A" * 50], ["ACGT", "ACGT", "ACGX", "A" * 50])
+    dev = device_results(p, "wfa", AFF, 2, max_length=40, aligner=aligner)
+    assert list(dev[1]) == [0, 4, 4, 4] and list(dev[0]) == [0, -1, -1, -1]
+    # per-pair threshold above the stated bound
+    dev = device_results(p, "wfa", AFF, 2, per_pair=np.array([1, 1, 1, 3], np.int32), aligner=aligner)
+    assert dev[1][3] == 4
+
+
+def test_cigar_overflow_reports_length(aligner, oracle_lib):
+    p = gen.from_strings(["ACGTACGT", "GATTACA"], ["ACTTACGGT", "GCATTAC"])
+    dev = device_results(p, "wfa", AFF, -1, cigar_cap=np.array([2, 20]), aligner=aligner)
+    assert dev[1][0] == oracle.F_CIGAR_OVERFLOW and dev[3][0] == 5 and dev[0][0] == 12
+    assert dev[1][1] == 0 and decode(dev[2][1]) == "MDMMMMMI"
+
+
+def test_device_packer_matches_layout(aligner):
+    import torch
+    import paper_2208_01243_gb300 as aim
+    from oracle import pack
+    rng = np.random.default_rng(5)
+    seqs = [bytes(rng.choice(list(b"ACGT"), size=int(L))) for L in [0, 1, 31, 32, 33, 63, 64, 65, 100, 1000, 5]]
+    seqs.append(b"ACGTN" + b"A" * 40)
+    lens = np.array([len(s) for s in seqs], np.uint32)
+    co = np.zeros(len(seqs), np.int64); co[1:] = np.cumsum(lens[:-1])
+    wo = np.zeros(len(seqs), np.int64); wo[1:] = np.cumsum((lens[:-1].astype(np.int64) + 31) // 32)
+    total = int(wo[-1] + (int(lens[-1]) + 31) // 32)
+    ascii_, l_, co_, wo_ = aim.upload(np.frombuffer(b"".join(seqs), np.uint8), lens, co, wo)
+    packed = torch.full((total,), -1, dtype=torch.int64, device=ascii_.device)
+    bad = torch.zeros(len(seqs), dtype=torch.uint8, device=ascii_.device)
+    aim.aim_pack_2bit(aligner.ctx, ascii_, co_, l_, packed, wo_, bad)
+    torch.cuda.synchronize()
+    got = packed.cpu().numpy().view(np.uint64)
+    for i, s in enumerate(seqs[:-1]):
+        want = np.array(pack.pack_one(s), np.uint64)
+        assert np.array_equal(got[wo[i]:wo[i] + len(want)], want), i
+    assert list(bad.cpu().numpy()) == [0] * (len(seqs) - 1) + [1]
+
+
+def test_results_independent_of_batch_composition(aligner, gen_lib):
+    """Each pair's result is the same alone, in a shuffled batch and with a small workspace."""
+    p = gen.generate(gen.WFA_UNEVEN, 600)
+    me = gen.per_pair_max_edits(gen.WFA_UNEVEN, p)
+    full = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    perm = np.random.default_rng(9).permutation(len(p))
+    sub = gen.generate(gen.WFA_UNEVEN, index=perm)
+    shuf = device_results(sub, "wfa", AFF, int(me.max()), per_pair=me[perm], max_length=1000, workspace=64 << 20)
+    for j, i in enumerate(perm):
+        assert shuf[0][j] == full[0][i] and shuf[1][j] == full[1][i]
+        assert np.array_equal(shuf[2][j], full[2][i])
