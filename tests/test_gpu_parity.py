@@ -166,7 +166,8 @@ def test_device_packer_matches_layout(aligner):
     import paper_2208_01243_gb300 as aim
     from oracle import pack
     rng = np.random.default_rng(5)
-    seqs = [bytes(rng.choice(list(b"ACGT"), size=int(L))) for L in [0, 1, 31, 32, 33, 63, 64, 65, 100, 1000, 5]]
+    seqs = [rng.choice(np.frombuffer(b"ACGT", np.uint8), size=int(L)).tobytes()
+            for L in [0, 1, 31, 32, 33, 63, 64, 65, 100, 1000, 5]]
     seqs.append(b"ACGTN" + b"A" * 40)
     lens = np.array([len(s) for s in seqs], np.uint32)
     co = np.zeros(len(seqs), np.int64); co[1:] = np.cumsum(lens[:-1])
