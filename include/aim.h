@@ -192,6 +192,42 @@ AIM_API int aim_stats_read(aim_ctx *ctx, uint64_t *out /* host, 4 entries */);
 AIM_API int aim_timing_enable(aim_ctx *ctx, int on);
 AIM_API int aim_timing_read(aim_ctx *ctx, int kind, double *total_ms /* host */, int *launches /* host */);
 
+/*
+ * aim_wfa_align_static -- the gap-affine wavefront aligner (as aim_align_batch
+ * with AIM_ALGO_WFA_AFFINE) for callers that cannot allocate device memory.
+ * The paper has no counterpart; this is a deployment convenience.
+ *
+ * Who needs it: code that is not free to call cudaMalloc -- a plugin inside a
+ * host application that owns a fixed device-memory budget, a latency-critical
+ * loop that must not make a call that can block on the device, or a process
+ * whose device footprint must be fixed at start-up.  Such callers cannot create
+ * a context (aim_create allocates its workspace), so this call takes none.
+ *
+ * Memory: the call allocates nothing.  The caller passes inputs and outputs
+ * exactly as for aim_align_batch.  Scratch comes from one 32 MiB device array
+ * inside the library, which every GPU that loads the library's device code
+ * holds until the process exits.  Every call on a device shares that array:
+ * calls that overlap on the GPU (two streams, two threads) race and give wrong
+ * results, so serialise them.  Each call clears what must start at zero.
+ *
+ * Set-up: the first call on each device (run it with that device current)
+ * looks up the array's device address and caches it; make that first call
+ * before any stream capture.
+ *
+ * Limits: if one pair's scratch (from max_length, the threshold and the band;
+ * about 4.5 KB for 150 bp reads at 6 edits, about 1 MB for 1 kbp at 100 edits)
+ * exceeds the 32 MiB array, the call returns AIM_ERR_NOMEM and launches
+ * nothing.  Smaller scratch needs let more warps run at once.  Otherwise
+ * arguments, flags and results are those of aim_align_batch, bit for bit.
+ */
+AIM_API int aim_wfa_align_static(const uint64_t *packed_reads, const uint64_t *packed_targets,
+                                 const uint64_t *read_offsets, const uint64_t *target_offsets,
+                                 const uint32_t *read_lengths, const uint32_t *target_lengths, uint32_t num_pairs,
+                                 uint32_t max_length, const aim_penalties_t *pen, int32_t max_edits,
+                                 const int32_t *max_edits_per_pair, int32_t *out_scores, uint32_t *out_cigars,
+                                 const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
+                                 aim_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

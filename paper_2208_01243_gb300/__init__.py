@@ -55,6 +55,8 @@ def _lib():
         lib.aim_align_batch.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.c_int, ctypes.POINTER(aim_penalties_t),
                                         i32, p, p, p, p, p, p, p]
         lib.aim_align_batch_ascii.argtypes = lib.aim_align_batch.argtypes
+        lib.aim_wfa_align_static.argtypes = [p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p,
+                                             p, p, p, p, p]
         lib.aim_stats_reset.argtypes = [p, p]
         lib.aim_stats_read.argtypes = [p, p]
         lib.aim_timing_enable.argtypes = [p, ctypes.c_int]
@@ -117,6 +119,24 @@ def aim_pack_2bit(ctx, ascii, char_offsets, lengths, packed, word_offsets, bad=N
                                 _ptr(lengths, u32, "lengths"), int(lengths.numel()), _ptr(packed, u64, "packed"),
                                 _ptr(word_offsets, u64, "word_offsets"), _ptr(bad, u8, "bad", True),
                                 _stream(stream)), "aim_pack_2bit")
+
+
+def aim_wfa_align_static(packed_reads, packed_targets, read_offsets, target_offsets, read_lengths, target_lengths,
+                         max_length, pen, max_edits, max_edits_per_pair, out_scores, out_cigars, cigar_offsets,
+                         out_cigar_lens, out_flags, stream=None) -> None:
+    """The WFA with the library's fixed 32 MiB scratch: no context, nothing allocated (see aim.h)."""
+    u64, u32 = torch.uint64, torch.uint32
+    n = int(read_lengths.numel())
+    args = _align_args(n, max_length, AIM_ALGO_WFA_AFFINE, pen, max_edits, max_edits_per_pair, out_scores,
+                       out_cigars, cigar_offsets, out_cigar_lens, out_flags, stream)
+    del args[2]   # no algorithm argument
+    _check(_lib().aim_wfa_align_static(_ptr(packed_reads, u64, "packed_reads"),
+                                       _ptr(packed_targets, u64, "packed_targets"),
+                                       _ptr(read_offsets, u64, "read_offsets"),
+                                       _ptr(target_offsets, u64, "target_offsets"),
+                                       _ptr(read_lengths, u32, "read_lengths"),
+                                       _ptr(target_lengths, u32, "target_lengths"), *args),
+           "aim_wfa_align_static")
 
 
 def aim_stats_reset(ctx, stream=None) -> None:
