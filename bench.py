@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count (0: as defined)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workspace-gb", type=float, default=8.0, help="aligner context workspace (GiB)")
     return ap.parse_args()
 
 
@@ -241,7 +242,7 @@ def run_ours(args, w, algo):
         host["pp"] = per_pair.astype(np.int32)
     d = dict(zip(host, aim.upload(*host.values(), device=local)))
     coff_d = aim.upload(coff, device=local)[0]
-    al = aim.Aligner(local, 8 << 30)
+    al = aim.Aligner(local, int(args.workspace_gb * (1 << 30)))
     out = {"scores": torch.empty(n_pairs, dtype=torch.int32, device=dev),
            "flags": torch.empty(n_pairs, dtype=torch.uint8, device=dev),
            "lens": torch.empty(n_pairs, dtype=torch.int32, device=dev),
