@@ -2,10 +2,14 @@
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
-A step aligns one whole batch: 2-bit packing of the ASCII pairs, the
-alignment kernel (threshold early exit, traceback, CIGAR and result writes),
-all through the C ABI (aim_align_batch_ascii) on inputs already in device
-memory.  `e2e` repeats the step with the inputs in pinned host memory and
+A step aligns one whole batch on inputs already in device memory.  The
+default workload (4M pairs, reads 100-1000 bp, 1-10 % edits, thresholds at
+10 % of length) runs the batched form: one CUDA-graph replay of 2-bit packing,
+device-side bucketing and one persistent WFA launch over the buckets with
+autotuned lanes per pair (aim_batch_run); the plain form (one
+aim_align_batch_ascii launch per read-length group) is timed beside it on the
+same pairs and must give identical results.  The other workloads run one
+aim_align_batch_ascii call per step.  `e2e` repeats the step with the inputs in pinned host memory and
 the host<->device copies inside the timed region.  Multi-GPU (torchrun): every
 rank aligns its own slice of the pair stream (weak scaling, no collective on
 the data path); timing is bracketed by barriers and the slowest rank counts.
@@ -46,9 +50,9 @@ INT32_LANES_PER_SM = 128
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="wfa_150bp", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="wfa_uneven", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count (0: as defined)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -87,6 +91,7 @@ def config_of(name, w, n_pairs, algo):
                                                           "gap_open": w.penalties[2], "gap_extend": w.penalties[3]},
          "max_edits": w.max_edits if w.max_edits is not None else f"ceil({w.max_edits_frac}*read_len)",
          "band": w.band if algo != "wfa" or name == "wfa_250bp" else -1,
+         "plain_form": "one launch per read-length group (8 log-spaced groups)" if name == "wfa_uneven" else None,
          "input": "ASCII pairs, 2-bit packed on device inside the step",
          "l2": "inputs larger than L2 (no flush needed)"}
     return c
@@ -214,6 +219,29 @@ def cpu_baseline(w, algo):
 
 # ---------------------------------------------------------------- our arm
 
+def _dist_max(x, dev, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def length_groups(p, edges=(100, 133, 178, 237, 316, 422, 562, 750, 1001)):
+    """Plain form: pairs grouped by read length (log-spaced edges), one launch per group."""
+    out = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        idx = np.nonzero((p.read_len >= lo) & (p.read_len < hi))[0]
+        if len(idx):
+            out.append(idx)
+    rest = np.setdiff1d(np.arange(len(p)), np.concatenate(out) if out else np.zeros(0, np.int64))
+    if len(rest):
+        out.append(rest)
+    return out
+
+
 def run_ours(args, w, algo):
     import torch
     import __graft_entry__
@@ -225,6 +253,7 @@ def run_ours(args, w, algo):
     import paper_2208_01243_gb300 as aim
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    batched = args.workload == "wfa_uneven"
 
     n_pairs = args.pairs or w.pairs
     p = gen.generate(w, n_pairs, first=rank * n_pairs)     # each rank: its own slice of the pair stream
@@ -248,18 +277,31 @@ def run_ours(args, w, algo):
            "lens": torch.empty(n_pairs, dtype=torch.int32, device=dev),
            "cigars": torch.empty(int(coff[-1]), dtype=torch.int32, device=dev)}
 
-    def step(src):
-        aim.aim_align_batch_ascii(al.ctx, src["reads"], src["targets"], src["ro"], src["to"], src["rl"], src["tl"],
-                                  max_len, algo, pen, max_edits, src.get("pp"), out["scores"], out["cigars"], coff_d,
-                                  out["lens"], out["flags"])
-
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
+    plan = None
+    if batched:
+        plan = aim.aim_batch_plan(al.ctx, d["reads"], d["targets"], d["ro"], d["to"], d["rl"], d["tl"], max_len, pen,
+                                  max_edits, d.get("pp"), out["scores"], out["cigars"], coff_d, out["lens"],
+                                  out["flags"], scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=True)
+        groups, counts = aim.aim_batch_info(plan)
+
+        def step(src=None):
+            aim.aim_batch_run(plan)
+        launches_per_step = 7          # 2 pack, bucket count/scan/scatter, alignment (+1 memset node)
+    else:
+        def step(src=None):
+            src = src or d
+            aim.aim_align_batch_ascii(al.ctx, src["reads"], src["targets"], src["ro"], src["to"], src["rl"], src["tl"],
+                                      max_len, algo, pen, max_edits, src.get("pp"), out["scores"], out["cigars"],
+                                      coff_d, out["lens"], out["flags"])
+        launches_per_step = 3          # 2 pack, alignment
+
     for _ in range(args.warmup):
-        step(d)
+        step()
     torch.cuda.synchronize()
 
     stream = torch.cuda.current_stream()
@@ -272,30 +314,77 @@ def run_ours(args, w, algo):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for _ in range(args.steps):
-        step(d)
+        step()
     ev1.record(stream)
     torch.cuda.synchronize(); barrier(); torch.cuda.synchronize()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = _dist_max(ev0.elapsed_time(ev1) / args.steps, dev, world)
     align_ms, align_n = aim.aim_timing_read(al.ctx, 1)
     pack_ms, pack_n = aim.aim_timing_read(al.ctx, 0)
     aim.aim_timing_enable(al.ctx, False)
     stats = aim.aim_stats_read(al.ctx)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     value = world * n_pairs / (ms / 1e3)
+    res_scores = out["scores"].cpu().numpy().copy()
+    res_flags = out["flags"].cpu().numpy().copy()
+    res_lens = out["lens"].cpu().numpy().copy()
+
+    # ---- plain form on the same pairs: one launch per read-length group
+    plain = None
+    if batched:
+        grp = length_groups(p)
+        gd = []
+        for idx in grp:
+            sub = {k: host[k][idx] for k in ("ro", "to", "rl", "tl")}
+            gcap = cap[idx]
+            goff = np.zeros(len(idx) + 1, np.int64); goff[1:] = np.cumsum(gcap)
+            t = dict(zip(("ro", "to", "rl", "tl"), aim.upload(*sub.values(), device=local)))
+            t["pp"] = aim.upload(host["pp"][idx], device=local)[0]
+            t["coff"] = aim.upload(goff, device=local)[0]
+            t["ml"] = int(max(p.read_len[idx].max(), p.target_len[idx].max()))
+            t["me"] = int(host["pp"][idx].max())
+            t["out"] = {"scores": torch.empty(len(idx), dtype=torch.int32, device=dev),
+                        "flags": torch.empty(len(idx), dtype=torch.uint8, device=dev),
+                        "lens": torch.empty(len(idx), dtype=torch.int32, device=dev),
+                        "cigars": torch.empty(int(goff[-1]), dtype=torch.int32, device=dev)}
+            gd.append(t)
+
+        def plain_step():
+            for t in gd:
+                o = t["out"]
+                aim.aim_align_batch_ascii(al.ctx, d["reads"], d["targets"], t["ro"], t["to"], t["rl"], t["tl"],
+                                          t["ml"], "wfa", pen, t["me"], t["pp"], o["scores"], o["cigars"], t["coff"],
+                                          o["lens"], o["flags"])
+        for _ in range(args.warmup):
+            plain_step()
+        torch.cuda.synchronize(); barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(args.steps):
+            plain_step()
+        p1.record(stream)
+        torch.cuda.synchronize(); barrier()
+        pms = _dist_max(p0.elapsed_time(p1) / args.steps, dev, world)
+        same = True
+        for idx, t in zip(grp, gd):
+            same &= bool(np.array_equal(t["out"]["scores"].cpu().numpy(), res_scores[idx]))
+            same &= bool(np.array_equal(t["out"]["flags"].cpu().numpy(), res_flags[idx]))
+            same &= bool(np.array_equal(t["out"]["lens"].cpu().numpy(), res_lens[idx]))
+        plain = {"value": world * n_pairs / (pms / 1e3), "unit": "alignments/s", "ms_per_step": pms,
+                 "launches_per_step": len(gd) * 3, "length_groups": len(gd), "results_identical": same,
+                 "batched_over_plain": pms / ms,
+                 "batched_lanes_per_bucket": {str(k): g for k, (g, c) in enumerate(zip(groups, counts)) if c},
+                 "batched_pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c}}
+        del gd
 
     # ---- end to end through the same call: pinned host inputs in, results out, copies timed
     hp = {k: torch.from_numpy(np.ascontiguousarray(v).view(
         {np.dtype(np.uint64): np.int64, np.dtype(np.uint32): np.int32}.get(np.asarray(v).dtype, np.asarray(v).dtype)))
         .pin_memory() for k, v in host.items()}
-    dd = {k: torch.empty_like(v, device=dev) for k, v in hp.items()}
     ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h2d = sum(v.numel() * v.element_size() for v in hp.values())
     d2h = sum(v.numel() * v.element_size() for v in ho.values())
+    # the batched plan is bound to the device buffers d: the e2e step refills them from pinned host memory
+    dd = d if batched else {k: torch.empty_like(v, device=dev) for k, v in hp.items()}
 
     def e2e_step():
         for k in hp:
@@ -313,16 +402,12 @@ def run_ours(args, w, algo):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize(); barrier()
-    e2e_ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    # the e2e results must equal the device-resident ones
-    assert torch.equal(ho["scores"], out["scores"].cpu())
+    e2e_ms = _dist_max(e0.elapsed_time(e1) / args.steps, dev, world)
+    assert np.array_equal(ho["scores"].numpy(), res_scores), "e2e results differ from the device-resident run"
 
     if rank != 0:
+        if plan is not None:
+            aim.aim_batch_destroy(plan)
         al.close()
         return 0
 
@@ -334,42 +419,49 @@ def run_ours(args, w, algo):
     launches = max(align_n, 1)
     if algo == "wfa":
         ops = stats["wf_entries"] * OPS_WF_ENTRY + stats["extend_windows"] * OPS_EXT_WINDOW
-        kernel = "wfa_kernel"; src_file = "wfa.cu"
+        kernel = "wfa_kernel"
     else:
         ops = stats["dp_cells"] * (OPS_UNIT_CELL if algo == "edit" else OPS_GOTOH_CELL)
-        kernel = "dp_kernel"; src_file = "dp_banded.cu"
+        kernel = "dp_kernel"
     ops_per_launch = ops / launches
     kern_s = align_ms / launches / 1e3
     achieved = ops_per_launch / kern_s / 1e12
     tr = traffic_record(kernel, w.name)
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_ops / 1e12, "unit": "Tops/s",
             "frac": achieved / (peak_ops / 1e12), "traffic": (tr["dram_bytes_per_launch"] if tr else None),
-            "kernel": kernel, "kernel_ms": kern_s * 1e3, "ops_per_launch": ops_per_launch,
+            "kernel": kernel, "kernel_ms": kern_s * 1e3, "kernel_launches_timed": align_n,
+            "ops_per_launch": ops_per_launch,
             "peak_note": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz "
-                         "(derived from unit counts and the max SM clock)",
-            "work": {k: v // launches for k, v in stats.items()},
-            "pack_ms_per_launch": pack_ms / max(pack_n, 1)}
-    # input ASCII + offsets + lengths, 2-bit words written and read back, results and the CIGAR runs written
-    packed_words = int(((p.read_len.astype(np.int64) + 31) // 32).sum() + ((p.target_len.astype(np.int64) + 31) // 32).sum())
+                         "(derived from unit counts and the max SM clock; no measured int32 peak exists)",
+            "work_per_launch": {k: v // launches for k, v in stats.items()},
+            "pack_ms_per_launch": pack_ms / max(pack_n, 1) if pack_n else None}
+    packed_words = int(((p.read_len.astype(np.int64) + 31) // 32).sum()
+                       + ((p.target_len.astype(np.int64) + 31) // 32).sum())
     hbm_bytes = (int(p.read_len.sum()) + int(p.target_len.sum()) + n_pairs * 2 * (8 + 4) + 2 * 8 * packed_words
-                 + n_pairs * (4 + 1 + 4 + 8) + 4 * int(out["lens"].cpu().numpy().astype(np.int64).sum()))
-    roof["hbm_note"] = {"algorithmic_bytes_per_step": hbm_bytes,
-                        "achieved_gbs": hbm_bytes / (ms / 1e3) / 1e9, "peak_gbs": peaks.get("hbm_gbs")}
+                 + n_pairs * (4 + 1 + 4 + 8) + 4 * int(res_lens.astype(np.int64).sum()))
+    roof["hbm_note"] = {"algorithmic_bytes_per_step": hbm_bytes, "achieved_gbs": hbm_bytes / (ms / 1e3) / 1e9,
+                        "peak_gbs": peaks.get("hbm_gbs"), "peak_source": "measured (MEASURED_PEAKS.json)"}
 
     line = {"metric": "alignments/s", "value": value, "unit": "alignments/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": config_of(args.workload, w, n_pairs, algo),
+            "form": "batched: bucketed queues + autotuned lanes per pair + CUDA graph replay" if batched
+                    else "plain: one aim_align_batch_ascii call per step",
             "cells_per_s": (stats["wf_entries"] if algo == "wfa" else stats["dp_cells"]) / launches / (ms / 1e3),
-            "rejected_frac": float((out["flags"].cpu().numpy() & 1).mean()),
+            "rejected_frac": float((res_flags & 1).mean()),
             "roofline": roof,
             "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
-            "gpu_launches": args.steps * 3,
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clk}
+    if plain is not None:
+        line["plain"] = plain
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, algo)
     print(json.dumps(line))
+    if plan is not None:
+        aim.aim_batch_destroy(plan)
     al.close()
     return 0
 

@@ -169,6 +169,50 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
                           aim_stream_t stream);
 
 /*
+ * Batched form (wavefront algorithm): pairs of uneven length and error rate
+ * in one persistent launch.  The batch is planned once and then replayed:
+ *   - packing, length/threshold bucketing of the pairs (on the device: a
+ *     histogram, a scan and a scatter into an order array, heaviest work class
+ *     first) and one persistent alignment launch that drains the buckets in
+ *     that order are recorded as one CUDA graph;
+ *   - with `autotune`, the lanes per pair of every non-empty bucket are chosen by
+ *     timed trial launches on up to 16,384 of its pairs (each choice cached in
+ *     the context per costs, band and bucket); otherwise from the bucket's
+ *     width class or an earlier cached choice.
+ * Arguments are those of aim_align_batch_ascii (the same buffers are bound to
+ * the plan: every aim_batch_run aligns their current contents, which may
+ * change between runs as long as the shapes and bounds still hold).
+ *   scratch_bytes  device scratch the plan may allocate for wavefronts (0: the
+ *                  context's workspace size)
+ * aim_batch_plan synchronises the device, allocates the plan's own device
+ * memory (packed copies, bucket arrays, order, scratch) and launches trial
+ * runs; aim_batch_run is asynchronous on `stream` (one graph launch).
+ * Results are bit-identical to aim_align_batch_ascii with AIM_ALGO_WFA_AFFINE.
+ * One plan must not run concurrently with itself.
+ */
+typedef struct aim_batch aim_batch;
+AIM_API int aim_batch_plan(aim_ctx *ctx, const uint8_t *reads, const uint8_t *targets,
+                           const uint64_t *read_char_offsets, const uint64_t *target_char_offsets,
+                           const uint32_t *read_lengths, const uint32_t *target_lengths, uint32_t num_pairs,
+                           uint32_t max_length, const aim_penalties_t *pen, int32_t max_edits,
+                           const int32_t *max_edits_per_pair, int32_t *out_scores, uint32_t *out_cigars,
+                           const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
+                           size_t scratch_bytes, int autotune, aim_batch **out);
+AIM_API int aim_batch_run(aim_batch *batch, aim_stream_t stream);
+/* Per bucket (32): lanes per pair in use and pairs seen at planning; returns the bucket count. */
+AIM_API int aim_batch_info(aim_batch *batch, int *groups /* host[32] */, uint32_t *counts /* host[32] */);
+AIM_API int aim_batch_destroy(aim_batch *batch);
+
+/*
+ * Lanes that cooperate on one pair in the wavefront kernel: 1, 2, 4, 8, 16 or 32
+ * (a warp then aligns 32/lanes pairs in lockstep), or 0 to let the library
+ * choose from the widest wavefront the call's lengths and threshold allow.
+ * Results do not depend on it; throughput does.  A choice whose scratch does
+ * not fit the workspace is widened until it fits.
+ */
+AIM_API int aim_set_wfa_group(aim_ctx *ctx, int lanes);
+
+/*
  * Work counters, accumulated by the kernels of every call since the last
  * reset (the figures behind cells/s and the roofline report):
  *   [0] wavefront entries computed by the WFA (each holds M~, I~, D~)

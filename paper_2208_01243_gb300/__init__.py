@@ -57,6 +57,12 @@ def _lib():
         lib.aim_align_batch_ascii.argtypes = lib.aim_align_batch.argtypes
         lib.aim_wfa_align_static.argtypes = [p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p,
                                              p, p, p, p, p]
+        lib.aim_set_wfa_group.argtypes = [p, ctypes.c_int]
+        lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
+                                       p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
+        lib.aim_batch_run.argtypes = [p, p]
+        lib.aim_batch_info.argtypes = [p, p, p]
+        lib.aim_batch_destroy.argtypes = [p]
         lib.aim_stats_reset.argtypes = [p, p]
         lib.aim_stats_read.argtypes = [p, p]
         lib.aim_timing_enable.argtypes = [p, ctypes.c_int]
@@ -137,6 +143,47 @@ def aim_wfa_align_static(packed_reads, packed_targets, read_offsets, target_offs
                                        _ptr(read_lengths, u32, "read_lengths"),
                                        _ptr(target_lengths, u32, "target_lengths"), *args),
            "aim_wfa_align_static")
+
+
+def aim_batch_plan(ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths, target_lengths,
+                   max_length, pen, max_edits, max_edits_per_pair, out_scores, out_cigars, cigar_offsets,
+                   out_cigar_lens, out_flags, scratch_bytes: int = 0, autotune: bool = True):
+    """Plan a batched WFA run over the bound buffers (see aim.h); returns the plan handle."""
+    u8, u64, u32 = torch.uint8, torch.uint64, torch.uint32
+    n = int(read_lengths.numel())
+    args = _align_args(n, max_length, AIM_ALGO_WFA_AFFINE, pen, max_edits, max_edits_per_pair, out_scores,
+                       out_cigars, cigar_offsets, out_cigar_lens, out_flags, None)
+    del args[2]          # no algorithm argument
+    del args[-1]         # no stream
+    plan = ctypes.c_void_p()
+    _check(_lib().aim_batch_plan(ctx, _ptr(reads, u8, "reads"), _ptr(targets, u8, "targets"),
+                                 _ptr(read_char_offsets, u64, "read_char_offsets"),
+                                 _ptr(target_char_offsets, u64, "target_char_offsets"),
+                                 _ptr(read_lengths, u32, "read_lengths"), _ptr(target_lengths, u32, "target_lengths"),
+                                 *args, ctypes.c_size_t(scratch_bytes), int(bool(autotune)), ctypes.byref(plan)),
+           "aim_batch_plan")
+    return plan
+
+
+def aim_batch_run(batch, stream=None) -> None:
+    _check(_lib().aim_batch_run(batch, _stream(stream)), "aim_batch_run")
+
+
+def aim_batch_info(batch):
+    """(lanes per pair, pairs at planning) for each of the 32 buckets."""
+    g = (ctypes.c_int * 32)(); c = (ctypes.c_uint32 * 32)()
+    nb = _lib().aim_batch_info(batch, g, c)
+    if nb < 0:
+        raise AimError(nb, "aim_batch_info")
+    return list(g)[:nb], list(c)[:nb]
+
+
+def aim_batch_destroy(batch) -> None:
+    _check(_lib().aim_batch_destroy(batch), "aim_batch_destroy")
+
+
+def aim_set_wfa_group(ctx, lanes: int) -> None:
+    _check(_lib().aim_set_wfa_group(ctx, int(lanes)), "aim_set_wfa_group")
 
 
 def aim_stats_reset(ctx, stream=None) -> None:

@@ -19,6 +19,8 @@ LIB = os.path.join(OUT_DIR, "libaim.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
               "-I", os.path.join(ROOT, "include")]
+# extra nvcc flags for tuning builds, e.g. AIM_NVCC_FLAGS="-DAIM_WFA_MIN_BLOCKS=3"
+EXTRA = os.environ.get("AIM_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:
@@ -52,7 +54,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     def compile_one(src: str) -> str:
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *EXTRA, *extra, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")

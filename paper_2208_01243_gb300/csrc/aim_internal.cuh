@@ -108,19 +108,52 @@ cudaError_t launch_dp(const DpPlan& plan, const Costs& c, const PairsView& P, co
                       int64_t max_limit, uint8_t* scratch, size_t scratch_bytes, uint32_t* counter,
                       int num_sms, cudaStream_t st, int* warps_used);
 
+constexpr int kMaxBuckets = 32;
+
 struct WfaPlan {
     int g;               // gcd of the costs; scores run in units of g
     int x, oe, e;        // scaled mismatch, open+extend, extend
     int64_t smax;        // largest scaled score any pair may reach
     int band;            // < 0: none
-    size_t slot_bytes;   // per-warp scratch
-    size_t hist_elems;   // int16 entries of wavefront history per warp
-    int runs_cap;        // CIGAR runs staged per warp
+    size_t hist_elems;   // int16 entries of wavefront history per pair (worst case)
+    int runs_cap;        // CIGAR runs staged per pair
+    size_t meta_bytes;   // per-score (lo, hi, base, width) records, int4 each
+    size_t runs_bytes;   // run staging
+    size_t group_bytes;  // scratch of one pair in flight: meta + runs + history
 };
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
-cudaError_t launch_wfa(const WfaPlan& plan, const Costs& c, const PairsView& P, const LimitView& L,
-                       const OutView& O, uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms,
-                       cudaStream_t st, int* warps_used);
+size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax);
+// lanes per pair suited to the widest wavefront the plan allows (4, 8, 16 or 32; 1 and 2 are valid too)
+int wfa_default_group(const WfaPlan& p, uint32_t max_length);
+
+struct WfaArgs {
+    int X, OE, E, g;
+    int64_t smax;
+    int band;
+    PairsView P;
+    LimitView L;
+    OutView O;
+    uint8_t* scratch;
+    size_t warp_bytes;         // scratch per warp; a warp of G-lane groups gives each group warp_bytes / (32/G)
+    size_t meta_bytes, runs_bytes;
+    uint32_t runs_cap;
+    uint32_t nwarps;
+    const uint32_t* order;     // pair index at each queue position, or null (identity)
+    const uint32_t* bounds;    // bucket b covers queue positions [bounds[b], bounds[b+1]); null: one bucket of all
+    uint32_t* counters;        // one claim counter per bucket, zero at launch
+    int nbuckets;
+    int8_t group[kMaxBuckets]; // lanes per pair of each bucket
+};
+
+// one launch over buckets (longest-first order given by the caller)
+cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const LimitView& L, const OutView& O,
+                               const uint32_t* order, const uint32_t* bounds, const int* groups, int nbuckets,
+                               size_t warp_bytes, uint8_t* scratch, size_t scratch_bytes, uint32_t* counters,
+                               int num_sms, cudaStream_t st, int* warps_used);
+// one launch over all pairs in index order with `group` lanes per pair
+cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const LimitView& L, const OutView& O,
+                       uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
+                       int* warps_used);
 
 }  // namespace aim
 
@@ -189,5 +222,53 @@ __device__ __forceinline__ void warp_stat_add(unsigned long long* stats, int slo
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     if (stats && lane == 0 && v) atomicAdd(stats + slot, v);
 }
+
+}  // namespace aim
+
+// ---- context (shared by the C ABI translation units) ----
+
+namespace aim {
+constexpr int kTimedLaunches = 4096;
+constexpr size_t kHeaderBytes = 256;   // launch counter and work counters at the start of the workspace
+constexpr size_t kStatsOffset = 64;    // four uint64 work counters
+struct KernelTimes;
+}  // namespace aim
+
+struct aim_ctx {
+    int device;
+    int num_sms;
+    uint8_t* ws;                  // workspace (device): [launch counter | stats | ...][scratch]
+    size_t ws_bytes;
+    bool timing;
+    aim::KernelTimes* times[2];   // 0: packer, 1: alignment kernels; created on first enable
+    int wfa_group;                // lanes per pair for the WFA; 0: chosen from the plan
+    void* tune_cache;             // autotuner choices (owned; see batch.cu)
+};
+
+namespace aim {
+
+struct Resolved {
+    Costs costs;
+    LimitView lim;
+    int64_t max_limit;   // largest limit of any pair (kUnbounded: none)
+};
+
+int cuda_status(cudaError_t e);
+unsigned long long* stats_of(aim_ctx* ctx);
+int time_begin(aim_ctx* ctx, int kind, cudaStream_t st);
+void time_end(aim_ctx* ctx, int kind, int slot, cudaStream_t st);
+int resolve(int algo, const aim_penalties_t* pen, int32_t max_edits, const int32_t* per_pair, Resolved* r);
+// timing ring access for launches recorded inside a graph: claim a slot (-1: timing off or ring full)
+int time_slot(aim_ctx* ctx, int kind);
+cudaEvent_t timing_start_event(aim_ctx* ctx, int kind, int slot);
+cudaEvent_t timing_stop_event(aim_ctx* ctx, int kind, int slot);
+void free_tune_cache(void* cache);
+
+struct DeviceGuardImpl {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuardImpl(int dev);
+    ~DeviceGuardImpl();
+};
 
 }  // namespace aim

@@ -7,37 +7,26 @@
 
 #include "aim_internal.cuh"
 
-namespace {
-constexpr int kTimedLaunches = 4096;
+namespace aim {
 struct KernelTimes {
     cudaEvent_t start[kTimedLaunches];
     cudaEvent_t stop[kTimedLaunches];
     int recorded;     // launches with events
     int launches;     // all launches since the last read
 };
-}  // namespace
-
-struct aim_ctx {
-    int device;
-    int num_sms;
-    uint8_t* ws;          // workspace (device): [launch counter | stats | ...][scratch]
-    size_t ws_bytes;
-    bool timing;
-    KernelTimes* times[2];   // 0: packer, 1: alignment kernels; created on first enable
-};
+}  // namespace aim
 
 namespace {
-
 thread_local int g_last_cuda_error = 0;
+}  // namespace
+
+namespace aim {
 
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return AIM_OK;
     g_last_cuda_error = (int)e;
     return AIM_ERR_CUDA;
 }
-
-constexpr size_t kHeaderBytes = 256;   // launch counter and friends at the start of the workspace
-constexpr size_t kStatsOffset = 64;    // four uint64 work counters
 
 unsigned long long* stats_of(aim_ctx* ctx) { return reinterpret_cast<unsigned long long*>(ctx->ws + kStatsOffset); }
 
@@ -59,30 +48,51 @@ void time_end(aim_ctx* ctx, int kind, int slot, cudaStream_t st) {
     t->recorded = slot + 1;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-    }
-};
+int time_slot(aim_ctx* ctx, int kind) {
+    if (!ctx->timing) return -1;
+    KernelTimes* t = ctx->times[kind];
+    const int i = t->recorded;
+    ++t->launches;
+    if (i >= kTimedLaunches) return -1;
+    t->recorded = i + 1;
+    return i;
+}
+
+cudaEvent_t timing_start_event(aim_ctx* ctx, int kind, int slot) { return ctx->times[kind]->start[slot]; }
+cudaEvent_t timing_stop_event(aim_ctx* ctx, int kind, int slot) { return ctx->times[kind]->stop[slot]; }
+
+}  // namespace aim
+
+using aim::cuda_status;
+using aim::kHeaderBytes;
+using aim::KernelTimes;
+using aim::kTimedLaunches;
+using aim::stats_of;
+using aim::time_begin;
+using aim::time_end;
+
+namespace aim {
+DeviceGuardImpl::DeviceGuardImpl(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+}
+DeviceGuardImpl::~DeviceGuardImpl() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+}  // namespace aim
+
+namespace {
+using DeviceGuard = aim::DeviceGuardImpl;
 
 bool penalties_ok(const aim_penalties_t* p) {
     return p && p->match == 0 && p->mismatch >= 1 && p->gap_open >= 0 && p->gap_extend >= 1 &&
            p->mismatch <= (1 << 20) && p->gap_open <= (1 << 20) && p->gap_extend <= (1 << 20);
 }
 
-struct Resolved {
-    aim::Costs costs;
-    aim::LimitView lim;
-    int64_t max_limit;   // largest limit of any pair (aim::kUnbounded: none)
-};
+}  // namespace
 
+namespace aim {
 // The threshold rule of aim.h: max_score overrides; else max_edits (x unit cost, or x max(x, o+e)).
 int resolve(int algo, const aim_penalties_t* pen, int32_t max_edits, const int32_t* per_pair, Resolved* r) {
     const bool unit = algo == AIM_ALGO_EDIT_NW;
@@ -107,6 +117,12 @@ int resolve(int algo, const aim_penalties_t* pen, int32_t max_edits, const int32
     r->max_limit = r->lim.limit;
     return AIM_OK;
 }
+}  // namespace aim
+
+using aim::Resolved;
+using aim::resolve;
+
+namespace {
 
 int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_penalties_t* pen, int32_t max_edits,
                  const int32_t* per_pair, const aim::OutView& O, cudaStream_t st, uint8_t* scratch,
@@ -122,9 +138,11 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
     if (algo == AIM_ALGO_WFA_AFFINE) {
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
         const aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
-        if (plan.slot_bytes > scratch_bytes) return AIM_ERR_NOMEM;
+        int group = ctx->wfa_group ? ctx->wfa_group : aim::wfa_default_group(plan, P.max_length);
+        while (group < 32 && (size_t)(32 / group) * plan.group_bytes > scratch_bytes) group *= 2;
+        if ((size_t)(32 / group) * plan.group_bytes > scratch_bytes) return AIM_ERR_NOMEM;
         slot = time_begin(ctx, 1, st);
-        err = aim::launch_wfa(plan, r.costs, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
+        err = aim::launch_wfa(plan, group, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
     } else {
         const bool unit = algo == AIM_ALGO_EDIT_NW;
         int64_t b = P.max_length;
@@ -203,6 +221,8 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     if (e != cudaSuccess) { cudaFree(c->ws); delete c; return cuda_status(e); }
     c->timing = false;
     c->times[0] = c->times[1] = nullptr;
+    c->wfa_group = 0;
+    c->tune_cache = nullptr;
     *out = c;
     return AIM_OK;
 }
@@ -217,8 +237,16 @@ int aim_destroy(aim_ctx* ctx) {
         for (int i = 0; i < kTimedLaunches; ++i) { cudaEventDestroy(t->start[i]); cudaEventDestroy(t->stop[i]); }
         delete t;
     }
+    aim::free_tune_cache(ctx->tune_cache);
     delete ctx;
     return cuda_status(e);
+}
+
+int aim_set_wfa_group(aim_ctx* ctx, int lanes) {
+    if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+        return AIM_ERR_ARG;
+    ctx->wfa_group = lanes;
+    return AIM_OK;
 }
 
 int aim_stats_reset(aim_ctx* ctx, aim_stream_t stream) {

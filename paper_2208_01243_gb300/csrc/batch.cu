@@ -1,0 +1,414 @@
+// Batched form of the wavefront aligner: pairs of uneven length and error
+// rate go into one persistent launch through length-bucketed work queues,
+// with the lanes per pair of every bucket chosen by an autotuner and the
+// whole run (packing, bucketing, alignment) replayed as a CUDA graph.
+//
+// Buckets.  Each pair's work is bounded by its threshold: with S = limit/g
+// scaled score steps, no wavefront is wider than W = min(2 S/E + 3, n+m+1,
+// 2 band + 1) diagonals, and the whole pair computes at most C = (S+1) W
+// wavefront entries.  A pair's bucket combines a work class (floor(log2(C+1))/3,
+// 8 classes) with a width class (W <= 64, 128, 256, more); buckets are
+// numbered heaviest work class first, so warps drain the longest pairs first
+// and the tail of the launch holds the shortest ones.  Bucketing runs on the
+// device (a block-aggregated histogram, a one-warp scan, a block-aggregated
+// scatter into an order array), so a replay needs no host round trip.
+//
+// Autotuner.  For every non-empty bucket, timed trial launches on a sample of
+// up to 4,096 of its pairs try the group sizes that suit its width class (so
+// that no lane walks more than about 64 diagonals per score step) and keep
+// the fastest; choices are cached in the context per (costs, band, bucket).
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "aim_internal.cuh"
+
+namespace aim {
+namespace {
+
+constexpr int kBuckets = 32;
+constexpr int kWidthClasses = 4;
+constexpr int kWorkClasses = 8;
+constexpr int kCandidates[6] = {1, 2, 4, 8, 16, 32};
+
+struct BucketParams {
+    int g, E, band;
+    int64_t smax;
+};
+
+__device__ __forceinline__ int bucket_of(const PairsView& P, const LimitView& L, const BucketParams& bp, uint32_t i) {
+    const int64_t n = P.read_len[i], m = P.target_len[i];
+    const int64_t lim = pair_limit(L, i);
+    int64_t S = lim < 0 ? 0 : lim / bp.g;
+    if (S > bp.smax) S = bp.smax;
+    int64_t W = 2 * (S / bp.E) + 3;
+    W = min(W, n + m + 1);
+    if (bp.band >= 0) W = min(W, 2 * (int64_t)bp.band + 1);
+    const int64_t C = (S + 1) * W;
+    const int wc = W <= 64 ? 0 : W <= 128 ? 1 : W <= 256 ? 2 : 3;
+    int kc = (63 - __clzll((long long)(C + 1))) / 3;
+    if (kc > kWorkClasses - 1) kc = kWorkClasses - 1;
+    return (kWorkClasses - 1 - kc) * kWidthClasses + (kWidthClasses - 1 - wc);
+}
+
+__global__ void __launch_bounds__(256) bucket_count_kernel(PairsView P, LimitView L, BucketParams bp,
+                                                           uint32_t* counts) {
+    __shared__ uint32_t h[kBuckets];
+    if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.num_pairs; i += gridDim.x * blockDim.x)
+        atomicAdd(&h[bucket_of(P, L, bp, i)], 1u);
+    __syncthreads();
+    if (threadIdx.x < kBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
+}
+
+// one warp: bounds[b] = first queue position of bucket b, bounds[32] = total; clears the fill and claim counters
+__global__ void bucket_scan_kernel(const uint32_t* counts, uint32_t* bounds, uint32_t* fill, uint32_t* claims) {
+    const uint32_t lane = threadIdx.x;
+    const uint32_t c = counts[lane];
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if ((int)lane >= o) incl += t;
+    }
+    bounds[lane] = incl - c;
+    if (lane == 31) bounds[32] = incl;
+    fill[lane] = 0;
+    claims[lane] = 0;
+}
+
+__global__ void __launch_bounds__(256) bucket_scatter_kernel(PairsView P, LimitView L, BucketParams bp,
+                                                             const uint32_t* bounds, uint32_t* fill,
+                                                             uint32_t* order) {
+    __shared__ uint32_t h[kBuckets], base[kBuckets];
+    for (uint32_t chunk = blockIdx.x * blockDim.x; chunk < P.num_pairs; chunk += gridDim.x * blockDim.x) {
+        if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
+        __syncthreads();
+        const uint32_t i = chunk + threadIdx.x;
+        int b = -1;
+        uint32_t r = 0;
+        if (i < P.num_pairs) {
+            b = bucket_of(P, L, bp, i);
+            r = atomicAdd(&h[b], 1u);
+        }
+        __syncthreads();
+        if (threadIdx.x < kBuckets && h[threadIdx.x])
+            base[threadIdx.x] = bounds[threadIdx.x] + atomicAdd(&fill[threadIdx.x], h[threadIdx.x]);
+        __syncthreads();
+        if (b >= 0) order[base[b] + r] = i;
+        __syncthreads();
+    }
+}
+
+// scratch one pair of bucket b can need (bounds of its classes, capped by the plan's worst case)
+// (every wavefront of a pair in width class wc is at most 64/128/256 diagonals wide, and a
+// pair in work class kc computes fewer than 2^(3(kc+1)) entries per component)
+size_t bucket_group_bytes(const WfaPlan& plan, int b, uint32_t max_length) {
+    const int kc = kWorkClasses - 1 - b / kWidthClasses;
+    const int wc = kWidthClasses - 1 - b % kWidthClasses;
+    size_t hist = plan.hist_elems;
+    if (kc < kWorkClasses - 1) {
+        const size_t cmax = ((size_t)1 << (3 * (kc + 1))) - 1;
+        hist = std::min(hist, 3 * cmax + 3);
+    }
+    if (wc < kWidthClasses - 1) {
+        const size_t wmax = (size_t)64 << wc;
+        hist = std::min(hist, 3 * ((size_t)plan.smax + 1) * wmax + 3);
+    }
+    (void)max_length;
+    return align_up(plan.meta_bytes + plan.runs_bytes + hist * sizeof(int16_t), 16);
+}
+
+int default_group_for_bucket(int b) {
+    const int wc = kWidthClasses - 1 - b % kWidthClasses;
+    return wc == 0 ? 4 : wc == 1 ? 8 : wc == 2 ? 16 : 32;
+}
+
+}  // namespace
+}  // namespace aim
+
+struct aim_batch {
+    aim_ctx* ctx;
+    uint32_t num_pairs, max_length;
+    aim_penalties_t pen;
+    int32_t max_edits;
+    aim::Resolved r;
+    aim::WfaPlan plan;
+    aim::PairsView P;
+    aim::OutView O;
+    const uint8_t *reads, *targets;
+    const uint64_t *read_coff, *target_coff;
+    uint64_t stride;
+    // owned device memory
+    uint8_t* mem;
+    size_t mem_bytes;
+    uint64_t *pr, *pt;
+    uint8_t *br, *bt;
+    uint32_t *counts, *bounds, *fill, *claims, *trial_bounds, *order;
+    uint8_t* scratch;
+    size_t scratch_bytes, warp_bytes;
+    int groups[aim::kBuckets];
+    uint32_t host_counts[aim::kBuckets];
+    aim::BucketParams bp;
+    cudaStream_t stream;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    cudaGraphNode_t ev_start_node, ev_stop_node;
+    cudaEvent_t ev_start, ev_stop;   // captured placeholders
+    int warps;
+};
+
+namespace aim {
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int, int64_t>;   // x, o, e, band, bucket, smax
+std::map<TuneKey, int>& tune_cache(aim_ctx* ctx) {
+    if (!ctx->tune_cache) ctx->tune_cache = new std::map<TuneKey, int>();
+    return *static_cast<std::map<TuneKey, int>*>(ctx->tune_cache);
+}
+
+// packing and bucketing on `st`
+cudaError_t enqueue_prepare(aim_batch* b, cudaStream_t st) {
+    cudaError_t e = launch_pack(b->reads, b->read_coff, b->P.read_len, b->num_pairs, b->pr, nullptr, b->stride, b->br,
+                                st);
+    if (e != cudaSuccess) return e;
+    e = launch_pack(b->targets, b->target_coff, b->P.target_len, b->num_pairs, b->pt, nullptr, b->stride, b->bt, st);
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b->counts, 0, kBuckets * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((b->num_pairs + 255) / 256, (uint64_t)b->ctx->num_sms * 8);
+    bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->counts);
+    bucket_scan_kernel<<<1, 32, 0, st>>>(b->counts, b->bounds, b->fill, b->claims);
+    bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->bounds, b->fill, b->order);
+    return cudaGetLastError();
+}
+
+cudaError_t enqueue_align(aim_batch* b, cudaStream_t st, int* warps) {
+    return launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, b->groups, kBuckets, b->warp_bytes,
+                              b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, warps);
+}
+
+int autotune(aim_batch* b) {
+    cudaStream_t st = b->stream;
+    cudaEvent_t t0, t1;
+    if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) return AIM_ERR_CUDA;
+    uint32_t bounds[kBuckets + 1];
+    cudaError_t e = cudaMemcpy(bounds, b->bounds, sizeof(bounds), cudaMemcpyDeviceToHost);
+    const size_t min_warps = (size_t)b->ctx->num_sms * 8;
+    for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
+        const uint32_t count = b->host_counts[k];
+        if (!count) continue;
+        const uint32_t sample = std::min<uint32_t>(count, 4096);
+        const uint32_t tb[2] = {bounds[k], bounds[k] + sample};
+        float best = 1e30f;
+        int best_g = b->groups[k];
+        // lanes per pair worth trying for this width class: at most ~64 diagonals per lane and score step
+        const int wc = kWidthClasses - 1 - k % kWidthClasses;
+        const int gmin = wc == 0 ? 1 : wc == 1 ? 2 : wc == 2 ? 4 : 8;
+        const int gmax = wc == 0 ? 8 : wc == 1 ? 16 : 32;
+        for (int G : kCandidates) {
+            if (G < gmin || G > gmax) continue;
+            const size_t wb = (size_t)(32 / G) * bucket_group_bytes(b->plan, k, b->max_length);
+            if (wb * min_warps > b->scratch_bytes) continue;
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                e = cudaMemcpyAsync(b->trial_bounds, tb, sizeof(tb), cudaMemcpyHostToDevice, st);
+                if (e == cudaSuccess) e = cudaMemsetAsync(b->claims, 0, sizeof(uint32_t), st);
+                if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+                int w = 0;
+                if (e == cudaSuccess)
+                    e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->trial_bounds, &G, 1, wb,
+                                           b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, &w);
+                if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
+            }
+            if (e == cudaSuccess && ms < best) { best = ms; best_g = G; }
+        }
+        b->groups[k] = best_g;
+        tune_cache(b->ctx)[TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, b->pen.band, k, b->plan.smax)] = best_g;
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    return cuda_status(e);
+}
+
+void free_batch(aim_batch* b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->ev_stop) cudaEventDestroy(b->ev_stop);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->mem) cudaFree(b->mem);
+    delete b;
+}
+
+}  // namespace
+
+void free_tune_cache(void* cache) { delete static_cast<std::map<TuneKey, int>*>(cache); }
+
+}  // namespace aim
+
+extern "C" {
+
+int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, const uint64_t* read_char_offsets,
+                   const uint64_t* target_char_offsets, const uint32_t* read_lengths, const uint32_t* target_lengths,
+                   uint32_t num_pairs, uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits,
+                   const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
+                   const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
+                   int autotune, aim_batch** out) {
+    using namespace aim;
+    if (!out) return AIM_ERR_ARG;
+    *out = nullptr;
+    if (!ctx || !pen || pen->match != 0 || pen->mismatch < 1 || pen->gap_open < 0 || pen->gap_extend < 1)
+        return AIM_ERR_ARG;
+    if (num_pairs == 0 || !reads || !targets || !read_char_offsets || !target_char_offsets || !read_lengths ||
+        !target_lengths || !out_scores || !out_flags || ((out_cigars == nullptr) != (cigar_offsets == nullptr)))
+        return AIM_ERR_ARG;
+    if (max_length > kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
+    DeviceGuardImpl guard(ctx->device);
+    aim_batch* b = new (std::nothrow) aim_batch();
+    if (!b) return AIM_ERR_NOMEM;
+    std::memset(b, 0, sizeof(*b));
+    b->ctx = ctx;
+    b->num_pairs = num_pairs;
+    b->max_length = max_length;
+    b->pen = *pen;
+    b->max_edits = max_edits;
+    int rc = resolve(AIM_ALGO_WFA_AFFINE, pen, max_edits, max_edits_per_pair, &b->r);
+    if (rc) { free_batch(b); return rc; }
+    b->plan = plan_wfa(b->r.costs, pen->band, max_length, b->r.max_limit);
+    b->bp = BucketParams{b->plan.g, b->plan.e, pen->band, b->plan.smax};
+    b->reads = reads; b->targets = targets; b->read_coff = read_char_offsets; b->target_coff = target_char_offsets;
+    b->stride = ((uint64_t)max_length + 31) / 32;
+
+    // groups: cached choice, else the width-class default
+    for (int k = 0; k < kBuckets; ++k) {
+        b->groups[k] = default_group_for_bucket(k);
+        if (ctx->tune_cache) {
+            auto& c = tune_cache(ctx);
+            auto it = c.find(TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, pen->band, k, b->plan.smax));
+            if (it != c.end()) b->groups[k] = it->second;
+        }
+    }
+    // owned memory: packed sequences, flags, bucket arrays, order, scratch
+    const size_t seq_bytes = align_up((size_t)num_pairs * b->stride * 8, 256);
+    const size_t flag_bytes = align_up(num_pairs, 256);
+    const size_t small_bytes = align_up(5 * (kBuckets + 1) * sizeof(uint32_t), 256);
+    const size_t order_bytes = align_up((size_t)num_pairs * sizeof(uint32_t), 256);
+    b->scratch_bytes = scratch_bytes ? scratch_bytes : ctx->ws_bytes;
+    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + order_bytes + b->scratch_bytes;
+    cudaError_t e = cudaMalloc(&b->mem, b->mem_bytes);
+    if (e != cudaSuccess) { cudaGetLastError(); free_batch(b); return AIM_ERR_NOMEM; }
+    uint8_t* p = b->mem;
+    b->pr = reinterpret_cast<uint64_t*>(p); p += seq_bytes;
+    b->pt = reinterpret_cast<uint64_t*>(p); p += seq_bytes;
+    b->br = p; p += flag_bytes;
+    b->bt = p; p += flag_bytes;
+    uint32_t* sm = reinterpret_cast<uint32_t*>(p); p += small_bytes;
+    b->counts = sm; b->bounds = sm + (kBuckets + 1); b->fill = sm + 2 * (kBuckets + 1);
+    b->claims = sm + 3 * (kBuckets + 1); b->trial_bounds = sm + 4 * (kBuckets + 1);
+    b->order = reinterpret_cast<uint32_t*>(p); p += order_bytes;
+    b->scratch = p;
+    b->P = PairsView{b->pr, b->pt, nullptr, nullptr, read_lengths, target_lengths, b->br, b->bt, num_pairs, max_length};
+    b->P.stride = b->stride;
+    b->O = OutView{out_scores, out_cigars, cigar_offsets, out_cigar_lens, out_flags, stats_of(ctx)};
+    e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { free_batch(b); return cuda_status(e); }
+
+    // prepare once (synchronously) to see the bucket sizes, then tune
+    e = enqueue_prepare(b, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(b->host_counts, b->counts, sizeof(b->host_counts), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { free_batch(b); return cuda_status(e); }
+    if (autotune) {
+        rc = aim::autotune(b);
+        if (rc) { free_batch(b); return rc; }
+    }
+    // buckets empty at planning keep one pair per warp, so their worst case does not shrink the grid
+    for (int k = 0; k < kBuckets; ++k)
+        if (!b->host_counts[k]) b->groups[k] = 32;
+    // scratch per warp: the largest need over all buckets (a replay may see a different mix)
+    size_t wb = 0;
+    for (int k = 0; k < kBuckets; ++k)
+        wb = std::max(wb, (size_t)(32 / b->groups[k]) * bucket_group_bytes(b->plan, k, max_length));
+    b->warp_bytes = wb;
+    if (wb > b->scratch_bytes) { free_batch(b); return AIM_ERR_NOMEM; }
+
+    // record prepare + align as a graph; the two event records bracket the alignment kernel
+    if (cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_stop) != cudaSuccess) {
+        free_batch(b);
+        return AIM_ERR_CUDA;
+    }
+    e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t ce = enqueue_prepare(b, b->stream);
+        if (ce == cudaSuccess) ce = cudaEventRecordWithFlags(b->ev_start, b->stream, cudaEventRecordExternal);
+        if (ce == cudaSuccess) ce = enqueue_align(b, b->stream, &b->warps);
+        if (ce == cudaSuccess) ce = cudaEventRecordWithFlags(b->ev_stop, b->stream, cudaEventRecordExternal);
+        e = cudaStreamEndCapture(b->stream, &b->graph);
+        if (ce != cudaSuccess) e = ce;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e == cudaSuccess) {
+        size_t nn = 0;
+        e = cudaGraphGetNodes(b->graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (e == cudaSuccess) e = cudaGraphGetNodes(b->graph, nodes.data(), &nn);
+        for (size_t i = 0; i < nn && e == cudaSuccess; ++i) {
+            cudaGraphNodeType t;
+            e = cudaGraphNodeGetType(nodes[i], &t);
+            if (e != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+            cudaEvent_t ev;
+            e = cudaGraphEventRecordNodeGetEvent(nodes[i], &ev);
+            if (ev == b->ev_start) b->ev_start_node = nodes[i];
+            if (ev == b->ev_stop) b->ev_stop_node = nodes[i];
+        }
+    }
+    if (e != cudaSuccess || b->warps == 0) {
+        free_batch(b);
+        return e != cudaSuccess ? cuda_status(e) : AIM_ERR_NOMEM;
+    }
+    *out = b;
+    return AIM_OK;
+}
+
+int aim_batch_run(aim_batch* b, aim_stream_t stream) {
+    using namespace aim;
+    if (!b) return AIM_ERR_ARG;
+    DeviceGuardImpl guard(b->ctx->device);
+    cudaError_t e = cudaSuccess;
+    aim_ctx* ctx = b->ctx;
+    if (b->ev_start_node && b->ev_stop_node) {
+        const int slot = ctx->timing ? time_slot(ctx, 1) : -1;
+        cudaEvent_t s0 = slot >= 0 ? timing_start_event(ctx, 1, slot) : b->ev_start;
+        cudaEvent_t s1 = slot >= 0 ? timing_stop_event(ctx, 1, slot) : b->ev_stop;
+        e = cudaGraphExecEventRecordNodeSetEvent(b->exec, b->ev_start_node, s0);
+        if (e == cudaSuccess) e = cudaGraphExecEventRecordNodeSetEvent(b->exec, b->ev_stop_node, s1);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+    return cuda_status(e);
+}
+
+int aim_batch_info(aim_batch* b, int* groups, uint32_t* counts) {
+    if (!b || !groups || !counts) return AIM_ERR_ARG;
+    for (int k = 0; k < aim::kBuckets; ++k) { groups[k] = b->groups[k]; counts[k] = b->host_counts[k]; }
+    return aim::kBuckets;
+}
+
+int aim_batch_destroy(aim_batch* b) {
+    if (!b) return AIM_OK;
+    aim::DeviceGuardImpl guard(b->ctx->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    aim::free_batch(b);
+    return aim::cuda_status(e);
+}
+
+}  // extern "C"

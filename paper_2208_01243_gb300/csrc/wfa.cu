@@ -1,5 +1,7 @@
 // Gap-affine wavefront alignment (WFA, Section 2.4.4) with the canonical
-// traceback, one warp per pair.
+// traceback.  A group of G lanes (G = 1, 2, 4, 8, 16 or 32) aligns one pair; a warp
+// runs 32/G pairs in lockstep over the score loop, so the per-score work of
+// one pair is shared by G lanes and the warp-uniform bookkeeping by 32/G pairs.
 //
 // Scores run in units of g = gcd(x, o, e) (every path cost is a sum of x,
 // o+e and e, so every reachable score is a multiple of g): X = x/g,
@@ -10,16 +12,18 @@
 //   f0      = max(M~[s-X, k] + 1, I~[s,k], D~[s,k])     (each candidate dropped if
 //                                                        it leaves the matrix)
 //   M~[s,k] = f0 + LCP(P[f0-k..], T[f0..])              (extend along matches)
-// ("compute_next" then "extend"); the pair is done at the first s with
-// M~[s, m-n] == m, and rejected once s passes the threshold (early exit).
-// Lane j handles diagonals lo+j, lo+j+32, ...  The extend compares 32 bases
-// at a time: a two-word funnel shift aligns each sequence to the current
-// base, XOR marks mismatching bases, and clz/2 counts the leading matches.
+// ("compute_next" then "extend").  A pair is done at the first s with
+// M~[s, m-n] == m and rejected once s passes its threshold (early exit).
+// Lane j of a group handles diagonals lo+j, lo+j+G, ...  The extend compares
+// 32 bases at a time: a two-word funnel shift aligns each sequence to the
+// current base, XOR marks mismatching bases, and clz/2 counts leading matches.
+// Each wavefront is trimmed to the diagonals that hold a valid entry, so the
+// next range grows only from reachable diagonals.
 //
-// Every wavefront (M~, I~, D~ as int16 offsets) is kept in the warp's
-// scratch for the traceback (the paper's WRAM+MRAM variant keeps all
-// wavefront components in the larger memory and fetches what the next
-// wavefront needs, Section 2.4.4).
+// Every wavefront (M~, I~, D~ as int16 offsets) stays in the group's scratch
+// for the traceback (the paper's WRAM+MRAM variant keeps all wavefront
+// components in the larger memory and fetches what the next wavefront needs,
+// Section 2.4.4).
 //
 // Traceback.  Along a diagonal with match cost 0, the optimal cost of each
 // state is non-decreasing, so "state S of cell (v,h) is reachable with cost
@@ -34,7 +38,13 @@
 // taken in the order X, I, D, M -- the same canonical alignment as the DP
 // (among optimal alignments, ops read backward smallest under X < I < D < M).
 // A run of M's continues while the bases match and neither I~[c,k] nor
-// D~[c,k] reaches the current offset.
+// D~[c,k] reaches the current offset; its length comes from a backward
+// comparison of 32-base windows (XOR, count trailing zero base pairs).
+//
+// Work distribution: the launch walks a list of buckets (a range of a pair
+// order array plus a group size each); warps take 32/G consecutive positions
+// of a bucket from its device counter, and move to the next bucket when it is
+// exhausted, so a longest-first bucket order leaves short pairs for the tail.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
@@ -44,47 +54,30 @@
 namespace aim {
 namespace {
 
-struct WfaArgs {
-    int X, OE, E, g;
-    int64_t smax;
-    int band;
-    PairsView P;
-    LimitView L;
-    OutView O;
-    uint8_t* scratch;
-    size_t slot_bytes;
-    size_t hist_elems;
-    size_t meta_off;     // byte offset of the per-score (lo, hi, base) table in a slot
-    size_t runs_off;     // byte offset of the run staging area
-    uint32_t runs_cap;
-    uint32_t nwarps;
-    uint32_t* counter;
-};
-
 struct Wf {
-    int lo, hi, base, w;   // w == 0: empty
+    int lo, hi, base, w;   // entries of diagonal k at base + c*w + k (base already offset by -lo); w == 0: empty
 };
 
 __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     Wf f;
     if (s < 0) { f.lo = 1; f.hi = 0; f.base = 0; f.w = 0; return f; }
-    f.lo = meta[3 * s]; f.hi = meta[3 * s + 1]; f.base = meta[3 * s + 2];
-    f.w = f.hi >= f.lo ? f.hi - f.lo + 1 : 0;
+    const int4 q = reinterpret_cast<const int4*>(meta)[s];
+    f.lo = q.x; f.hi = q.y; f.base = q.z; f.w = q.w;
     return f;
 }
 
 // component c (0 M, 1 I, 2 D) of wavefront f at diagonal k, or a negative value
 __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, int k) {
     if (k < f.lo || k > f.hi) return kNeg16;
-    return hist[f.base + c * f.w + (k - f.lo)];
+    return hist[f.base + c * f.w + k];
 }
 
 // furthest offset reached from (h - k, h) along matches on diagonal k
 __device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, const uint64_t* Tw, uint32_t nwT,
-                                      int m, int k, int h, unsigned long long& words) {
+                                      int m, int k, int h, unsigned long long& windows) {
     int v = h - k;
     while (v < n && h < m) {
-        ++words;
+        ++windows;
         const uint64_t d = window32(Pw, nwP, (uint32_t)v) ^ window32(Tw, nwT, (uint32_t)h);
         const int rem = min(n - v, m - h);
         int adv = d ? (__clzll((long long)d) >> 1) : 32;
@@ -95,78 +88,123 @@ __device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, c
     return h;
 }
 
-__global__ void __launch_bounds__(256) wfa_kernel(WfaArgs a) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gwarp >= a.nwarps) return;
-    uint8_t* slot = a.scratch + (size_t)gwarp * a.slot_bytes;
-    int16_t* hist = reinterpret_cast<int16_t*>(slot);
-    int* meta = reinterpret_cast<int*>(slot + a.meta_off);
-    uint32_t* staged = reinterpret_cast<uint32_t*>(slot + a.runs_off);
-    const int X = a.X, OE = a.OE, E = a.E;
-    unsigned long long st_cells = 0, st_words = 0, st_pairs = 0;
+// 32 bases ending at base p (inclusive) with base p in the low two bits; for
+// p < 31 only bases 0..p are present (in the low bits).
+__device__ __forceinline__ uint64_t window_ending(const uint64_t* w, uint32_t nwords, int p) {
+    if (p >= 31) return window32(w, nwords, (uint32_t)(p - 31));
+    return window32(w, nwords, 0) >> (2 * (31 - p));
+}
 
+// number of consecutive matches P[v-1-i] == T[h-1-i], i = 0, 1, ... (at most min(v, h))
+__device__ __forceinline__ int match_run_back(const uint64_t* Pw, uint32_t nwP, int v, const uint64_t* Tw,
+                                              uint32_t nwT, int h) {
+    int run = 0;
     for (;;) {
-        uint32_t pi = 0;
-        if (lane == 0) pi = atomicAdd(a.counter, 1u);
-        pi = __shfl_sync(kFull, pi, 0);
-        if (pi >= a.P.num_pairs) break;
-        st_pairs += lane == 0;
+        const int pv = v - 1 - run, ph = h - 1 - run;
+        if (pv < 0 || ph < 0) break;
+        const uint64_t d = window_ending(Pw, nwP, pv) ^ window_ending(Tw, nwT, ph);
+        const int avail = min(min(pv, ph) + 1, 32);
+        int z = d ? ((__ffsll((long long)d) - 1) >> 1) : 32;
+        if (z > avail) z = avail;
+        run += z;
+        if (z < 32) break;
+    }
+    return run;
+}
 
-        const int n = (int)a.P.read_len[pi], m = (int)a.P.target_len[pi];
+enum : int { kRun = 0, kDone = 1, kRejected = 2, kCap = 3, kBad = 4, kIdle = 5 };
+
+struct Counters {
+    unsigned long long cells, windows, pairs;
+};
+
+// One step of the warp's work: groups g = 0 .. 32/G - 1 align the pairs at
+// order positions q0 + g (those < qend).  All lanes must call this together.
+template <int G>
+__device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
+                             Counters& st) {
+    constexpr int P = 32 / G;
+    const int g = (int)lane / G, gl = (int)lane % G, leader = g * G;
+    const uint32_t gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader);
+    const size_t group_bytes = (a.warp_bytes / P) & ~(size_t)15;
+    uint8_t* slot = warp_slot + (size_t)g * group_bytes;
+    int* meta = reinterpret_cast<int*>(slot);
+    uint32_t* staged = reinterpret_cast<uint32_t*>(slot + a.meta_bytes);
+    int16_t* hist = reinterpret_cast<int16_t*>(slot + a.meta_bytes + a.runs_bytes);
+    const size_t hist_cap = (group_bytes - a.meta_bytes - a.runs_bytes) / sizeof(int16_t);
+    const int X = a.X, OE = a.OE, E = a.E;
+
+    const uint32_t q = q0 + (uint32_t)g;
+    int status = kIdle;
+    uint32_t pi = 0;
+    int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0;
+    const uint64_t *Pw = nullptr, *Tw = nullptr;
+    uint32_t nwP = 0, nwT = 0;
+    if (q < qend) {
+        pi = a.order ? a.order[q] : q;
+        n = (int)a.P.read_len[pi];
+        m = (int)a.P.target_len[pi];
         const int64_t lim = pair_limit(a.L, pi);
-        const bool bad = pair_bad(a.P, pi) || (uint32_t)n > a.P.max_length ||
-                         (uint32_t)m > a.P.max_length || lim == -2;
-        if (bad) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_BAD_PAIR, 0);
-            continue;
+        kend = m - n;
+        if (pair_bad(a.P, pi) || (uint32_t)n > a.P.max_length || (uint32_t)m > a.P.max_length || lim == -2) {
+            status = kBad;
+        } else if (a.band >= 0 && (kend > a.band || -kend > a.band)) {
+            status = kRejected;
+        } else {
+            status = kRun;
+            int64_t S64 = lim / a.g;
+            S = (int)(S64 > a.smax ? a.smax : S64);
+            Pw = read_words(a.P, pi);
+            Tw = target_words(a.P, pi);
+            nwP = (uint32_t)(n + 31) >> 5;
+            nwT = (uint32_t)(m + 31) >> 5;
+            klo = a.band >= 0 ? max(-n, -a.band) : -n;
+            khi = a.band >= 0 ? min(m, a.band) : m;
         }
-        const int kend = m - n;
-        if (a.band >= 0 && (kend > a.band || -kend > a.band)) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
-            continue;
-        }
-        int64_t S64 = lim / a.g;
-        if (S64 > a.smax) S64 = a.smax;
-        const int S = (int)S64;
-        const uint64_t* Pw = read_words(a.P, pi);
-        const uint64_t* Tw = target_words(a.P, pi);
-        const uint32_t nwP = (uint32_t)(n + 31) >> 5, nwT = (uint32_t)(m + 31) >> 5;
-        const int klo = a.band >= 0 ? max(-n, -a.band) : -n;
-        const int khi = a.band >= 0 ? min(m, a.band) : m;
+        if (gl == 0) st.pairs += 1;
+    }
 
-        // score 0: diagonal 0 only
-        int top = 3;
-        int found = 0;
-        if (lane == 0) {
-            const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, st_words);
-            ++st_cells;
-            hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16;
-            meta[0] = 0; meta[1] = 0; meta[2] = 0;
-            found = (kend == 0 && m0 >= m);
-        }
-        found = __shfl_sync(kFull, found, 0);
-        __syncwarp();
-        int s = 0;
-        uint8_t status = 0;   // 0 running/found, AIM_F_REJECTED, AIM_F_STEP_CAP
-        while (!found) {
-            ++s;
-            if (s > S) { status = AIM_F_REJECTED; break; }
-            const Wf fx = load_wf(meta, s - X), fo = load_wf(meta, s - OE), fe = load_wf(meta, s - E);
-            int lo = 1 << 30, hi = -(1 << 30);
+    // score 0: diagonal 0 only
+    int top = 0, final_s = 0;
+    int found0 = 0;
+    if (status == kRun && gl == 0) {
+        const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, st.windows);
+        ++st.cells;
+        hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16;
+        reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
+        found0 = (kend == 0 && m0 >= m);
+    }
+    found0 = __shfl_sync(kFull, found0, leader);
+    if (status == kRun) {
+        top = 3;
+        if (found0) status = kDone;
+    }
+    __syncwarp();
+
+    int s = 0;
+    while (__any_sync(kFull, status == kRun)) {
+        ++s;
+        bool run = status == kRun;
+        if (run && s > S) { status = kRejected; run = false; }
+        int lo = 0, hi = -1, w = 0;
+        Wf fx, fo, fe;
+        if (run) {
+            fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+            lo = 1 << 30; hi = -(1 << 30);
             if (fx.w) { lo = min(lo, fx.lo); hi = max(hi, fx.hi); }
             if (fo.w) { lo = min(lo, fo.lo - 1); hi = max(hi, fo.hi + 1); }
             if (fe.w) { lo = min(lo, fe.lo - 1); hi = max(hi, fe.hi + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
-            if (lo > hi) {
-                if (lane == 0) { meta[3 * s] = 1; meta[3 * s + 1] = 0; meta[3 * s + 2] = top; }
-                __syncwarp();
-                continue;
-            }
-            const int w = hi - lo + 1;
-            if ((size_t)top + 3 * (size_t)w > a.hist_elems) { status = AIM_F_STEP_CAP; break; }
-            bool hit = false;
-            for (int k = lo + (int)lane; k <= hi; k += 32) {
+            w = lo <= hi ? hi - lo + 1 : 0;
+            if (w && (size_t)top + 3 * (size_t)w > hist_cap) { status = kCap; run = false; w = 0; }
+        }
+        const int iters = (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G));
+        bool hit = false;
+        int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
+        const int base = top - lo;
+        for (int it = 0; it < iters; ++it) {
+            const int k = lo + gl + it * G;
+            if (run && k <= hi) {
                 int ins = max(wf_get(hist, fo, 0, k + 1), wf_get(hist, fe, 1, k + 1));
                 if (ins >= 0 && ins - k > n) ins = kNeg16;
                 int del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1));
@@ -176,76 +214,142 @@ __global__ void __launch_bounds__(256) wfa_kernel(WfaArgs a) {
                 mis = mis >= 0 ? mis + 1 : kNeg16;
                 if (mis > m || mis - k > n) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));
-                const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, st_words) : kNeg16;
-                ++st_cells;
-                const int j = k - lo;
-                hist[top + j] = (int16_t)mv;
-                hist[top + w + j] = (int16_t)ins;
-                hist[top + 2 * w + j] = (int16_t)del;
+                const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, st.windows) : kNeg16;
+                ++st.cells;
+                hist[base + k] = (int16_t)mv;
+                hist[base + w + k] = (int16_t)ins;
+                hist[base + 2 * w + k] = (int16_t)del;
                 hit |= (k == kend && mv >= m);
+                if (f0 >= 0 || ins >= 0 || del >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
             }
-            found = __any_sync(kFull, hit);
-            if (lane == 0) { meta[3 * s] = lo; meta[3 * s + 1] = hi; meta[3 * s + 2] = top; }
+        }
+        // group-wide trimmed range (butterfly inside the group's lanes)
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            vlo = min(vlo, __shfl_xor_sync(kFull, vlo, o));
+            vhi = max(vhi, __shfl_xor_sync(kFull, vhi, o));
+        }
+        const uint32_t hits = __ballot_sync(kFull, hit);
+        if (run) {
+            if (gl == 0) {
+                const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
+                reinterpret_cast<int4*>(meta)[s] = rec;
+            }
             top += 3 * w;
-            __syncwarp();
+            if (hits & gmask) { status = kDone; final_s = s; }
         }
-        if (!found) {
-            if (lane == 0) write_header(a.O, pi, -1, status, 0);
-            continue;
-        }
-        const int32_t score = s * a.g;
-
-        // canonical traceback on lane 0
-        uint32_t nruns = 0;
-        bool ok = true;
-        if (lane == 0) {
-            RunWriter wr;
-            wr.init(staged, a.runs_cap);
-            int v = n, h = m, cM = s, cI = s, cD = s;
-            while (v > 0 || h > 0) {
-                const int k = h - v;
-                const bool diag = v > 0 && h > 0;
-                const bool match = diag && base_at(Pw, v - 1) == base_at(Tw, h - 1);
-                if (diag && !match && wf_get(hist, load_wf(meta, cM - X), 0, k) >= h - 1) {
-                    const int c = cM - X;
-                    cM = cI = cD = c; --v; --h;
-                    wr.put(kOpMismatch, 1);
-                } else if (v > 0 && wf_get(hist, load_wf(meta, cI), 1, k) >= h) {
-                    const int c = cI;
-                    cM = c - OE; cD = c - OE; cI = c - E; --v;
-                    wr.put(kOpIns, 1);
-                } else if (h > 0 && wf_get(hist, load_wf(meta, cD), 2, k) >= h) {
-                    const int c = cD;
-                    cM = c - OE; cI = c - OE; cD = c - E; --h;
-                    wr.put(kOpDel, 1);
-                } else if (match && wf_get(hist, load_wf(meta, cM), 0, k) >= h - 1) {
-                    const int c = cM;
-                    const Wf f = load_wf(meta, c);
-                    const int stop = max(wf_get(hist, f, 1, k), wf_get(hist, f, 2, k));
-                    int run = 0;
-                    do {
-                        --v; --h; ++run;
-                    } while (v > 0 && h > 0 && h > stop && base_at(Pw, v - 1) == base_at(Tw, h - 1));
-                    cM = cI = cD = c;
-                    wr.put(kOpMatch, (uint32_t)run);
-                } else {
-                    ok = false;
-                    break;
-                }
-            }
-            wr.finish();
-            nruns = wr.n;
-            ok = ok && wr.n <= wr.cap;
-        }
-        __syncwarp();
-        nruns = __shfl_sync(kFull, nruns, 0);
-        ok = __shfl_sync(kFull, ok, 0);
-        write_cigar(a.O, pi, score, staged, nruns, ok, lane);
         __syncwarp();
     }
-    warp_stat_add(a.O.stats, 0, st_cells, lane);
-    warp_stat_add(a.O.stats, 1, st_words, lane);
-    warp_stat_add(a.O.stats, 3, st_pairs, lane);
+
+    // canonical traceback on each group's first lane; every step issues the loads of all four tight
+    // tests at once (two memory round trips per step instead of a chain of dependent ones)
+    uint32_t nruns = 0;
+    bool ok = true;
+    if (status == kDone && gl == 0) {
+        const int* __restrict__ cmeta = meta;
+        const int16_t* __restrict__ chist = hist;
+        RunWriter wr;
+        wr.init(staged, a.runs_cap);
+        int v = n, h = m, cM = final_s, cI = final_s, cD = final_s;
+        while (v > 0 || h > 0) {
+            const int k = h - v;
+            const bool diag = v > 0 && h > 0;
+            const Wf fX = load_wf(cmeta, cM - X), fI = load_wf(cmeta, cI), fD = load_wf(cmeta, cD);
+            const Wf fM = load_wf(cmeta, cM);
+            const uint32_t pb = diag ? base_at(Pw, v - 1) : 0u, tb = diag ? base_at(Tw, h - 1) : 1u;
+            const int vX = wf_get(chist, fX, 0, k), vI = wf_get(chist, fI, 1, k), vD = wf_get(chist, fD, 2, k);
+            const int vM = wf_get(chist, fM, 0, k);
+            const int stop = max(wf_get(chist, fM, 1, k), wf_get(chist, fM, 2, k));
+            const bool match = diag && pb == tb;
+            if (diag && !match && vX >= h - 1) {
+                const int c = cM - X;
+                cM = cI = cD = c; --v; --h;
+                wr.put(kOpMismatch, 1);
+            } else if (v > 0 && vI >= h) {
+                const int c = cI;
+                cM = c - OE; cD = c - OE; cI = c - E; --v;
+                wr.put(kOpIns, 1);
+            } else if (h > 0 && vD >= h) {
+                const int c = cD;
+                cM = c - OE; cI = c - OE; cD = c - E; --h;
+                wr.put(kOpDel, 1);
+            } else if (match && vM >= h - 1) {
+                const int c = cM;
+                int run = match_run_back(Pw, nwP, v, Tw, nwT, h);
+                if (run > h - stop) run = h - stop;
+                if (run < 1) { ok = false; break; }
+                v -= run; h -= run;
+                cM = cI = cD = c;
+                wr.put(kOpMatch, (uint32_t)run);
+            } else {
+                ok = false;
+                break;
+            }
+        }
+        wr.finish();
+        nruns = wr.n;
+        ok = ok && wr.n <= wr.cap;
+    }
+    __syncwarp();
+    nruns = __shfl_sync(kFull, nruns, leader);
+    ok = __shfl_sync(kFull, ok, leader);
+    if (status == kDone) {
+        const int32_t score = final_s * a.g;
+        uint8_t flags = ok ? 0 : AIM_F_STEP_CAP;
+        if (ok && a.O.cigars && a.O.cigar_off) {
+            const uint64_t off = a.O.cigar_off[pi];
+            const uint64_t cap = a.O.cigar_off[pi + 1] - off;
+            if (nruns <= cap) {
+                for (uint32_t j = (uint32_t)gl; j < nruns; j += G) a.O.cigars[off + j] = staged[nruns - 1 - j];
+            } else {
+                flags |= AIM_F_CIGAR_OVERFLOW;
+            }
+        }
+        if (gl == 0) write_header(a.O, pi, ok ? score : -1, flags, nruns);
+    } else if (status != kIdle && gl == 0) {
+        const uint8_t f = status == kBad ? AIM_F_BAD_PAIR : status == kRejected ? AIM_F_REJECTED : AIM_F_STEP_CAP;
+        write_header(a.O, pi, -1, f, 0);
+    }
+    __syncwarp();
+}
+
+template <int G>
+__device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
+    constexpr int P = 32 / G;
+    const uint32_t begin = a.bounds ? a.bounds[b] : 0;
+    const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
+    for (;;) {
+        uint32_t pos = 0;
+        if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
+        pos = __shfl_sync(kFull, pos, 0);
+        if (pos >= end - begin || end <= begin) break;
+        align_groups<G>(a, warp_slot, begin + pos, end, lane, st);
+    }
+}
+
+#ifndef AIM_WFA_MIN_BLOCKS
+#define AIM_WFA_MIN_BLOCKS 4
+#endif
+
+__global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (gwarp >= a.nwarps) return;
+    uint8_t* warp_slot = a.scratch + (size_t)gwarp * a.warp_bytes;
+    Counters st{0, 0, 0};
+    for (int b = 0; b < a.nbuckets; ++b) {
+        switch (a.group[b]) {
+            case 1: run_bucket<1>(a, b, warp_slot, lane, st); break;
+            case 2: run_bucket<2>(a, b, warp_slot, lane, st); break;
+            case 4: run_bucket<4>(a, b, warp_slot, lane, st); break;
+            case 8: run_bucket<8>(a, b, warp_slot, lane, st); break;
+            case 16: run_bucket<16>(a, b, warp_slot, lane, st); break;
+            default: run_bucket<32>(a, b, warp_slot, lane, st); break;
+        }
+    }
+    warp_stat_add(a.O.stats, 0, st.cells, lane);
+    warp_stat_add(a.O.stats, 1, st.windows, lane);
+    warp_stat_add(a.O.stats, 3, st.pairs, lane);
 }
 
 int gcd_i(int a, int b) {
@@ -255,20 +359,10 @@ int gcd_i(int a, int b) {
 
 }  // namespace
 
-WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit) {
-    WfaPlan p;
-    p.g = gcd_i(gcd_i(c.x, c.o), c.e);
-    if (p.g <= 0) p.g = 1;
-    p.x = c.x / p.g; p.oe = (c.o + c.e) / p.g; p.e = c.e / p.g;
-    p.band = band;
-    const int64_t L = max_length;
-    const int64_t trivial = ((int64_t)c.x * L + c.o + (int64_t)c.e * L) / p.g;   // an alignment that always exists
-    int64_t smax = max_limit >= kUnbounded ? trivial : max_limit / p.g;
-    if (smax > trivial) smax = trivial;
-    p.smax = smax;
-    // worst-case wavefront ranges: every source wavefront non-empty
-    const int64_t klo = band >= 0 ? -std::min<int64_t>(L, band) : -L;
-    const int64_t khi = band >= 0 ? std::min<int64_t>(L, band) : L;
+// Worst-case entries of the wavefront history of one pair: every wavefront as wide as its sources allow.
+size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax) {
+    const int64_t klo = p.band >= 0 ? -std::min<int64_t>(max_len, p.band) : -max_len;
+    const int64_t khi = p.band >= 0 ? std::min<int64_t>(max_len, p.band) : max_len;
     std::vector<int64_t> lo(smax + 1), hi(smax + 1);
     lo[0] = 0; hi[0] = 0;
     size_t elems = 3;
@@ -283,44 +377,78 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
         lo[s] = l; hi[s] = h;
         if (l <= h) elems += 3 * (size_t)(h - l + 1);
     }
-    p.hist_elems = elems;
+    return elems;
+}
+
+WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit) {
+    WfaPlan p;
+    p.g = gcd_i(gcd_i(c.x, c.o), c.e);
+    if (p.g <= 0) p.g = 1;
+    p.x = c.x / p.g; p.oe = (c.o + c.e) / p.g; p.e = c.e / p.g;
+    p.band = band;
+    const int64_t L = max_length;
+    const int64_t trivial = ((int64_t)c.x * L + c.o + (int64_t)c.e * L) / p.g;   // an alignment that always exists
+    int64_t smax = max_limit >= kUnbounded ? trivial : max_limit / p.g;
+    if (smax > trivial) smax = trivial;
+    p.smax = smax;
+    p.hist_elems = wfa_hist_elems(p, L, smax);
     const int64_t minc = std::min<int64_t>(p.x, p.oe);
     int64_t runs = 2 * L + 1;
     if (minc > 0) runs = std::min<int64_t>(runs, 2 * (smax / minc) + 1);
     p.runs_cap = (int)runs;
-    const size_t meta_off = align_up(elems * sizeof(int16_t), 16);
-    const size_t runs_off = align_up(meta_off + (size_t)(smax + 1) * 3 * sizeof(int), 16);
-    p.slot_bytes = align_up(runs_off + (size_t)p.runs_cap * sizeof(uint32_t), 128);
+    p.meta_bytes = align_up((size_t)(smax + 1) * 4 * sizeof(int), 16);
+    p.runs_bytes = align_up((size_t)p.runs_cap * sizeof(uint32_t), 16);
+    p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
     return p;
 }
 
-cudaError_t launch_wfa(const WfaPlan& plan, const Costs& c, const PairsView& P, const LimitView& L,
-                       const OutView& O, uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms,
-                       cudaStream_t st, int* warps_used) {
-    (void)c;
+int wfa_default_group(const WfaPlan& p, uint32_t max_length) {
+    // widest wavefront a pair can reach: 2 * smax / E + 1 diagonals, clamped by the matrix and the band
+    int64_t w = 2 * (p.smax / std::max(p.e, 1)) + 1;
+    w = std::min<int64_t>(w, 2 * (int64_t)max_length + 1);
+    if (p.band >= 0) w = std::min<int64_t>(w, 2 * (int64_t)p.band + 1);
+    return w <= 64 ? 4 : w <= 128 ? 8 : w <= 256 ? 16 : 32;
+}
+
+cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const LimitView& L, const OutView& O,
+                               const uint32_t* order, const uint32_t* bounds, const int* groups, int nbuckets,
+                               size_t warp_bytes, uint8_t* scratch, size_t scratch_bytes, uint32_t* counters,
+                               int num_sms, cudaStream_t st, int* warps_used) {
     *warps_used = 0;
     if (P.num_pairs == 0) return cudaSuccess;
+    if (nbuckets < 1 || nbuckets > kMaxBuckets) return cudaErrorInvalidValue;
     WfaArgs a;
     a.X = plan.x; a.OE = plan.oe; a.E = plan.e; a.g = plan.g; a.smax = plan.smax; a.band = plan.band;
-    a.P = P; a.L = L; a.O = O; a.scratch = scratch; a.slot_bytes = plan.slot_bytes;
-    a.hist_elems = plan.hist_elems;
-    a.meta_off = align_up(plan.hist_elems * sizeof(int16_t), 16);
-    a.runs_off = align_up(a.meta_off + (size_t)(plan.smax + 1) * 3 * sizeof(int), 16);
-    a.runs_cap = (uint32_t)plan.runs_cap;
-    a.counter = counter;
+    a.P = P; a.L = L; a.O = O;
+    a.scratch = scratch; a.warp_bytes = warp_bytes;
+    a.meta_bytes = plan.meta_bytes; a.runs_bytes = plan.runs_bytes; a.runs_cap = (uint32_t)plan.runs_cap;
+    a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
+    for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int8_t)(b < nbuckets ? groups[b] : 32);
     int bps = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     size_t warps = (size_t)num_sms * bps * 8;
-    const size_t fit = scratch_bytes / plan.slot_bytes;
+    const size_t fit = scratch_bytes / warp_bytes;
     if (warps > fit) warps = fit;
-    if (warps > P.num_pairs) warps = P.num_pairs;
     if (warps == 0) return cudaSuccess;
+    if (!bounds) {
+        const size_t P1 = (size_t)(32 / std::max(groups[0], 1));
+        const size_t need = (P.num_pairs + P1 - 1) / P1;
+        if (warps > need) warps = need;
+    }
     a.nwarps = (uint32_t)warps;
     wfa_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
+}
+
+cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const LimitView& L, const OutView& O,
+                       uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
+                       int* warps_used) {
+    const size_t warp_bytes = (size_t)(32 / group) * plan.group_bytes;
+    return launch_wfa_buckets(plan, P, L, O, nullptr, nullptr, &group, 1, warp_bytes, scratch, scratch_bytes,
+                              counter, num_sms, st, warps_used);
 }
 
 }  // namespace aim

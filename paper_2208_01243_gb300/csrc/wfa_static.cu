@@ -96,7 +96,9 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
 
     const aim::WfaPlan plan = aim::plan_wfa(costs, pen->band, max_length, max_limit);
     const size_t capacity = kStaticScratchBytes - kStaticHeaderBytes;
-    if (plan.slot_bytes > capacity) return AIM_ERR_NOMEM;   // one pair's scratch exceeds the static array
+    int group = aim::wfa_default_group(plan, max_length);
+    while (group < 32 && (size_t)(32 / group) * plan.group_bytes > capacity) group *= 2;
+    if ((size_t)(32 / group) * plan.group_bytes > capacity) return AIM_ERR_NOMEM;   // one pair's scratch is too big
 
     uint8_t* base = nullptr;
     int sms = 0;
@@ -110,7 +112,7 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
                      nullptr, nullptr, num_pairs, max_length};
     aim::OutView O{out_scores, out_cigars, cigar_offsets, out_cigar_lens, out_flags, nullptr};
     int warps = 0;
-    e = aim::launch_wfa(plan, costs, P, lim, O, base + kStaticHeaderBytes, capacity, counter, sms, st, &warps);
+    e = aim::launch_wfa(plan, group, P, lim, O, base + kStaticHeaderBytes, capacity, counter, sms, st, &warps);
     if (e != cudaSuccess) return AIM_ERR_CUDA;
     return warps > 0 ? AIM_OK : AIM_ERR_NOMEM;
 }

@@ -1,0 +1,101 @@
+"""Batched form (bucketed queues, autotuned lanes per pair, CUDA-graph replay) against the plain form and the oracle."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from devutil import assert_same, device_results, oracle_results
+
+pytestmark = pytest.mark.gpu
+
+AFF = (0, 4, 6, 2)
+
+
+def _mixed(n_uneven=2_500, n_short=2_003):
+    pu = gen.generate(gen.WFA_UNEVEN, n_uneven)
+    ps = gen.generate(gen.WFA_150BP, n_short)
+    p = gen.concat([pu, ps])
+    me = np.concatenate([gen.per_pair_max_edits(gen.WFA_UNEVEN, pu), np.full(n_short, 6, np.int32)])
+    return p, me
+
+
+def _batched(p, me, autotune, runs=2, scratch=0):
+    import torch
+    import paper_2208_01243_gb300 as aim
+    n = len(p)
+    cap = p.read_len.astype(np.int64) + p.target_len.astype(np.int64) + 1
+    coff = np.zeros(n + 1, np.int64); coff[1:] = np.cumsum(cap)
+    reads, targets, ro, to, rl, tl, cd, pp = aim.upload(p.reads, p.targets, p.read_off, p.target_off, p.read_len,
+                                                        p.target_len, coff, me.astype(np.int32))
+    al = aim.Aligner(0, 1 << 30)
+    dev = rl.device
+    scores = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    lens = torch.zeros(n, dtype=torch.int32, device=dev)
+    cig = torch.zeros(int(coff[-1]), dtype=torch.int32, device=dev)
+    ml = int(max(p.read_len.max(), p.target_len.max()))
+    plan = aim.aim_batch_plan(al.ctx, reads, targets, ro, to, rl, tl, ml, aim.penalties(4, 6, 2), int(me.max()), pp,
+                              scores, cig, cd, lens, flags, scratch_bytes=scratch, autotune=autotune)
+    groups, counts = aim.aim_batch_info(plan)
+    outs = []
+    for _ in range(runs):
+        scores.fill_(-7); flags.fill_(255)
+        aim.aim_batch_run(plan)
+        torch.cuda.synchronize()
+        s = scores.cpu().numpy(); f = flags.cpu().numpy(); ln = lens.cpu().numpy().view(np.uint32)
+        cg = cig.cpu().numpy().view(np.uint32)
+        outs.append((s, f, [cg[coff[i]:coff[i] + ln[i]] for i in range(n)], ln))
+    aim.aim_batch_destroy(plan)
+    al.close()
+    return outs, groups, counts
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_batched_equals_plain_and_oracle(oracle_lib, gen_lib, autotune):
+    import __graft_entry__
+    __graft_entry__.build()
+    p, me = _mixed()
+    outs, groups, counts = _batched(p, me, autotune)
+    assert sum(counts) == len(p)
+    assert all(g in (1, 2, 4, 8, 16, 32) for g in groups)
+    plain = device_results(p, "wfa", AFF, int(me.max()), per_pair=me)
+    for o in outs:                       # every replay gives the plain form's results, bit for bit
+        assert np.array_equal(o[0], plain[0]) and np.array_equal(o[1], plain[1])
+        assert all(np.array_equal(x, y) for x, y in zip(o[2], plain[2]))
+    idx = np.random.default_rng(4).choice(len(p), 400, replace=False)
+    sub = gen.concat([gen.from_strings([p.read(i)], [p.target(i)]) for i in idx])
+    lim = np.array([oracle.limit_for(AFF, int(me[i])) for i in idx], np.int64)
+    assert_same(outs[-1], oracle_results(sub, AFF, lim), idx=idx, what="batched vs oracle")
+
+
+def test_batched_replay_sees_new_contents(gen_lib):
+    """The plan binds buffers, not data: a replay after the inputs change aligns the new pairs."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    p1 = gen.generate(gen.WFA_150BP, 3000)
+    p2 = gen.generate(gen.WFA_150BP, 3000, first=3000)
+    # same shapes: every read 150 bp, targets of varying length -> pad both batches into fixed slots
+    slot = 160
+    def slots(p):
+        buf = np.full(2 * len(p) * slot, ord("A"), np.uint8)
+        for i in range(len(p)):
+            r, t = p.read(i), p.target(i)
+            buf[2 * i * slot:2 * i * slot + len(r)] = np.frombuffer(r, np.uint8)
+            buf[(2 * i + 1) * slot:(2 * i + 1) * slot + len(t)] = np.frombuffer(t, np.uint8)
+        return buf
+    n = len(p1)
+    ro = np.arange(n, dtype=np.int64) * 2 * slot; to = ro + slot
+    buf, ro_d, to_d = aim.upload(slots(p1), ro, to)
+    rl, tl = aim.upload(p1.read_len, p1.target_len)
+    al = aim.Aligner(0, 1 << 30)
+    out = al.outputs(n)
+    plan = aim.aim_batch_plan(al.ctx, buf, buf, ro_d, to_d, rl, tl, slot, aim.penalties(4, 6, 2), 6, None,
+                              out["scores"], None, None, out["cigar_lens"], out["flags"], autotune=False)
+    aim.aim_batch_run(plan); torch.cuda.synchronize()
+    a = out["scores"].cpu().numpy().copy()
+    buf.copy_(torch.from_numpy(slots(p2)).cuda()); tl.copy_(torch.from_numpy(p2.target_len.view(np.int32)).cuda())
+    aim.aim_batch_run(plan); torch.cuda.synchronize()
+    b = out["scores"].cpu().numpy().copy()
+    aim.aim_batch_destroy(plan); al.close()
+    assert np.array_equal(a, device_results(p1, "wfa", AFF, 6)[0])
+    assert np.array_equal(b, device_results(p2, "wfa", AFF, 6)[0])

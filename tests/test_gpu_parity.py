@@ -196,3 +196,20 @@ def test_results_independent_of_batch_composition(aligner, gen_lib):
     for j, i in enumerate(perm):
         assert shuf[0][j] == full[0][i] and shuf[1][j] == full[1][i]
         assert np.array_equal(shuf[2][j], full[2][i])
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+def test_wfa_every_group_size_matches_oracle(aligner, oracle_lib, gen_lib, lanes):
+    """Lanes per pair change only the schedule, never a result."""
+    import paper_2208_01243_gb300 as aim
+    w = gen.WFA_UNEVEN
+    p = gen.concat([gen.generate(gen.WFA_150BP, 1_203), gen.generate(w, 301)])
+    me = np.concatenate([np.full(1_203, 6, np.int32), gen.per_pair_max_edits(w, p)[1_203:]])
+    lim = np.array([oracle.limit_for(AFF, int(k)) for k in me], np.int64)
+    orc = oracle_results(p, AFF, lim)
+    aim.aim_set_wfa_group(aligner.ctx, lanes)
+    try:
+        dev = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    finally:
+        aim.aim_set_wfa_group(aligner.ctx, 0)
+    assert_same(dev, orc, what=f"wfa lanes={lanes}")
