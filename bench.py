@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count (0: as defined)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workspace-gb", type=float, default=8.0, help="aligner context workspace (GiB)")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving wavefront-state budget (GiB)")
     return ap.parse_args()
 
 
@@ -219,6 +222,11 @@ def cpu_baseline(w, algo):
 
 # ---------------------------------------------------------------- our arm
 
+def rank_first(rank: int, pairs_per_rank: int) -> int:
+    """First pair index of a rank's slice of the workload's pair stream (weak scaling: disjoint slices)."""
+    return rank * pairs_per_rank
+
+
 def _dist_max(x, dev, world):
     if world == 1:
         return x
@@ -256,7 +264,7 @@ def run_ours(args, w, algo):
     batched = args.workload == "wfa_uneven"
 
     n_pairs = args.pairs or w.pairs
-    p = gen.generate(w, n_pairs, first=rank * n_pairs)     # each rank: its own slice of the pair stream
+    p = gen.generate(w, n_pairs, first=rank_first(rank, n_pairs))   # each rank: its own slice of the pair stream
     max_edits, per_pair = max_edits_args(w, p)
     band = w.band if algo != "wfa" or args.workload == "wfa_250bp" else -1
     pen_t = (0, 1, 0, 1) if algo == "edit" else w.penalties
@@ -457,6 +465,8 @@ def run_ours(args, w, algo):
             "clocks": clk}
     if plain is not None:
         line["plain"] = plain
+    if batched and not args.no_serve and world == 1:
+        line["serving"] = serving(args, local)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, algo)
     print(json.dumps(line))
@@ -464,6 +474,75 @@ def run_ours(args, w, algo):
         aim.aim_batch_destroy(plan)
     al.close()
     return 0
+
+
+# ---------------------------------------------------------------- serving loop
+
+def serving(args, local):
+    """Poisson arrivals of requests (1-4096 pairs, log-uniform; reads 100-10,000 bp log-uniform; 1-10 % edits;
+    thresholds at 10 % of length) through the continuous-batching server: peak = closed-loop throughput with
+    a backlog of requests, then p50/p99 latency and sustained alignments/s at 50/80/95 % of that peak."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    w = gen.SERVE_LONG
+    pool = gen.generate(w, 40_000)
+    me_all = gen.per_pair_max_edits(w, pool).astype(np.int32)
+    ctx = aim.aim_create(local, 64 << 20)
+    srv = aim.aim_server_create(ctx, aim.penalties(*w.penalties[1:]), int(args.serve_budget_gb * (1 << 30)), 6 << 30)
+    cursor = [0]
+
+    def make_request(k):
+        at = cursor[0] % (len(pool) - k) if len(pool) > k else 0
+        cursor[0] += k
+        idx = slice(at, at + k)
+        ro = pool.read_off[idx]; to = pool.target_off[idx]
+        reads, targets = pool.reads, pool.targets
+        cap = (pool.read_len[idx].astype(np.int64) + pool.target_len[idx].astype(np.int64) + 1)
+        coff = np.zeros(k + 1, np.uint64); coff[1:] = np.cumsum(cap)
+        out = (np.empty(k, np.int32), np.empty(k, np.uint8), np.empty(k, np.uint32),
+               np.empty(int(coff[-1]), np.uint32))
+        return (reads, targets, ro, to, pool.read_len[idx], pool.target_len[idx], me_all[idx], out[0], out[1], out[2],
+                out[3], coff), k
+
+    def run(arrivals, sizes):
+        t0 = time.perf_counter()
+        tickets = []
+        for a, k in zip(arrivals, sizes):
+            req, k = make_request(int(k))
+            now = time.perf_counter() - t0
+            if a > now:
+                time.sleep(a - now)
+            t, keep = aim.aim_server_submit(srv, *req)
+            tickets.append((t, keep, k))
+        lats = [aim.aim_server_wait(srv, t) for t, _, _ in tickets]
+        wall = time.perf_counter() - t0
+        pairs = sum(k for _, _, k in tickets)
+        return np.array(lats), pairs, wall
+
+    # peak: a backlog of requests submitted at once
+    _, sizes = gen.arrivals(505, 160, 1.0)
+    run(np.zeros(16), sizes[:16])                               # warm-up
+    lat, pairs, wall = run(np.zeros(len(sizes)), sizes)
+    peak = pairs / wall
+    mean_req = float(sizes.mean())
+    levels = {}
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * peak / mean_req                          # requests per second
+        count = max(20, int(rate * args.serve_seconds))
+        arr, sz = gen.arrivals(600 + int(frac * 100), count, rate)
+        lat, pairs, wall = run(arr, sz)
+        levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": frac * peak, "requests": count,
+                                         "sustained_alignments_per_s": pairs / wall,
+                                         "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
+                                         "p99_latency_ms": float(np.percentile(lat, 99) * 1e3)}
+    st = aim.aim_server_stats(srv)
+    aim.aim_server_destroy(srv)
+    aim.aim_destroy(ctx)
+    return {"workload": "serve_100_10000bp_1_10pct: Poisson requests of 1-4096 pairs (log-uniform), reads "
+                        "100-10,000 bp (log-uniform), 1-10 % edits, WFA 4/6/2, thresholds ceil(0.1*len)",
+            "wavefront_budget_gib": args.serve_budget_gb, "peak_alignments_per_s": peak, "mean_pairs_per_request": mean_req,
+            "loads": levels, "failed": st["failed"],
+            "latency": "server clock from submission to results in host memory (includes queueing, copies)"}
 
 
 def main():

@@ -204,6 +204,50 @@ AIM_API int aim_batch_info(aim_batch *batch, int *groups /* host[32] */, uint32_
 AIM_API int aim_batch_destroy(aim_batch *batch);
 
 /*
+ * Serving loop (wavefront algorithm, continuous batching).  Requests of 1 to
+ * many pairs arrive over time from host memory; a worker thread admits them
+ * in arrival order whenever the server's fixed arenas have room: pinned
+ * staging and device I/O (io_budget_bytes each, 0: 1 GiB) and device
+ * wavefront scratch (wavefront_budget_bytes, 0: 4 GiB; the memory budget for
+ * wavefront state, which never leaves the device).  A request's pairs are
+ * grouped into jobs by their work bound (each job with its own scratch per
+ * warp); an admitted request gets one scratch grant of up to half of the
+ * budget and runs on its own stream (copy in, pack, one launch per job, copy
+ * out), so requests that arrive while others run overlap on the device.  Results are those of
+ * aim_align_batch_ascii for the same pairs, independent of what else runs.
+ * aim_server_create allocates the arenas and starts the worker thread.
+ */
+typedef struct aim_server aim_server;
+typedef struct {
+    const uint8_t *reads, *targets;                 /* host: ASCII */
+    const uint64_t *read_offsets, *target_offsets;  /* host: byte offsets */
+    const uint32_t *read_lengths, *target_lengths;  /* host */
+    const int32_t *max_edits;                       /* host: per pair, or NULL to use max_edits_all */
+    int32_t max_edits_all;                          /* >= 0 (the server needs a threshold) */
+    uint32_t num_pairs;
+    int32_t *out_scores;                            /* host, written when the request completes */
+    uint8_t *out_flags;                             /* host */
+    uint32_t *out_cigar_lens;                       /* host, optional */
+    uint32_t *out_cigars;                           /* host, optional (with cigar_offsets) */
+    const uint64_t *cigar_offsets;                  /* host, num_pairs + 1 entries, optional */
+} aim_request;
+/* pen: costs and band for every request (max_score must be < 0: thresholds are per pair). */
+AIM_API int aim_server_create(aim_ctx *ctx, const aim_penalties_t *pen, size_t wavefront_budget_bytes,
+                              size_t io_budget_bytes, aim_server **out);
+/* Copies the request's inputs and queues it; the output buffers must stay valid until it completes.
+ * AIM_ERR_NOMEM: one pair's wavefront scratch or the request's I/O exceeds the server's budgets. */
+AIM_API int aim_server_submit(aim_server *server, const aim_request *request, uint64_t *ticket);
+/* *done = 1 once the request's results are in its output buffers; then the ticket is released and
+ * *latency_ns (optional) holds submission-to-completion time.  Returns the request's status when done. */
+AIM_API int aim_server_poll(aim_server *server, uint64_t ticket, int *done, uint64_t *latency_ns);
+/* Blocks until the request completes (then as aim_server_poll with done = 1). */
+AIM_API int aim_server_wait(aim_server *server, uint64_t ticket, uint64_t *latency_ns);
+/* out[6]: submitted, completed, pairs completed, failed, queued now, running now. */
+AIM_API int aim_server_stats(aim_server *server, uint64_t *out);
+/* Finishes every queued and running request, then frees the server. */
+AIM_API int aim_server_destroy(aim_server *server);
+
+/*
  * Lanes that cooperate on one pair in the wavefront kernel: 1, 2, 4, 8, 16 or 32
  * (a warp then aligns 32/lanes pairs in lockstep), or 0 to let the library
  * choose from the widest wavefront the call's lengths and threshold allow.

@@ -26,6 +26,15 @@ class aim_penalties_t(ctypes.Structure):
                 ("gap_extend", ctypes.c_int32), ("max_score", ctypes.c_int32), ("band", ctypes.c_int32)]
 
 
+class aim_request(ctypes.Structure):
+    _fields_ = [("reads", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("read_offsets", ctypes.c_void_p),
+                ("target_offsets", ctypes.c_void_p), ("read_lengths", ctypes.c_void_p),
+                ("target_lengths", ctypes.c_void_p), ("max_edits", ctypes.c_void_p), ("max_edits_all", ctypes.c_int32),
+                ("num_pairs", ctypes.c_uint32), ("out_scores", ctypes.c_void_p), ("out_flags", ctypes.c_void_p),
+                ("out_cigar_lens", ctypes.c_void_p), ("out_cigars", ctypes.c_void_p),
+                ("cigar_offsets", ctypes.c_void_p)]
+
+
 class AimError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -61,6 +70,14 @@ def _lib():
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
+        lib.aim_server_create.argtypes = [p, ctypes.POINTER(aim_penalties_t), ctypes.c_size_t, ctypes.c_size_t,
+                                          ctypes.POINTER(p)]
+        lib.aim_server_submit.argtypes = [p, ctypes.POINTER(aim_request), ctypes.POINTER(ctypes.c_uint64)]
+        lib.aim_server_poll.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_uint64)]
+        lib.aim_server_wait.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
+        lib.aim_server_stats.argtypes = [p, p]
+        lib.aim_server_destroy.argtypes = [p]
         lib.aim_batch_info.argtypes = [p, p, p]
         lib.aim_batch_destroy.argtypes = [p]
         lib.aim_stats_reset.argtypes = [p, p]
@@ -180,6 +197,78 @@ def aim_batch_info(batch):
 
 def aim_batch_destroy(batch) -> None:
     _check(_lib().aim_batch_destroy(batch), "aim_batch_destroy")
+
+
+def _host(a, dtype, name, optional=False):
+    import numpy as np
+    if a is None:
+        if optional:
+            return None, None
+        raise ValueError(f"{name} is required")
+    a = np.ascontiguousarray(a)
+    if a.dtype.itemsize != np.dtype(dtype).itemsize:
+        raise TypeError(f"{name} must be {np.dtype(dtype)}")
+    return a, ctypes.c_void_p(a.ctypes.data)
+
+
+def aim_server_create(ctx, pen, wavefront_budget_bytes: int = 0, io_budget_bytes: int = 0):
+    s = ctypes.c_void_p()
+    _check(_lib().aim_server_create(ctx, ctypes.byref(pen), wavefront_budget_bytes, io_budget_bytes, ctypes.byref(s)),
+           "aim_server_create")
+    return s
+
+
+def aim_server_submit(server, reads, targets, read_offsets, target_offsets, read_lengths, target_lengths,
+                      max_edits, out_scores, out_flags, out_cigar_lens=None, out_cigars=None, cigar_offsets=None,
+                      max_edits_all: int = 0):
+    """Queue one request (numpy host arrays; outputs are filled when it completes).  Returns (ticket, keep):
+    `keep` holds the arrays the server reads or writes and must live until the request completes."""
+    import numpy as np
+    keep = []
+    def h(a, dt, name, optional=False):
+        arr, ptr = _host(a, dt, name, optional)
+        keep.append(arr)
+        return ptr
+    q = aim_request(h(reads, np.uint8, "reads"), h(targets, np.uint8, "targets"),
+                    h(read_offsets, np.uint64, "read_offsets"), h(target_offsets, np.uint64, "target_offsets"),
+                    h(read_lengths, np.uint32, "read_lengths"), h(target_lengths, np.uint32, "target_lengths"),
+                    h(max_edits, np.int32, "max_edits", True), int(max_edits_all), int(len(read_lengths)),
+                    h(out_scores, np.int32, "out_scores"), h(out_flags, np.uint8, "out_flags"),
+                    h(out_cigar_lens, np.uint32, "out_cigar_lens", True), h(out_cigars, np.uint32, "out_cigars", True),
+                    h(cigar_offsets, np.uint64, "cigar_offsets", True))
+    for name, a in (("out_scores", out_scores), ("out_flags", out_flags), ("out_cigar_lens", out_cigar_lens),
+                    ("out_cigars", out_cigars)):
+        if a is not None and not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+            raise TypeError(f"{name} must be a C-contiguous numpy array (the server writes into it)")
+    t = ctypes.c_uint64()
+    _check(_lib().aim_server_submit(server, ctypes.byref(q), ctypes.byref(t)), "aim_server_submit")
+    return t.value, keep
+
+
+def aim_server_poll(server, ticket: int):
+    """(done, latency_s or None)."""
+    d = ctypes.c_int(); lat = ctypes.c_uint64()
+    rc = _lib().aim_server_poll(server, ticket, ctypes.byref(d), ctypes.byref(lat))
+    _check(rc, "aim_server_poll")
+    return bool(d.value), (lat.value * 1e-9 if d.value else None)
+
+
+def aim_server_wait(server, ticket: int) -> float:
+    """Block until the request completes; returns its latency in seconds."""
+    lat = ctypes.c_uint64()
+    _check(_lib().aim_server_wait(server, ticket, ctypes.byref(lat)), "aim_server_wait")
+    return lat.value * 1e-9
+
+
+def aim_server_stats(server) -> dict:
+    import numpy as np
+    o = np.zeros(6, np.uint64)
+    _check(_lib().aim_server_stats(server, ctypes.c_void_p(o.ctypes.data)), "aim_server_stats")
+    return dict(zip(["submitted", "completed", "pairs_completed", "failed", "queued", "running"], map(int, o)))
+
+
+def aim_server_destroy(server) -> None:
+    _check(_lib().aim_server_destroy(server), "aim_server_destroy")
 
 
 def aim_set_wfa_group(ctx, lanes: int) -> None:
