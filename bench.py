@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 import gen  # noqa: E402
 
 WORKLOADS = {"wfa_150bp": gen.WFA_150BP, "edit_nw_100bp": gen.EDIT_NW_100BP,
-             "gotoh_250bp": gen.GOTOH_WFA_250BP, "wfa_250bp": gen.GOTOH_WFA_250BP, "wfa_uneven": gen.WFA_UNEVEN}
+             "gotoh_250bp": gen.GOTOH_WFA_250BP, "wfa_250bp": gen.GOTOH_WFA_250BP, "wfa_uneven": gen.WFA_UNEVEN,
+             "wfa_uneven_plain": gen.WFA_UNEVEN}
 ALGO_OF = {"wfa_150bp": "wfa", "edit_nw_100bp": "edit", "gotoh_250bp": "gotoh", "wfa_250bp": "wfa",
-           "wfa_uneven": "wfa"}
+           "wfa_uneven": "wfa", "wfa_uneven_plain": "wfa"}
 
 # Algorithmic integer operations per unit of counted work (the roofline numerator):
 #   WFA wavefront entry: I~ one max, D~ one max + one add, mismatch candidate one add, f0 two max = 6
@@ -58,6 +59,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workspace-gb", type=float, default=8.0, help="aligner context workspace (GiB)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per pair for the plain WFA calls (0: library choice)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving wavefront-state budget (GiB)")
     return ap.parse_args()
@@ -280,6 +282,8 @@ def run_ours(args, w, algo):
     d = dict(zip(host, aim.upload(*host.values(), device=local)))
     coff_d = aim.upload(coff, device=local)[0]
     al = aim.Aligner(local, int(args.workspace_gb * (1 << 30)))
+    if args.lanes:
+        aim.aim_set_wfa_group(al.ctx, args.lanes)
     out = {"scores": torch.empty(n_pairs, dtype=torch.int32, device=dev),
            "flags": torch.empty(n_pairs, dtype=torch.uint8, device=dev),
            "lens": torch.empty(n_pairs, dtype=torch.int32, device=dev),
