@@ -249,7 +249,8 @@ AIM_API int aim_server_destroy(aim_server *server);
 
 /*
  * Lanes that cooperate on one pair in the wavefront kernel: 1, 2, 4, 8, 16 or 32
- * (a warp then aligns 32/lanes pairs in lockstep), or 0 to let the library
+ * (a warp then aligns 32/lanes pairs in lockstep), 256 (a whole block of 8
+ * warps aligns one pair: for long, noisy pairs), or 0 to let the library
  * choose from the widest wavefront the call's lengths and threshold allow.
  * Results do not depend on it; throughput does.  A choice whose scratch does
  * not fit the workspace is widened until it fits.

@@ -123,8 +123,10 @@ struct WfaPlan {
 };
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
 size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax);
-// lanes per pair suited to the widest wavefront the plan allows (4, 8, 16 or 32; 1 and 2 are valid too)
+// lanes per pair suited to the widest wavefront the plan allows (4, 8, 16, 32 or 256; 1 and 2 are valid too)
 int wfa_default_group(const WfaPlan& p, uint32_t max_length);
+// scratch per warp for `group` lanes per pair (256: the block's 8 warps share one pair's scratch)
+size_t wfa_warp_bytes(int group, size_t group_bytes);
 
 struct WfaArgs {
     int X, OE, E, g;

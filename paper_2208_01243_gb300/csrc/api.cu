@@ -139,8 +139,10 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
         const aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
         int group = ctx->wfa_group ? ctx->wfa_group : aim::wfa_default_group(plan, P.max_length);
-        while (group < 32 && (size_t)(32 / group) * plan.group_bytes > scratch_bytes) group *= 2;
-        if ((size_t)(32 / group) * plan.group_bytes > scratch_bytes) return AIM_ERR_NOMEM;
+        // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
+        while (group <= 32 && 8 * aim::wfa_warp_bytes(group, plan.group_bytes) > scratch_bytes)
+            group = group == 32 ? 256 : group * 2;
+        if (8 * aim::wfa_warp_bytes(group, plan.group_bytes) > scratch_bytes) return AIM_ERR_NOMEM;
         slot = time_begin(ctx, 1, st);
         err = aim::launch_wfa(plan, group, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
     } else {
@@ -243,7 +245,8 @@ int aim_destroy(aim_ctx* ctx) {
 }
 
 int aim_set_wfa_group(aim_ctx* ctx, int lanes) {
-    if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+    if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32 ||
+                  lanes == 256))
         return AIM_ERR_ARG;
     ctx->wfa_group = lanes;
     return AIM_OK;

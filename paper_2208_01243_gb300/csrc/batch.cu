@@ -15,8 +15,8 @@
 //
 // Autotuner.  For every non-empty bucket, timed trial launches on a sample of
 // up to 4,096 of its pairs try the group sizes that suit its width class (so
-// that no lane walks more than about 64 diagonals per score step) and keep
-// the fastest; choices are cached in the context per (costs, band, bucket).
+// that no lane walks more than about 64 diagonals per score step; the widest
+// class may also use a whole block per pair) and keep the fastest; choices are cached in the context per (costs, band, bucket).
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -33,7 +33,7 @@ namespace {
 constexpr int kBuckets = 32;
 constexpr int kWidthClasses = 4;
 constexpr int kWorkClasses = 8;
-constexpr int kCandidates[6] = {1, 2, 4, 8, 16, 32};
+constexpr int kCandidates[7] = {1, 2, 4, 8, 16, 32, 256};
 
 struct BucketParams {
     int g, E, band;
@@ -210,10 +210,10 @@ int autotune(aim_batch* b) {
         // lanes per pair worth trying for this width class: at most ~64 diagonals per lane and score step
         const int wc = kWidthClasses - 1 - k % kWidthClasses;
         const int gmin = wc == 0 ? 1 : wc == 1 ? 2 : wc == 2 ? 4 : 8;
-        const int gmax = wc == 0 ? 8 : wc == 1 ? 16 : 32;
+        const int gmax = wc == 0 ? 8 : wc == 1 ? 16 : wc == 2 ? 32 : 256;
         for (int G : kCandidates) {
             if (G < gmin || G > gmax) continue;
-            const size_t wb = (size_t)(32 / G) * bucket_group_bytes(b->plan, k, b->max_length);
+            const size_t wb = wfa_warp_bytes(G, bucket_group_bytes(b->plan, k, b->max_length));
             if (wb * min_warps > b->scratch_bytes) continue;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -337,7 +337,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     // scratch per warp: the largest need over all buckets (a replay may see a different mix)
     size_t wb = 0;
     for (int k = 0; k < kBuckets; ++k)
-        wb = std::max(wb, (size_t)(32 / b->groups[k]) * bucket_group_bytes(b->plan, k, max_length));
+        wb = std::max(wb, wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k, max_length)));
     b->warp_bytes = wb;
     if (wb > b->scratch_bytes) { free_batch(b); return AIM_ERR_NOMEM; }
 

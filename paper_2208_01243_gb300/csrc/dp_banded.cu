@@ -29,6 +29,7 @@
 // Trace bits are stored per warp as rows of anti-diagonals, entry (d, q/2),
 // so the 32 lanes of a step write one contiguous row.
 #include <type_traits>
+#include <utility>
 
 #include "aim_internal.cuh"
 
@@ -91,69 +92,102 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
         const uint64_t* Pw = read_words(a.P, pi);
         const uint64_t* Tw = target_words(a.P, pi);
 
-        // per slot (block r, parity p): the latest cell of that diagonal
-        int32_t M0[R], I0[R], D0[R], M1[R], I1[R], D1[R];
+        // per slot (parity p, block r): the latest cell of that diagonal, the anti-diagonal range where the
+        // diagonal holds cells of this pair, and the packed words its cells read (advanced, not reloaded)
+        int32_t Ms[2][R], Is[2][R], Ds[2][R];
+        int dlo[2][R], dhi[2][R];
+        uint64_t pw[2][R], tw[2][R];
+        int pwi[2][R], twi[2][R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) { M0[r] = I0[r] = D0[r] = M1[r] = I1[r] = D1[r] = kInf; }
+        for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                Ms[pp][r] = Is[pp][r] = Ds[pp][r] = kInf;
+                const int q = 2 * (32 * r + (int)lane) + pp, k = q - b;
+                // cell (v,h) of diagonal k lies on anti-diagonal d = 2v + k: v >= 0, h >= 0, v <= n, h <= m
+                dlo[pp][r] = q <= 2 * b ? (k < 0 ? -k : k) : (1 << 30);
+                dhi[pp][r] = min(2 * (int)n + k, 2 * (int)m - k);
+                pwi[pp][r] = twi[pp][r] = -1;
+                pw[pp][r] = tw[pp][r] = 0;
+            }
         {   // seed: cell (0,0) on diagonal k = 0, q = b
             const int i0 = b >> 1, p0 = b & 1;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (r == (i0 >> 5) && (int)lane == (i0 & 31)) { if (p0) M1[r] = 0; else M0[r] = 0; }
+                if (r == (i0 >> 5) && (int)lane == (i0 & 31)) Ms[p0][r] = 0;
         }
         bool prev_over = false, rejected = false;
         const int dend = (int)(n + m);
-        for (int d = 1; d <= dend; ++d) {
-            const int p = (d + b) & 1;
+
+        // one anti-diagonal step on the slots of parity P (P == (d + b) & 1)
+        auto step = [&](const int d, auto parity) -> bool {
+            constexpr int P = decltype(parity)::value;
             bool over = true;
+            TB* trow = trace + (size_t)d * RW;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const int i = 32 * r + (int)lane;
-                const int q = 2 * i + p;
-                const int k = q - b;
-                const int v = (d - k) >> 1, h = (d + k) >> 1;
-                const bool valid = q <= 2 * b && v >= 0 && h >= 0 && v <= (int)n && h <= (int)m;
-                // neighbour on the other parity: p == 0 needs q-1 (lane-1, wraps to block r-1),
-                // p == 1 needs q+1 (lane+1, wraps to block r+1)
-                int32_t nM, nI, nD;
-                if (p == 0) {
-                    nM = __shfl_up_sync(kFull, M1[r], 1);
-                    nI = __shfl_up_sync(kFull, I1[r], 1);
-                    nD = __shfl_up_sync(kFull, D1[r], 1);
-                    const int32_t wM = __shfl_sync(kFull, r > 0 ? M1[r > 0 ? r - 1 : 0] : kInf, 31);
-                    const int32_t wI = __shfl_sync(kFull, r > 0 ? I1[r > 0 ? r - 1 : 0] : kInf, 31);
-                    const int32_t wD = __shfl_sync(kFull, r > 0 ? D1[r > 0 ? r - 1 : 0] : kInf, 31);
-                    if (lane == 0) { nM = wM; nI = wI; nD = wD; }
+                // neighbour slot on the other parity: P == 0 needs q-1 (lane-1, wrapping to block r-1),
+                // P == 1 needs q+1 (lane+1, wrapping to block r+1)
+                int32_t nM, nI = kInf, nD = kInf;
+                if (P == 0) {
+                    nM = __shfl_up_sync(kFull, Ms[1][r], 1);
+                    if (!UNIT) { nI = __shfl_up_sync(kFull, Is[1][r], 1); nD = __shfl_up_sync(kFull, Ds[1][r], 1); }
+                    if constexpr (R > 1) {
+                        const int rr = r > 0 ? r - 1 : 0;
+                        const int32_t wM = __shfl_sync(kFull, r > 0 ? Ms[1][rr] : kInf, 31);
+                        int32_t wI = kInf, wD = kInf;
+                        if (!UNIT) {
+                            wI = __shfl_sync(kFull, r > 0 ? Is[1][rr] : kInf, 31);
+                            wD = __shfl_sync(kFull, r > 0 ? Ds[1][rr] : kInf, 31);
+                        }
+                        if (lane == 0) { nM = wM; nI = wI; nD = wD; }
+                    } else if (lane == 0) {
+                        nM = kInf; nI = kInf; nD = kInf;
+                    }
                 } else {
-                    nM = __shfl_down_sync(kFull, M0[r], 1);
-                    nI = __shfl_down_sync(kFull, I0[r], 1);
-                    nD = __shfl_down_sync(kFull, D0[r], 1);
-                    const int32_t wM = __shfl_sync(kFull, r + 1 < R ? M0[r + 1 < R ? r + 1 : r] : kInf, 0);
-                    const int32_t wI = __shfl_sync(kFull, r + 1 < R ? I0[r + 1 < R ? r + 1 : r] : kInf, 0);
-                    const int32_t wD = __shfl_sync(kFull, r + 1 < R ? D0[r + 1 < R ? r + 1 : r] : kInf, 0);
-                    if (lane == 31) { nM = wM; nI = wI; nD = wD; }
+                    nM = __shfl_down_sync(kFull, Ms[0][r], 1);
+                    if (!UNIT) { nI = __shfl_down_sync(kFull, Is[0][r], 1); nD = __shfl_down_sync(kFull, Ds[0][r], 1); }
+                    if constexpr (R > 1) {
+                        const int rr = r + 1 < R ? r + 1 : r;
+                        const int32_t wM = __shfl_sync(kFull, r + 1 < R ? Ms[0][rr] : kInf, 0);
+                        int32_t wI = kInf, wD = kInf;
+                        if (!UNIT) {
+                            wI = __shfl_sync(kFull, r + 1 < R ? Is[0][rr] : kInf, 0);
+                            wD = __shfl_sync(kFull, r + 1 < R ? Ds[0][rr] : kInf, 0);
+                        }
+                        if (lane == 31) { nM = wM; nI = wI; nD = wD; }
+                    } else if (lane == 31) {
+                        nM = kInf; nI = kInf; nD = kInf;
+                    }
                 }
-                // diagonal predecessor = own slot of parity p; up = q+1, left = q-1
-                const int32_t dM = p ? M1[r] : M0[r], dI = p ? I1[r] : I0[r], dD = p ? D1[r] : D0[r];
-                const int32_t uM = p ? nM : M1[r], uI = p ? nI : I1[r], uD = p ? nD : D1[r];
-                const int32_t lM = p ? M0[r] : nM, lI = p ? I0[r] : nI, lD = p ? D0[r] : nD;
-
+                // diagonal predecessor = own slot of parity P; up = q+1, left = q-1
+                const int32_t dM = Ms[P][r], dI = Is[P][r], dD = Ds[P][r];
+                const int32_t uM = P ? nM : Ms[1][r], uI = P ? nI : Is[1][r], uD = P ? nD : Ds[1][r];
+                const int32_t lM = P ? Ms[0][r] : nM, lI = P ? Is[0][r] : nI, lD = P ? Ds[0][r] : nD;
                 int32_t Mv = kInf, Iv = kInf, Dv = kInf;
-                uint32_t bits = 0;
-                if (valid) {
+                if (d >= dlo[P][r] && d <= dhi[P][r]) {
+                    const int k = 2 * (32 * r + (int)lane) + P - b;
+                    const int v = (d - k) >> 1, h = (d + k) >> 1;
+                    uint32_t bits = 0;
                     if (v >= 1 && h >= 1) {
-                        const int32_t delta = base_at(Pw, v - 1) == base_at(Tw, h - 1) ? 0 : x;
-                        const int32_t Hd = min3(dM, dI, dD);
-                        Mv = cap_inf(Hd + delta);
-                        if (Mv < kInf) {
-                            if (UNIT) bits |= 1u;
-                            else bits |= (dM + delta == Mv ? 1u : 0u) | (dI + delta == Mv ? 2u : 0u) |
-                                         (dD + delta == Mv ? 4u : 0u);
+                        const int iv = v - 1, ih = h - 1;
+                        if ((iv >> 5) != pwi[P][r]) { pwi[P][r] = iv >> 5; pw[P][r] = __ldg(Pw + (iv >> 5)); }
+                        if ((ih >> 5) != twi[P][r]) { twi[P][r] = ih >> 5; tw[P][r] = __ldg(Tw + (ih >> 5)); }
+                        const uint32_t pb = (uint32_t)(pw[P][r] >> (62 - 2 * (iv & 31))) & 3u;
+                        const uint32_t tb = (uint32_t)(tw[P][r] >> (62 - 2 * (ih & 31))) & 3u;
+                        const int32_t delta = pb == tb ? 0 : x;
+                        if (UNIT) {
+                            Mv = cap_inf(dM + delta);
+                        } else {
+                            Mv = cap_inf(min3(dM, dI, dD) + delta);
+                            if (Mv < kInf)
+                                bits |= (dM + delta == Mv ? 1u : 0u) | (dI + delta == Mv ? 2u : 0u) |
+                                        (dD + delta == Mv ? 4u : 0u);
                         }
                     }
                     if (v >= 1) {
                         if (UNIT) {
-                            Iv = cap_inf(min3(uM, uI, uD) + 1);
+                            Iv = cap_inf(uM + 1);
                         } else {
                             Iv = cap_inf(min3(uM + oe, uD + oe, uI + e));
                             if (Iv < kInf)
@@ -163,7 +197,7 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                     }
                     if (h >= 1) {
                         if (UNIT) {
-                            Dv = cap_inf(min3(lM, lI, lD) + 1);
+                            Dv = cap_inf(lM + 1);
                         } else {
                             Dv = cap_inf(min3(lM + oe, lI + oe, lD + e));
                             if (Dv < kInf)
@@ -178,15 +212,30 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                                (Dv == H && H < kInf ? 4u : 0u);
                         Mv = H; Iv = kInf; Dv = kInf;
                     }
-                    trace[(size_t)d * RW + i] = (TB)bits;
+                    trow[32 * r + lane] = (TB)bits;
                     ++st_cells;
                     over = over && min3(Mv, Iv, Dv) > limc;
                 }
-                if (p) { M1[r] = Mv; I1[r] = Iv; D1[r] = Dv; } else { M0[r] = Mv; I0[r] = Iv; D0[r] = Dv; }
+                Ms[P][r] = Mv; Is[P][r] = Iv; Ds[P][r] = Dv;
             }
-            const bool all_over = __all_sync(kFull, over);
-            if (all_over && prev_over) { rejected = true; break; }
-            prev_over = all_over;
+            return __all_sync(kFull, over);
+        };
+        using P0 = std::integral_constant<int, 0>;
+        using P1 = std::integral_constant<int, 1>;
+        int d = 1;
+        if (d <= dend && ((d + b) & 1)) {   // start on parity 1 so the loop below alternates 0, 1
+            const bool o = step(d, P1{});
+            prev_over = o;
+            ++d;
+        }
+        for (; d <= dend && !rejected; d += 2) {
+            bool o = step(d, P0{});
+            if (o && prev_over) { rejected = true; break; }
+            prev_over = o;
+            if (d + 1 > dend) break;
+            o = step(d + 1, P1{});
+            if (o && prev_over) { rejected = true; break; }
+            prev_over = o;
         }
         if (rejected) {
             if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
@@ -197,7 +246,9 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
         int32_t eM = kInf, eI = kInf, eD = kInf;
 #pragma unroll
         for (int r = 0; r < R; ++r)
-            if (r == re) { eM = pe ? M1[r] : M0[r]; eI = pe ? I1[r] : I0[r]; eD = pe ? D1[r] : D0[r]; }
+            if (r == re) {
+                eM = pe ? Ms[1][r] : Ms[0][r]; eI = pe ? Is[1][r] : Is[0][r]; eD = pe ? Ds[1][r] : Ds[0][r];
+            }
         eM = __shfl_sync(kFull, eM, je); eI = __shfl_sync(kFull, eI, je); eD = __shfl_sync(kFull, eD, je);
         const int32_t s = min3(eM, eI, eD);
         if (s > limc) {

@@ -474,14 +474,16 @@ int aim_server_submit(aim_server* s, const aim_request* q, uint64_t* ticket) {
         job.begin = i; job.count = j - i;
         job.plan = plan_wfa(s->costs, s->pen.band, jl, (int64_t)jme * ecost);
         job.group = wfa_default_group(job.plan, jl);
-        job.warp_bytes = (size_t)(32 / job.group) * job.plan.group_bytes;
-        if (job.warp_bytes > s->scratch.size() / 8 && job.group < 32) {   // one pair per warp when scratch is scarce
+        job.warp_bytes = wfa_warp_bytes(job.group, job.plan.group_bytes);
+        if (job.warp_bytes > s->scratch.size() / 64 && job.group < 32) {   // one pair per warp when scratch is scarce
             job.group = 32;
             job.warp_bytes = job.plan.group_bytes;
         }
-        const size_t P = 32 / job.group;
-        job.warps = std::min<size_t>((job.count + P - 1) / P, (size_t)s->warps_cap);
-        r->scratch_min = std::max(r->scratch_min, job.warp_bytes);
+        // warps wanted: every pair in flight at once (a 256-lane group uses 8 warps), within the device's capacity
+        const size_t want = job.group > 32 ? (size_t)job.count * (job.group / 32)
+                                           : (job.count + (32 / job.group) - 1) / (size_t)(32 / job.group);
+        job.warps = std::min<size_t>((want + 7) / 8 * 8, (size_t)s->warps_cap);
+        r->scratch_min = std::max(r->scratch_min, 8 * job.warp_bytes);   // launches use whole blocks
         r->scratch_want = std::max(r->scratch_want, job.warps * job.warp_bytes);
         r->jobs.push_back(job);
         i = j;

@@ -2,6 +2,8 @@
 // traceback.  A group of G lanes (G = 1, 2, 4, 8, 16 or 32) aligns one pair; a warp
 // runs 32/G pairs in lockstep over the score loop, so the per-score work of
 // one pair is shared by G lanes and the warp-uniform bookkeeping by 32/G pairs.
+// For very wide wavefronts (long, noisy pairs) a whole block of 256 threads
+// aligns one pair (G = 256), with block barriers in place of warp votes.
 //
 // Scores run in units of g = gcd(x, o, e) (every path cost is a sum of x,
 // o+e and e, so every reachable score is a multiple of g): X = x/g,
@@ -114,6 +116,69 @@ __device__ __forceinline__ int match_run_back(const uint64_t* Pw, uint32_t nwP, 
 
 enum : int { kRun = 0, kDone = 1, kRejected = 2, kCap = 3, kBad = 4, kIdle = 5 };
 
+// Collectives of one group.  G <= 32: a warp holds 32/G groups that run in lockstep, so loop
+// conditions are warp-wide and group results come from masked ballots and butterflies.  G == 256:
+// the whole block is one group and block barriers carry the same results.
+template <int G, bool BLOCK = (G > 32)>
+struct Group;
+
+template <int G>
+struct Group<G, false> {
+    int gl, leader;
+    uint32_t gmask;
+    __device__ explicit Group(uint32_t lane) {
+        gl = (int)lane % G;
+        leader = (int)lane - gl;
+        gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader);
+    }
+    __device__ int index(uint32_t lane) const { return (int)lane / G; }
+    __device__ bool any_running(bool x) const { return __any_sync(kFull, x); }
+    __device__ int iterations(int w) const { return (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G)); }
+    __device__ void min_max(int& lo, int& hi) const {
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+    }
+    __device__ bool group_any(bool x) const { return (__ballot_sync(kFull, x) & gmask) != 0; }
+    __device__ int bcast(int x) const { return __shfl_sync(kFull, x, leader); }
+    __device__ void sync() const { __syncwarp(); }
+};
+
+template <int G>
+struct Group<G, true> {
+    int gl, leader;
+    __device__ explicit Group(uint32_t) { gl = (int)threadIdx.x; leader = 0; }
+    __device__ int index(uint32_t) const { return 0; }
+    __device__ bool any_running(bool x) const { return __syncthreads_or(x) != 0; }
+    __device__ int iterations(int w) const { return (w + G - 1) / G; }   // w is block-uniform
+    __device__ void min_max(int& lo, int& hi) const {
+        __shared__ int s_lo, s_hi;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+            hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+        }
+        if (threadIdx.x == 0) { s_lo = 1 << 30; s_hi = -(1 << 30); }
+        __syncthreads();
+        if ((threadIdx.x & 31) == 0) { atomicMin(&s_lo, lo); atomicMax(&s_hi, hi); }
+        __syncthreads();
+        lo = s_lo; hi = s_hi;
+        __syncthreads();
+    }
+    __device__ bool group_any(bool x) const { return __syncthreads_or(x) != 0; }
+    __device__ int bcast(int x) const {
+        __shared__ int s_v;
+        if (threadIdx.x == 0) s_v = x;
+        __syncthreads();
+        const int r = s_v;
+        __syncthreads();
+        return r;
+    }
+    __device__ void sync() const { __syncthreads(); }
+};
+
 struct Counters {
     unsigned long long cells, windows, pairs;
 };
@@ -123,10 +188,10 @@ struct Counters {
 template <int G>
 __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
                              Counters& st) {
-    constexpr int P = 32 / G;
-    const int g = (int)lane / G, gl = (int)lane % G, leader = g * G;
-    const uint32_t gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader);
-    const size_t group_bytes = (a.warp_bytes / P) & ~(size_t)15;
+    const Group<G> grp(lane);
+    const int g = grp.index(lane), gl = grp.gl;
+    const size_t group_bytes =
+        G > 32 ? a.warp_bytes * (size_t)(G / 32) : (a.warp_bytes / (size_t)(32 / (G > 32 ? 32 : G))) & ~(size_t)15;
     uint8_t* slot = warp_slot + (size_t)g * group_bytes;
     int* meta = reinterpret_cast<int*>(slot);
     uint32_t* staged = reinterpret_cast<uint32_t*>(slot + a.meta_bytes);
@@ -174,15 +239,15 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
         found0 = (kend == 0 && m0 >= m);
     }
-    found0 = __shfl_sync(kFull, found0, leader);
+    found0 = grp.bcast(found0);
     if (status == kRun) {
         top = 3;
         if (found0) status = kDone;
     }
-    __syncwarp();
+    grp.sync();
 
     int s = 0;
-    while (__any_sync(kFull, status == kRun)) {
+    while (grp.any_running(status == kRun)) {
         ++s;
         bool run = status == kRun;
         if (run && s > S) { status = kRejected; run = false; }
@@ -198,7 +263,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
             w = lo <= hi ? hi - lo + 1 : 0;
             if (w && (size_t)top + 3 * (size_t)w > hist_cap) { status = kCap; run = false; w = 0; }
         }
-        const int iters = (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G));
+        const int iters = grp.iterations(w);
         bool hit = false;
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
@@ -223,22 +288,17 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 if (f0 >= 0 || ins >= 0 || del >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
             }
         }
-        // group-wide trimmed range (butterfly inside the group's lanes)
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            vlo = min(vlo, __shfl_xor_sync(kFull, vlo, o));
-            vhi = max(vhi, __shfl_xor_sync(kFull, vhi, o));
-        }
-        const uint32_t hits = __ballot_sync(kFull, hit);
+        grp.min_max(vlo, vhi);   // group-wide trimmed range
+        const bool group_hit = grp.group_any(hit);
         if (run) {
             if (gl == 0) {
                 const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
                 reinterpret_cast<int4*>(meta)[s] = rec;
             }
             top += 3 * w;
-            if (hits & gmask) { status = kDone; final_s = s; }
+            if (group_hit) { status = kDone; final_s = s; }
         }
-        __syncwarp();
+        grp.sync();
     }
 
     // canonical traceback on each group's first lane; every step issues the loads of all four tight
@@ -290,9 +350,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         nruns = wr.n;
         ok = ok && wr.n <= wr.cap;
     }
-    __syncwarp();
-    nruns = __shfl_sync(kFull, nruns, leader);
-    ok = __shfl_sync(kFull, ok, leader);
+    grp.sync();
+    nruns = (uint32_t)grp.bcast((int)nruns);
+    ok = grp.bcast(ok ? 1 : 0) != 0;
     if (status == kDone) {
         const int32_t score = final_s * a.g;
         uint8_t flags = ok ? 0 : AIM_F_STEP_CAP;
@@ -315,15 +375,29 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
 
 template <int G>
 __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
-    constexpr int P = 32 / G;
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
-    for (;;) {
-        uint32_t pos = 0;
-        if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
-        pos = __shfl_sync(kFull, pos, 0);
-        if (pos >= end - begin || end <= begin) break;
-        align_groups<G>(a, warp_slot, begin + pos, end, lane, st);
+    if constexpr (G > 32) {
+        // the whole block takes one pair at a time; its warps' scratch regions form the pair's slot
+        __shared__ uint32_t s_pos;
+        uint8_t* block_slot = a.scratch + (size_t)blockIdx.x * (blockDim.x / 32) * a.warp_bytes;
+        for (;;) {
+            if (threadIdx.x == 0) s_pos = atomicAdd(a.counters + b, 1u);
+            __syncthreads();
+            const uint32_t pos = s_pos;
+            __syncthreads();
+            if (pos >= end - begin || end <= begin) break;
+            align_groups<G>(a, block_slot, begin + pos, end, lane, st);
+        }
+    } else {
+        constexpr int P = 32 / G;
+        for (;;) {
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
+            pos = __shfl_sync(kFull, pos, 0);
+            if (pos >= end - begin || end <= begin) break;
+            align_groups<G>(a, warp_slot, begin + pos, end, lane, st);
+        }
     }
 }
 
@@ -344,7 +418,8 @@ __global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a)
             case 4: run_bucket<4>(a, b, warp_slot, lane, st); break;
             case 8: run_bucket<8>(a, b, warp_slot, lane, st); break;
             case 16: run_bucket<16>(a, b, warp_slot, lane, st); break;
-            default: run_bucket<32>(a, b, warp_slot, lane, st); break;
+            case 32: run_bucket<32>(a, b, warp_slot, lane, st); break;
+            default: run_bucket<256>(a, b, warp_slot, lane, st); break;
         }
     }
     warp_stat_add(a.O.stats, 0, st.cells, lane);
@@ -407,7 +482,7 @@ int wfa_default_group(const WfaPlan& p, uint32_t max_length) {
     int64_t w = 2 * (p.smax / std::max(p.e, 1)) + 1;
     w = std::min<int64_t>(w, 2 * (int64_t)max_length + 1);
     if (p.band >= 0) w = std::min<int64_t>(w, 2 * (int64_t)p.band + 1);
-    return w <= 64 ? 4 : w <= 128 ? 8 : w <= 256 ? 16 : 32;
+    return w <= 64 ? 4 : w <= 128 ? 8 : w <= 256 ? 16 : w <= 1024 ? 32 : 256;
 }
 
 cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const LimitView& L, const OutView& O,
@@ -428,25 +503,32 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
+    // whole blocks of 8 warps (a 256-lane group uses all of them)
     size_t warps = (size_t)num_sms * bps * 8;
     const size_t fit = scratch_bytes / warp_bytes;
     if (warps > fit) warps = fit;
-    if (warps == 0) return cudaSuccess;
     if (!bounds) {
-        const size_t P1 = (size_t)(32 / std::max(groups[0], 1));
-        const size_t need = (P.num_pairs + P1 - 1) / P1;
-        if (warps > need) warps = need;
+        const int g0 = groups[0];
+        const size_t need = g0 > 32 ? (size_t)P.num_pairs * (g0 / 32) : (P.num_pairs + (32 / g0) - 1) / (32 / g0);
+        if (warps > need) warps = (need + 7) / 8 * 8 <= fit ? (need + 7) / 8 * 8 : need;
     }
+    warps = warps / 8 * 8;
+    if (warps == 0) return cudaSuccess;
     a.nwarps = (uint32_t)warps;
     wfa_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
 }
 
+size_t wfa_warp_bytes(int group, size_t group_bytes) {
+    if (group > 32) return align_up((group_bytes + (size_t)(group / 32) - 1) / (size_t)(group / 32), 16);
+    return (size_t)(32 / group) * group_bytes;
+}
+
 cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const LimitView& L, const OutView& O,
                        uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
                        int* warps_used) {
-    const size_t warp_bytes = (size_t)(32 / group) * plan.group_bytes;
+    const size_t warp_bytes = wfa_warp_bytes(group, plan.group_bytes);
     return launch_wfa_buckets(plan, P, L, O, nullptr, nullptr, &group, 1, warp_bytes, scratch, scratch_bytes,
                               counter, num_sms, st, warps_used);
 }

@@ -97,8 +97,9 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
     const aim::WfaPlan plan = aim::plan_wfa(costs, pen->band, max_length, max_limit);
     const size_t capacity = kStaticScratchBytes - kStaticHeaderBytes;
     int group = aim::wfa_default_group(plan, max_length);
-    while (group < 32 && (size_t)(32 / group) * plan.group_bytes > capacity) group *= 2;
-    if ((size_t)(32 / group) * plan.group_bytes > capacity) return AIM_ERR_NOMEM;   // one pair's scratch is too big
+    while (group <= 32 && 8 * aim::wfa_warp_bytes(group, plan.group_bytes) > capacity)
+        group = group == 32 ? 256 : group * 2;
+    if (8 * aim::wfa_warp_bytes(group, plan.group_bytes) > capacity) return AIM_ERR_NOMEM;   // one pair is too big
 
     uint8_t* base = nullptr;
     int sms = 0;

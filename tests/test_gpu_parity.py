@@ -198,7 +198,7 @@ def test_results_independent_of_batch_composition(aligner, gen_lib):
         assert np.array_equal(shuf[2][j], full[2][i])
 
 
-@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32])
+@pytest.mark.parametrize("lanes", [1, 2, 4, 8, 16, 32, 256])
 def test_wfa_every_group_size_matches_oracle(aligner, oracle_lib, gen_lib, lanes):
     """Lanes per pair change only the schedule, never a result."""
     import paper_2208_01243_gb300 as aim
@@ -213,3 +213,22 @@ def test_wfa_every_group_size_matches_oracle(aligner, oracle_lib, gen_lib, lanes
     finally:
         aim.aim_set_wfa_group(aligner.ctx, 0)
     assert_same(dev, orc, what=f"wfa lanes={lanes}")
+
+
+LONG = gen.Workload("long_2000_4000bp_2_10pct", 6, 0, 2000, 4000, 0.02, 0.10, 0.0, "wfa", AFF, None,
+                    max_edits_frac=0.10)
+
+
+@pytest.mark.parametrize("lanes", [0, 32, 256])
+def test_long_reads_match_oracle(aligner, oracle_lib, gen_lib, lanes):
+    """Long, noisy pairs (2-4 kbp, up to 10 % edits): the default (block-wide groups) and warp groups agree with the oracle."""
+    import paper_2208_01243_gb300 as aim
+    p = gen.generate(LONG, 24)
+    me = gen.per_pair_max_edits(LONG, p)
+    orc = oracle_results(p, AFF, np.array([oracle.limit_for(AFF, int(k)) for k in me], np.int64))
+    aim.aim_set_wfa_group(aligner.ctx, lanes)
+    try:
+        dev = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    finally:
+        aim.aim_set_wfa_group(aligner.ctx, 0)
+    assert_same(dev, orc, what=f"long reads lanes={lanes}")
