@@ -303,7 +303,7 @@ def run_ours(args, w, algo):
 
         def step(src=None):
             aim.aim_batch_run(plan)
-        launches_per_step = 7          # 2 pack, bucket count/scan/scatter, alignment (+1 memset node)
+        launches_per_step = 6          # kernels per replay: 2 pack, bucket count/scan/scatter, alignment
     else:
         def step(src=None):
             src = src or d

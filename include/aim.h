@@ -176,7 +176,7 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
  *     first) and one persistent alignment launch that drains the buckets in
  *     that order are recorded as one CUDA graph;
  *   - with `autotune`, the lanes per pair of every non-empty bucket are chosen by
- *     timed trial launches on up to 16,384 of its pairs (each choice cached in
+ *     timed trial launches on a device-filling sample of its pairs (each choice cached in
  *     the context per costs, band and bucket); otherwise from the bucket's
  *     width class or an earlier cached choice.
  * Arguments are those of aim_align_batch_ascii (the same buffers are bound to

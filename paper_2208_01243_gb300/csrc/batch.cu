@@ -14,7 +14,7 @@
 // scatter into an order array), so a replay needs no host round trip.
 //
 // Autotuner.  For every non-empty bucket, timed trial launches on a sample of
-// up to 4,096 of its pairs try the group sizes that suit its width class (so
+// its pairs large enough to fill the device several times try the group sizes that suit its width class (so
 // that no lane walks more than about 64 diagonals per score step; the widest
 // class may also use a whole block per pair) and keep the fastest; choices are cached in the context per (costs, band, bucket).
 #include <algorithm>
@@ -203,7 +203,9 @@ int autotune(aim_batch* b) {
     for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
         const uint32_t count = b->host_counts[k];
         if (!count) continue;
-        const uint32_t sample = std::min<uint32_t>(count, 4096);
+        // a sample that fills the device several times over, so the trial measures throughput, not the
+        // latency of a handful of pairs
+        const uint32_t sample = std::min<uint32_t>(count, (uint32_t)std::max<size_t>(4096, 16 * min_warps * 4));
         const uint32_t tb[2] = {bounds[k], bounds[k] + sample};
         float best = 1e30f;
         int best_g = b->groups[k];

@@ -383,7 +383,7 @@ int aim_server_create(aim_ctx* ctx, const aim_penalties_t* pen, size_t wavefront
     s->scratch.reset(wavefront_budget_bytes);
     s->io.reset(io_budget_bytes);
     s->stage.reset(io_budget_bytes);
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {   // up to 32 requests in flight at once
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) s->streams.push_back(st);
     }
