@@ -232,3 +232,15 @@ def test_long_reads_match_oracle(aligner, oracle_lib, gen_lib, lanes):
     finally:
         aim.aim_set_wfa_group(aligner.ctx, 0)
     assert_same(dev, orc, what=f"long reads lanes={lanes}")
+
+
+@pytest.mark.parametrize("algo,pen,band", [("gotoh", (0, 3, 0, 4), -1),       # NW linear gap, x=3, e=4 (Section 2.4.1)
+                                           ("gotoh", (0, 3, 4, 1), -1),       # SWG, x=3, o=4, e=1 (Section 2.4.2)
+                                           ("wfa", (0, 3, 4, 1), -1)])        # WFA, x=3, o=4, e=1 (Section 2.4.4)
+def test_paper_cost_schemes(aligner, oracle_lib, gen_lib, algo, pen, band):
+    """The paper's own costs on 150 bp pairs at 4 % edits (max_edits 6)."""
+    p = gen.generate(gen.WFA_150BP, 5_003)
+    lim = np.full(len(p), oracle.limit_for(pen, 6), np.int64)
+    orc = oracle_results(p, pen, lim, band=band)
+    dev = device_results(p, algo, pen, 6, band=band, aligner=aligner)
+    assert_same(dev, orc, what=f"{algo} {pen}")
