@@ -211,9 +211,10 @@ AIM_API int aim_batch_destroy(aim_batch *batch);
  * wavefront scratch (wavefront_budget_bytes, 0: 4 GiB; the memory budget for
  * wavefront state, which never leaves the device).  A request's pairs are
  * grouped into jobs by their work bound (each job with its own scratch per
- * warp); an admitted request gets one scratch grant of up to half of the
- * budget and runs on its own stream (copy in, pack, one launch per job, copy
- * out), so requests that arrive while others run overlap on the device.  Results are those of
+ * warp); an admitted request gets one scratch grant of up to 1/16 of the
+ * budget, split between its jobs, and runs on its own streams (copy in, pack,
+ * one launch per job side by side, copy out), so its jobs and the requests
+ * that arrive while others run overlap on the device.  Results are those of
  * aim_align_batch_ascii for the same pairs, independent of what else runs.
  * aim_server_create allocates the arenas and starts the worker thread.
  */

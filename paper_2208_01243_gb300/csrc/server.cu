@@ -6,22 +6,26 @@
 // arrival order as soon as three fixed arenas have room for them:
 //   - pinned host staging (inputs out, results back),
 //   - device I/O (sequences, packed words, lengths, thresholds, results),
-//   - device wavefront scratch: the memory budget for wavefront state.
-// At submission a request's pairs are grouped into jobs by the bound on their
-// wavefront work (the bucket rule of the batched form), heaviest first; each
-// job gets its own plan, lanes per pair and scratch per warp, so short pairs
-// do not pay for the scratch of the longest one.  An admitted request receives
-// one scratch grant (what its jobs want, capped at half of the budget so
-// that other requests can run beside it, never less than one warp of its
-// heaviest job); a request whose heaviest pair would not fit even an empty
-// budget is refused at submission.  Every admitted request runs on its own
-// stream (H2D copy, 2-bit packing, one WFA launch per job, D2H copy), so the
-// work of requests that arrive while others run overlaps on the device;
-// wavefront state never leaves the device.  A host function enqueued behind the request's work stamps its
-// completion time and wakes the worker, which copies results to the caller's
-// buffers, releases the arenas (admitting waiting requests) and marks the
-// ticket done.  Each pair is aligned independently and deterministically, so
-// a request's results are the same alone and in any mix.
+//   - device wavefront scratch: the memory budget for wavefront state,
+// and enough streams are free for it.  At submission a request's pairs are
+// grouped into jobs by the bound on their wavefront work (the bucket rule of
+// the batched form), heaviest first; each job gets its own plan, lanes per
+// pair and scratch per warp, so short pairs do not pay for the scratch of the
+// longest one.  An admitted request receives one scratch grant (what its jobs
+// want, capped at 1/16 of the budget so that many requests share the device
+// at once, never less than one block of scratch for each of its jobs), split
+// between its jobs; a request whose heaviest pair would not fit even an empty
+// budget is refused at submission.  An admitted request holds its own streams:
+// one for the H2D copy and the 2-bit packing, then one per job (one WFA launch
+// each, on its slice of the grant), joined again for the copy back, so the
+// jobs of one request and the work of requests that arrive while others run
+// overlap on the device without waiting behind each other; wavefront state
+// never leaves the device.  A host function enqueued behind the request's work
+// stamps its completion time and wakes the worker, which copies results to
+// the caller's buffers, releases the arenas and streams (admitting waiting
+// requests) and marks the ticket done.  Each pair is aligned independently
+// and deterministically, so a request's results are the same alone and in any
+// mix.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -104,6 +108,7 @@ struct Request {
         int group;
         size_t warp_bytes;
         size_t warps;        // wanted
+        size_t slice_off, slice_bytes;   // its part of the request's scratch grant
     };
     std::vector<Job> jobs;
     // caller's output buffers
@@ -117,6 +122,8 @@ struct Request {
     // resources while admitted
     size_t io_off, host_off, scratch_off;
     cudaStream_t stream;
+    std::vector<cudaStream_t> job_streams;
+    std::vector<cudaEvent_t> events;    // [0]: inputs ready; [1 + j]: job j done
     Clock::time_point t_submit, t_done;
     bool done;
     int status;
@@ -175,7 +182,9 @@ struct aim_server {
     uint8_t* host_stage;
     aim::Arena io, scratch, stage;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> free_streams;
     size_t next_stream;
+    std::vector<cudaEvent_t> event_pool;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<aim::Request*> queue;
@@ -210,14 +219,28 @@ bool try_admit(aim_server* s, Request* r) {
     if (!s->io.alloc(r->io_bytes, &io_off)) return false;
     const IoLayout L = layout_of(*r);
     if (!s->stage.alloc(L.total, &host_off)) { s->io.release(io_off, r->io_bytes); return false; }
-    // one scratch grant for the request's jobs (they run one after another on its stream): as much as
-    // it wants up to half of the budget, never less than one warp of its heaviest job
-    const size_t cap = std::max(r->scratch_min, s->scratch.size() / 2);
+    // one scratch grant per request, split between its jobs (which run side by side on their own streams):
+    // what they want up to 1/16 of the budget (so that many requests share the device at once), never less
+    // than one block of scratch for each job
+    const size_t cap = std::max(r->scratch_min, s->scratch.size() / 16);
     const size_t grant = std::min(std::min(r->scratch_want, cap), s->scratch.largest());
     if (grant < r->scratch_min || !s->scratch.alloc(grant, &scr_off)) {
         s->io.release(io_off, r->io_bytes);
         s->stage.release(host_off, L.total);
         return false;
+    }
+    size_t extra_want = 0;
+    for (auto& j : r->jobs) extra_want += align_up(j.warps * j.warp_bytes, 256) - align_up(8 * j.warp_bytes, 256);
+    const size_t extra = grant - r->scratch_min;
+    size_t at = 0;
+    for (auto& j : r->jobs) {
+        const size_t lo = align_up(8 * j.warp_bytes, 256);
+        const size_t more = align_up(j.warps * j.warp_bytes, 256) - lo;
+        size_t give = extra_want ? (size_t)((double)extra * ((double)more / (double)extra_want)) : 0;
+        give = give / 256 * 256;
+        j.slice_off = at;
+        j.slice_bytes = lo + give;
+        at += j.slice_bytes;
     }
     r->io_off = io_off; r->host_off = host_off; r->scratch_off = scr_off;
     r->scratch_bytes = grant;
@@ -225,6 +248,12 @@ bool try_admit(aim_server* s, Request* r) {
 }
 
 void release(aim_server* s, Request* r) {
+    for (cudaEvent_t ev : r->events) if (ev) s->event_pool.push_back(ev);
+    r->events.clear();
+    if (r->stream) s->free_streams.push_back(r->stream);
+    for (cudaStream_t js : r->job_streams) s->free_streams.push_back(js);
+    r->stream = nullptr;
+    r->job_streams.clear();
     const IoLayout L = layout_of(*r);
     s->io.release(r->io_off, r->io_bytes);
     s->stage.release(r->host_off, L.total);
@@ -265,10 +294,13 @@ int launch_request(aim_server* s, Request* r) {
               r->out_cigars ? reinterpret_cast<const uint64_t*>(d + L.coff) : nullptr,
               reinterpret_cast<uint32_t*>(d + L.lens), d + L.flags, stats_of(s->ctx)};
     const uint32_t* order = reinterpret_cast<const uint32_t*>(d + L.order);
+    if (e == cudaSuccess) e = cudaEventRecord(r->events[0], st);
     for (size_t j = 0; j < r->jobs.size() && e == cudaSuccess; ++j) {
         const Request::Job& job = r->jobs[j];
+        cudaStream_t js = r->job_streams[j];
         uint32_t* counter = reinterpret_cast<uint32_t*>(d + L.counter) + j % 32;
-        e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+        e = cudaStreamWaitEvent(js, r->events[0], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), js);
         if (e != cudaSuccess) break;
         PairsView P{reinterpret_cast<const uint64_t*>(d + L.packed_r), reinterpret_cast<const uint64_t*>(d + L.packed_t),
                     nullptr, nullptr, reinterpret_cast<const uint32_t*>(d + L.rl),
@@ -276,8 +308,11 @@ int launch_request(aim_server* s, Request* r) {
         P.stride = L.stride;
         int warps = 0;
         e = launch_wfa_buckets(job.plan, P, lim, O, order + job.begin, nullptr, &job.group, 1, job.warp_bytes,
-                               s->dev_scratch + r->scratch_off, r->scratch_bytes, counter, s->num_sms, st, &warps);
+                               s->dev_scratch + r->scratch_off + job.slice_off, job.slice_bytes, counter, s->num_sms,
+                               js, &warps);
         if (e == cudaSuccess && warps == 0) e = cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaEventRecord(r->events[1 + j], js);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, r->events[1 + j], 0);
     }
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h + L.scores, d + L.scores, L.cigars + r->cigar_total * 4 - L.scores,
@@ -319,9 +354,23 @@ void worker_loop(aim_server* s) {
         // admissions, in arrival order
         while (!s->queue.empty()) {
             Request* r = s->queue.front();
+            if (s->free_streams.size() < r->jobs.size() + 1) break;   // a request holds its own streams
             if (!try_admit(s, r)) break;
             s->queue.pop_front();
-            r->stream = s->streams[s->next_stream++ % s->streams.size()];
+            r->stream = s->free_streams.back();
+            s->free_streams.pop_back();
+            r->job_streams.clear();
+            for (size_t j = 0; j < r->jobs.size(); ++j) {
+                r->job_streams.push_back(s->free_streams.back());
+                s->free_streams.pop_back();
+            }
+            r->events.clear();
+            for (size_t j = 0; j <= r->jobs.size(); ++j) {
+                cudaEvent_t ev = nullptr;
+                if (!s->event_pool.empty()) { ev = s->event_pool.back(); s->event_pool.pop_back(); }
+                else cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+                r->events.push_back(ev);
+            }
             s->running.push_back(r);
             lock.unlock();
             const int rc = launch_request(s, r);
@@ -383,10 +432,11 @@ int aim_server_create(aim_ctx* ctx, const aim_penalties_t* pen, size_t wavefront
     s->scratch.reset(wavefront_budget_bytes);
     s->io.reset(io_budget_bytes);
     s->stage.reset(io_budget_bytes);
-    for (int i = 0; i < 32; ++i) {   // up to 32 requests in flight at once
+    for (int i = 0; i < 128; ++i) {   // requests and their jobs spread over 128 streams
         cudaStream_t st;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess) s->streams.push_back(st);
     }
+    s->free_streams = s->streams;
     if (s->streams.empty()) { cudaFree(s->dev_scratch); cudaFree(s->dev_io); cudaFreeHost(s->host_stage); delete s;
                               return AIM_ERR_CUDA; }
     s->worker = std::thread(worker_loop, s);
@@ -483,12 +533,12 @@ int aim_server_submit(aim_server* s, const aim_request* q, uint64_t* ticket) {
         const size_t want = job.group > 32 ? (size_t)job.count * (job.group / 32)
                                            : (job.count + (32 / job.group) - 1) / (size_t)(32 / job.group);
         job.warps = std::min<size_t>((want + 7) / 8 * 8, (size_t)s->warps_cap);
-        r->scratch_min = std::max(r->scratch_min, 8 * job.warp_bytes);   // launches use whole blocks
-        r->scratch_want = std::max(r->scratch_want, job.warps * job.warp_bytes);
+        r->scratch_min += align_up(8 * job.warp_bytes, 256);   // launches use whole blocks
+        r->scratch_want += align_up(job.warps * job.warp_bytes, 256);
         r->jobs.push_back(job);
         i = j;
     }
-    if (r->jobs.size() > 32) return AIM_ERR_UNSUPPORTED;
+    if (r->jobs.size() > 32 || r->jobs.size() + 1 > s->streams.size()) return AIM_ERR_UNSUPPORTED;
     r->io_bytes = layout_of(*r).total;
     if (r->scratch_min > s->scratch.size() || r->io_bytes > s->io.size()) return AIM_ERR_NOMEM;
     r->done = false;
@@ -554,6 +604,7 @@ int aim_server_destroy(aim_server* s) {
     if (s->worker.joinable()) s->worker.join();
     aim::DeviceGuardImpl guard(s->ctx->device);
     for (cudaStream_t st : s->streams) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
+    for (cudaEvent_t ev : s->event_pool) cudaEventDestroy(ev);
     cudaFree(s->dev_scratch);
     cudaFree(s->dev_io);
     cudaFreeHost(s->host_stage);
