@@ -57,26 +57,29 @@ namespace aim {
 namespace {
 
 struct Wf {
-    int lo, hi, base, w;   // entries of diagonal k at base + c*w + k (base already offset by -lo); w == 0: empty
+    int lo, cnt, base, w;   // diagonals lo .. lo+cnt-1 (cnt == 0: empty); diagonal k of component c at
+                            // base + c*w + k (base already offset by -lo)
 };
 
 __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     Wf f;
-    if (s < 0) { f.lo = 1; f.hi = 0; f.base = 0; f.w = 0; return f; }
+    if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
     const int4 q = reinterpret_cast<const int4*>(meta)[s];
-    f.lo = q.x; f.hi = q.y; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y >= q.x ? q.y - q.x + 1 : 0; f.base = q.z; f.w = q.w;
     return f;
 }
 
+__device__ __forceinline__ int wf_hi(const Wf& f) { return f.lo + f.cnt - 1; }
+
 // component c (0 M, 1 I, 2 D) of wavefront f at diagonal k, or a negative value
 __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, int k) {
-    if (k < f.lo || k > f.hi) return kNeg16;
+    if ((unsigned)(k - f.lo) >= (unsigned)f.cnt) return kNeg16;   // one compare covers both ends and empty
     return hist[f.base + c * f.w + k];
 }
 
 // furthest offset reached from (h - k, h) along matches on diagonal k
 __device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, const uint64_t* Tw, uint32_t nwT,
-                                      int m, int k, int h, unsigned long long& windows) {
+                                      int m, int k, int h, uint32_t& windows) {
     int v = h - k;
     while (v < n && h < m) {
         ++windows;
@@ -233,7 +236,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     int top = 0, final_s = 0;
     int found0 = 0;
     if (status == kRun && gl == 0) {
-        const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, st.windows);
+        uint32_t w0 = 0;
+        const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, w0);
+        st.windows += w0;
         ++st.cells;
         hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16;
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
@@ -256,9 +261,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         if (run) {
             fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
             lo = 1 << 30; hi = -(1 << 30);
-            if (fx.w) { lo = min(lo, fx.lo); hi = max(hi, fx.hi); }
-            if (fo.w) { lo = min(lo, fo.lo - 1); hi = max(hi, fo.hi + 1); }
-            if (fe.w) { lo = min(lo, fe.lo - 1); hi = max(hi, fe.hi + 1); }
+            if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
+            if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
+            if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
             w = lo <= hi ? hi - lo + 1 : 0;
             if (w && (size_t)top + 3 * (size_t)w > hist_cap) { status = kCap; run = false; w = 0; }
@@ -267,6 +272,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         bool hit = false;
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
+        uint32_t n_cells = 0, n_windows = 0;
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
             if (run && k <= hi) {
@@ -278,16 +284,18 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 int mis = wf_get(hist, fx, 0, k);
                 mis = mis >= 0 ? mis + 1 : kNeg16;
                 if (mis > m || mis - k > n) mis = kNeg16;
-                const int f0 = max(mis, max(ins, del));
-                const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, st.windows) : kNeg16;
-                ++st.cells;
+                const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
+                const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, n_windows) : kNeg16;
+                ++n_cells;
                 hist[base + k] = (int16_t)mv;
                 hist[base + w + k] = (int16_t)ins;
                 hist[base + 2 * w + k] = (int16_t)del;
                 hit |= (k == kend && mv >= m);
-                if (f0 >= 0 || ins >= 0 || del >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
+                if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
             }
         }
+        st.cells += n_cells;
+        st.windows += n_windows;
         grp.min_max(vlo, vhi);   // group-wide trimmed range
         const bool group_hit = grp.group_any(hit);
         if (run) {
