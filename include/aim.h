@@ -14,8 +14,11 @@
  *   AIM_ALGO_GOTOH_BANDED  gap-affine global DP with three tables M, I, D
  *                          (Section 2.4.2, "SWG"; read as global alignment), banded.
  *   AIM_ALGO_WFA_AFFINE    gap-affine wavefront algorithm (Section 2.4.4), exact.
- * All three compute the same exact optimum for the same costs; the CIGAR is
- * the canonical one (below), so they agree bit for bit.
+ *   AIM_ALGO_WFA_ADAPTIVE  WFA-adaptive (Section 2.4.4: prunes outer diagonals unlikely
+ *                          to lead to an optimal alignment), a heuristic; see
+ *                          aim_set_wfa_adaptive for the rule and its CIGAR.
+ * The three exact algorithms compute the same optimum for the same costs; the
+ * CIGAR is the canonical one (below), so they agree bit for bit.
  *
  * Conventions (the paper fixes none of these; they are this library's):
  *   - Read P[0..n) is the query, target T[0..m) the reference.  Op M/'='
@@ -79,7 +82,12 @@ enum {
     AIM_F_STEP_CAP = 8         /* internal bound hit (scratch exhausted); no result */
 };
 
-typedef enum { AIM_ALGO_EDIT_NW = 0, AIM_ALGO_GOTOH_BANDED = 1, AIM_ALGO_WFA_AFFINE = 2 } aim_algo_t;
+typedef enum {
+    AIM_ALGO_EDIT_NW = 0,
+    AIM_ALGO_GOTOH_BANDED = 1,
+    AIM_ALGO_WFA_AFFINE = 2,
+    AIM_ALGO_WFA_ADAPTIVE = 3   /* heuristic: see aim_set_wfa_adaptive */
+} aim_algo_t;
 
 typedef struct {
     int32_t match;      /* must be 0 (the wavefront algorithm needs it; Section 2.4.4 uses a=0) */
@@ -167,6 +175,20 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
                           const int32_t *max_edits_per_pair, int32_t *out_scores, uint32_t *out_cigars,
                           const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
                           aim_stream_t stream);
+
+/*
+ * WFA-adaptive parameters of a context (defaults 10 and 50; the paper gives
+ * none).  After wavefront s (unless the pair finished at s), if it spans at
+ * least min_length diagonals, each diagonal's distance to the end cell,
+ * max(n - v, m - h) at its furthest offset, is compared with the smallest,
+ * and outer diagonals (from both ends inward, up to the first one kept) more
+ * than max_distance behind are dropped.  The CIGAR of AIM_ALGO_WFA_ADAPTIVE
+ * follows the wavefront sources (mismatch, then I, then D for a match run's
+ * start; gap extension before gap opening), so it is a valid alignment of the
+ * reported score but not necessarily the canonical one; the score can exceed
+ * the optimum and a pair can be rejected when pruning loses the end cell.
+ */
+AIM_API int aim_set_wfa_adaptive(aim_ctx *ctx, int min_length, int max_distance);
 
 /*
  * Batched form (wavefront algorithm): pairs of uneven length and error rate

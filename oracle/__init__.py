@@ -8,7 +8,9 @@ and never imports it.
 Contents:
   aim_oracle.c  full-matrix 3-state DP (Gotoh; NW edit distance as the unit-cost
                 special case) with the canonical backward state-set traceback,
-                plus a textbook one-state Levenshtein (Sections 2.4.1, 2.4.2)
+                plus a textbook one-state Levenshtein (Sections 2.4.1, 2.4.2),
+                and the WFA-adaptive heuristic written out step by step
+                (Section 2.4.4; exact WFA when pruning is off)
   brute.py      brute-force enumeration of every op string on tiny pairs
   cigar.py      decode / re-cost / reconstruct helpers for CIGAR runs
   pack.py       the 2-bit layout written out per base (pins the device packer)
@@ -66,6 +68,11 @@ def _load():
         lib.oracle_levenshtein.restype = i32
         lib.oracle_align_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, p, p, p, p, p,
                                            ctypes.c_int]
+        lib.oracle_wfa_adaptive.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i32, i32, i32, i32, i64,
+                                            i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8), p, u32,
+                                            ctypes.POINTER(u32)]
+        lib.oracle_wfa_adaptive_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, i32, i32, p, p, p, p,
+                                                  p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -98,6 +105,49 @@ def align(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int = -1, li
     if r:
         raise RuntimeError(f"oracle_align failed: {r}")
     return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
+
+
+# WFA-adaptive parameters (the build's reading; the paper gives none): prune when a wavefront spans at
+# least ADAPT_MIN_LEN diagonals, dropping outer diagonals more than ADAPT_MAX_DIST behind the closest to the end.
+ADAPT_MIN_LEN = 10
+ADAPT_MAX_DIST = 50
+
+
+def wfa_adaptive(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int = -1, limit: int = 1 << 62,
+                 min_len: int = ADAPT_MIN_LEN, max_dist: int = ADAPT_MAX_DIST):
+    """One pair through the step-by-step WFA-adaptive (min_len < 0: no pruning) -> (score, flags, [runs])."""
+    lib = _load()
+    _, x, o, e = penalties
+    sc = ctypes.c_int32(); fl = ctypes.c_uint8(); nc = ctypes.c_uint32()
+    cap = len(read) + len(target) + 1
+    buf = np.zeros(cap, np.uint32)
+    r = lib.oracle_wfa_adaptive(bytes(read), len(read), bytes(target), len(target), x, o, e, band, limit, min_len,
+                                max_dist, ctypes.byref(sc), ctypes.byref(fl), ctypes.c_void_p(buf.ctypes.data), cap,
+                                ctypes.byref(nc))
+    if r:
+        raise RuntimeError(f"oracle_wfa_adaptive failed: {r}")
+    return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
+
+
+def wfa_adaptive_batch(pairs, penalties, limits: np.ndarray, band: int = -1, min_len: int = ADAPT_MIN_LEN,
+                       max_dist: int = ADAPT_MAX_DIST, threads: int | None = None):
+    """gen.Pairs through the WFA-adaptive -> (scores, flags, cigar_off, cigars, cigar_lens)."""
+    lib = _load()
+    n = len(pairs)
+    _, x, o, e = penalties
+    threads = threads or os.cpu_count() or 1
+    lim = np.ascontiguousarray(limits, dtype=np.int64)
+    scores = np.empty(n, np.int32); flags = np.empty(n, np.uint8); lens = np.zeros(n, np.uint32)
+    cap = pairs.read_len.astype(np.uint64) + pairs.target_len.astype(np.uint64) + 1
+    off = np.zeros(n + 1, np.uint64); off[1:] = np.cumsum(cap, dtype=np.uint64)
+    cig = np.zeros(int(off[-1]), np.uint32)
+    P = lambda a: ctypes.c_void_p(a.ctypes.data)
+    r = lib.oracle_wfa_adaptive_batch(P(pairs.reads), P(pairs.read_off), P(pairs.read_len), P(pairs.targets),
+                                      P(pairs.target_off), P(pairs.target_len), n, x, o, e, band, P(lim), min_len,
+                                      max_dist, P(scores), P(flags), P(cig), P(off), P(lens), threads)
+    if r:
+        raise RuntimeError(f"oracle_wfa_adaptive_batch failed: {r}")
+    return scores, flags, off, cig, lens
 
 
 def levenshtein(read: bytes, target: bytes) -> int:

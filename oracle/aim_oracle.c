@@ -210,3 +210,258 @@ int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32
     free(th);
     return j.err;
 }
+
+/* ---------------------------------------------------------------------------
+ * WFA-adaptive (Section 2.4.4: "a heuristic variant of WFA" that "reduces the
+ * number of the spanned diagonals by eliminating outer diagonals that are
+ * unlikely to lead to an optimal alignment").  The paper gives no parameters;
+ * this is the build's reading, written out step by step:
+ *
+ *   Scores run in units of g = gcd(x, o, e) (X = x/g, OE = (o+e)/g, E = e/g).
+ *   Wavefront s spans diagonals [lo_s, hi_s]; for each k in the candidate
+ *   range (one beyond the source ranges, clamped to [-n, m] and the band):
+ *     I[s,k] = max(M[s-OE,k+1], I[s-E,k+1])      dropped if it leaves the matrix
+ *     D[s,k] = max(M[s-OE,k-1], D[s-E,k-1]) + 1  dropped if it leaves the matrix
+ *     f0     = max(M[s-X,k] + 1, I[s,k], D[s,k]) (the mismatch candidate dropped likewise)
+ *     M[s,k] = f0 extended along matches
+ *   The wavefront's range becomes the diagonals holding a valid entry.  Done
+ *   when M[s, m-n] == m (before any pruning of that wavefront).  Otherwise,
+ *   if the range spans at least L_min diagonals, every diagonal's distance to
+ *   the end cell is max(n - v, m - h) at its M offset h (v = h - k); outer
+ *   diagonals (from both ends inward, up to the first one kept) whose distance
+ *   exceeds the smallest by more than D_max are removed.  L_min < 0: no
+ *   pruning (exact WFA).
+ *
+ *   Traceback follows the sources: in state M at offset h of (s, k) the
+ *   matches run back to f0; f0's source is taken in the order mismatch
+ *   candidate, I, D.  In state I (value h at (s, k)) an extension I[s-E,k+1]
+ *   == h is taken before an opening M[s-OE,k+1] == h; in state D likewise
+ *   with D[s-E,k-1] + 1 and M[s-OE,k-1] + 1.
+ *
+ * Pinned by: with pruning off the score equals the full-matrix DP optimum
+ * and the CIGAR re-costs to it (brute force and DP tests); with pruning the
+ * CIGAR is a valid alignment that re-costs to the reported score.
+ * --------------------------------------------------------------------------- */
+
+static int32_t gcd32(int32_t a, int32_t b) { while (b) { int32_t t = a % b; a = b; b = t; } return a < 0 ? -a : a; }
+
+typedef struct {
+    int32_t lo, hi;          /* lo > hi: empty */
+    int32_t *M, *I, *D;      /* indexed by k - lo */
+} wfa_front;
+
+#define WNEG (-(1 << 30))
+
+static int32_t wf_val(const wfa_front *F, int64_t s, int which, int32_t k) {
+    if (s < 0) return WNEG;
+    const wfa_front *f = &F[s];
+    if (f->lo > f->hi || k < f->lo || k > f->hi) return WNEG;
+    const int32_t *a = which == 0 ? f->M : which == 1 ? f->I : f->D;
+    return a[k - f->lo];
+}
+
+static int32_t wfa_extend_plain(const char *P, int32_t n, const char *T, int32_t m, int32_t k, int32_t h) {
+    int32_t v = h - k;
+    while (v < n && h < m && P[v] == T[h]) { ++v; ++h; }
+    return h;
+}
+
+int oracle_wfa_adaptive(const char *P, uint32_t un, const char *T, uint32_t um, int32_t x, int32_t o, int32_t e,
+                        int32_t band, int64_t limit, int32_t lmin, int32_t dmax, int32_t *score, uint8_t *flags,
+                        uint32_t *cigar, uint32_t cap, uint32_t *ncig) {
+    const int32_t n = (int32_t)un, m = (int32_t)um;
+    *score = -1; *flags = 0; *ncig = 0;
+    const int32_t kend = m - n;
+    if (band >= 0 && (kend > band || -kend > band)) { *flags = 1; return 0; }
+    int32_t g = gcd32(gcd32(x, o), e);
+    if (g <= 0) g = 1;
+    const int32_t X = x / g, OE = (o + e) / g, E = e / g;
+    int64_t trivial = ((int64_t)x * (n > m ? n : m) + o + (int64_t)e * (n > m ? n : m)) / g;
+    int64_t S = limit / g;
+    if (S > trivial) S = trivial;
+    const int32_t klo = band >= 0 ? (-n > -band ? -n : -band) : -n;
+    const int32_t khi = band >= 0 ? (m < band ? m : band) : m;
+    wfa_front *F = (wfa_front *)calloc((size_t)S + 1, sizeof(wfa_front));
+    if (!F) return -3;
+    int64_t s = 0, found = -1;
+    F[0].lo = F[0].hi = 0;
+    F[0].M = (int32_t *)malloc(sizeof(int32_t)); F[0].I = (int32_t *)malloc(sizeof(int32_t));
+    F[0].D = (int32_t *)malloc(sizeof(int32_t));
+    int rc = 0;
+    if (!F[0].M || !F[0].I || !F[0].D) { rc = -3; goto done; }
+    F[0].M[0] = wfa_extend_plain(P, n, T, m, 0, 0); F[0].I[0] = WNEG; F[0].D[0] = WNEG;
+    if (kend == 0 && F[0].M[0] >= m) found = 0;
+    for (s = 1; found < 0 && s <= S; ++s) {
+        int32_t lo = 1 << 30, hi = -(1 << 30);
+        const int64_t src[3] = {s - X, s - OE, s - E};
+        for (int j = 0; j < 3; ++j) {
+            if (src[j] < 0 || F[src[j]].lo > F[src[j]].hi) continue;
+            const int32_t grow = j == 0 ? 0 : 1;
+            if (F[src[j]].lo - grow < lo) lo = F[src[j]].lo - grow;
+            if (F[src[j]].hi + grow > hi) hi = F[src[j]].hi + grow;
+        }
+        if (lo < klo) lo = klo;
+        if (hi > khi) hi = khi;
+        F[s].lo = 1; F[s].hi = 0;
+        if (lo > hi) continue;
+        const int32_t w = hi - lo + 1;
+        int32_t *Mv = (int32_t *)malloc(sizeof(int32_t) * w), *Iv = (int32_t *)malloc(sizeof(int32_t) * w);
+        int32_t *Dv = (int32_t *)malloc(sizeof(int32_t) * w);
+        if (!Mv || !Iv || !Dv) { free(Mv); free(Iv); free(Dv); rc = -3; goto done; }
+        int32_t vlo = 1 << 30, vhi = -(1 << 30);
+        for (int32_t k = lo; k <= hi; ++k) {
+            int32_t ins = wf_val(F, s - OE, 0, k + 1), t = wf_val(F, s - E, 1, k + 1);
+            if (t > ins) ins = t;
+            if (ins >= 0 && ins - k > n) ins = WNEG;
+            int32_t del = wf_val(F, s - OE, 0, k - 1);
+            t = wf_val(F, s - E, 2, k - 1);
+            if (t > del) del = t;
+            del = del >= 0 ? del + 1 : WNEG;
+            if (del > m) del = WNEG;
+            int32_t mis = wf_val(F, s - X, 0, k);
+            mis = mis >= 0 ? mis + 1 : WNEG;
+            if (mis > m || mis - k > n) mis = WNEG;
+            int32_t f0 = mis;
+            if (ins > f0) f0 = ins;
+            if (del > f0) f0 = del;
+            Mv[k - lo] = f0 >= 0 ? wfa_extend_plain(P, n, T, m, k, f0) : WNEG;
+            Iv[k - lo] = ins; Dv[k - lo] = del;
+            if (f0 >= 0) { if (k < vlo) vlo = k; if (k > vhi) vhi = k; }
+            if (k == kend && Mv[k - lo] >= m) found = s;
+        }
+        if (vlo > vhi) { free(Mv); free(Iv); free(Dv); continue; }
+        if (found < 0 && lmin >= 0 && vhi - vlo + 1 >= lmin) {
+            /* distance of every valid diagonal to the end cell; drop outer ones too far behind the closest */
+            int64_t dmin = INT64_MAX;
+            for (int32_t k = vlo; k <= vhi; ++k) {
+                const int32_t h = Mv[k - lo];
+                if (h < 0) continue;
+                const int64_t dv = (int64_t)n - (h - k), dh = (int64_t)m - h;
+                const int64_t d = dv > dh ? dv : dh;
+                if (d < dmin) dmin = d;
+            }
+            int32_t a = vlo, b = vhi;
+            while (a <= b) {
+                const int32_t h = Mv[a - lo];
+                const int64_t dv = (int64_t)n - (h - a), dh = (int64_t)m - h, d = dv > dh ? dv : dh;
+                if (h >= 0 && d - dmin <= dmax) break;
+                ++a;
+            }
+            while (b >= a) {
+                const int32_t h = Mv[b - lo];
+                const int64_t dv = (int64_t)n - (h - b), dh = (int64_t)m - h, d = dv > dh ? dv : dh;
+                if (h >= 0 && d - dmin <= dmax) break;
+                --b;
+            }
+            vlo = a; vhi = b;
+        }
+        /* keep [vlo, vhi] */
+        const int32_t nw = vhi - vlo + 1;
+        F[s].lo = vlo; F[s].hi = vhi;
+        F[s].M = (int32_t *)malloc(sizeof(int32_t) * nw); F[s].I = (int32_t *)malloc(sizeof(int32_t) * nw);
+        F[s].D = (int32_t *)malloc(sizeof(int32_t) * nw);
+        if (!F[s].M || !F[s].I || !F[s].D) { free(Mv); free(Iv); free(Dv); rc = -3; goto done; }
+        memcpy(F[s].M, Mv + (vlo - lo), sizeof(int32_t) * nw);
+        memcpy(F[s].I, Iv + (vlo - lo), sizeof(int32_t) * nw);
+        memcpy(F[s].D, Dv + (vlo - lo), sizeof(int32_t) * nw);
+        free(Mv); free(Iv); free(Dv);
+        if (found >= 0) break;
+    }
+    if (found < 0) { *flags = 1; goto done; }
+    {
+        /* source-following traceback, ops collected end-first */
+        char *ops = (char *)malloc((size_t)n + m + 1);
+        if (!ops) { rc = -3; goto done; }
+        uint32_t nops = 0;
+        int state = 0; /* 0 M, 1 I, 2 D */
+        int64_t c = found;
+        int32_t k = kend, h = m;
+        for (;;) {
+            if (state == 0) {
+                if (c == 0 && k == 0) { while (h > 0) { ops[nops++] = 'M'; --h; } break; }
+                int32_t mis = wf_val(F, c - X, 0, k);
+                mis = mis >= 0 ? mis + 1 : WNEG;
+                if (mis > m || mis - k > n) mis = WNEG;
+                const int32_t ins = wf_val(F, c, 1, k), del = wf_val(F, c, 2, k);
+                int32_t f0 = mis;
+                if (ins > f0) f0 = ins;
+                if (del > f0) f0 = del;
+                if (f0 < 0 || f0 > h) { free(ops); rc = -5; goto done; }
+                while (h > f0) { ops[nops++] = 'M'; --h; }
+                if (f0 == mis) { ops[nops++] = 'X'; --h; c -= X; }
+                else if (f0 == ins) state = 1;
+                else state = 2;
+            } else if (state == 1) {
+                ops[nops++] = 'I';
+                if (wf_val(F, c - E, 1, k + 1) == h) { c -= E; }
+                else if (wf_val(F, c - OE, 0, k + 1) == h) { c -= OE; state = 0; }
+                else { free(ops); rc = -5; goto done; }
+                k += 1;
+            } else {
+                ops[nops++] = 'D';
+                if (wf_val(F, c - E, 2, k - 1) + 1 == h) { c -= E; }
+                else if (wf_val(F, c - OE, 0, k - 1) + 1 == h) { c -= OE; state = 0; }
+                else { free(ops); rc = -5; goto done; }
+                k -= 1; h -= 1;
+            }
+            if (nops > (uint32_t)(n + m)) { free(ops); rc = -5; goto done; }
+        }
+        *score = (int32_t)(found * g);
+        uint32_t runs = 0;
+        for (int64_t i = (int64_t)nops - 1; i >= 0;) {
+            char op = ops[i]; uint32_t len = 0;
+            while (i >= 0 && ops[i] == op) { ++len; --i; }
+            if (cigar && runs < cap) cigar[runs] = (len << 4) | bam_code(op);
+            ++runs;
+        }
+        *ncig = runs;
+        if (cigar && runs > cap) *flags |= 2;
+        free(ops);
+    }
+done:
+    for (int64_t t = 0; t <= S; ++t) { free(F[t].M); free(F[t].I); free(F[t].D); }
+    free(F);
+    return rc;
+}
+
+/* ---- batch driver for the adaptive WFA (same layout as oracle_align_batch) ---- */
+
+typedef struct {
+    batch_job base;
+    int32_t lmin, dmax;
+} adaptive_job;
+
+static void *adaptive_worker(void *arg) {
+    adaptive_job *aj = (adaptive_job *)arg;
+    batch_job *j = &aj->base;
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&j->next, 1, __ATOMIC_RELAXED);
+        if (i >= (int64_t)j->num_pairs) break;
+        uint32_t *cig = NULL, cap = 0;
+        if (j->cigars) { cig = j->cigars + j->cigar_off[i]; cap = (uint32_t)(j->cigar_off[i + 1] - j->cigar_off[i]); }
+        int r = oracle_wfa_adaptive(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
+                                    j->target_len[i], j->x, j->o, j->e, j->band, j->limit[i], aj->lmin, aj->dmax,
+                                    &j->scores[i], &j->flags[i], cig, cap, &j->cigar_lens[i]);
+        if (r) j->err = r;
+    }
+    return NULL;
+}
+
+int oracle_wfa_adaptive_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len,
+                              const char *targets, const uint64_t *target_off, const uint32_t *target_len,
+                              uint64_t num_pairs, int32_t x, int32_t o, int32_t e, int32_t band, const int64_t *limit,
+                              int32_t lmin, int32_t dmax, int32_t *scores, uint8_t *flags, uint32_t *cigars,
+                              const uint64_t *cigar_off, uint32_t *cigar_lens, int threads) {
+    adaptive_job aj = {{reads, targets, read_off, target_off, read_len, target_len, num_pairs, x, o, e, band, limit,
+                        scores, flags, cigars, cigar_off, cigar_lens, 0, 0}, lmin, dmax};
+    if (threads < 1) threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    if (!th) return -3;
+    int started = 0;
+    for (int t = 0; t < threads; ++t)
+        if (pthread_create(&th[t], NULL, adaptive_worker, &aj) == 0) ++started;
+    if (started == 0) adaptive_worker(&aj);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    return aj.base.err;
+}

@@ -17,8 +17,9 @@ from .build import LIB
 
 AIM_OK, AIM_ERR_ARG, AIM_ERR_INPUT, AIM_ERR_NOMEM, AIM_ERR_CUDA, AIM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 AIM_F_REJECTED, AIM_F_CIGAR_OVERFLOW, AIM_F_BAD_PAIR, AIM_F_STEP_CAP = 1, 2, 4, 8
-AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE = 0, 1, 2
-ALGO = {"edit": AIM_ALGO_EDIT_NW, "gotoh": AIM_ALGO_GOTOH_BANDED, "wfa": AIM_ALGO_WFA_AFFINE}
+AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE, AIM_ALGO_WFA_ADAPTIVE = 0, 1, 2, 3
+ALGO = {"edit": AIM_ALGO_EDIT_NW, "gotoh": AIM_ALGO_GOTOH_BANDED, "wfa": AIM_ALGO_WFA_AFFINE,
+        "wfa_adaptive": AIM_ALGO_WFA_ADAPTIVE}
 
 
 class aim_penalties_t(ctypes.Structure):
@@ -67,6 +68,7 @@ def _lib():
         lib.aim_wfa_align_static.argtypes = [p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p,
                                              p, p, p, p, p]
         lib.aim_set_wfa_group.argtypes = [p, ctypes.c_int]
+        lib.aim_set_wfa_adaptive.argtypes = [p, ctypes.c_int, ctypes.c_int]
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
@@ -269,6 +271,10 @@ def aim_server_stats(server) -> dict:
 
 def aim_server_destroy(server) -> None:
     _check(_lib().aim_server_destroy(server), "aim_server_destroy")
+
+
+def aim_set_wfa_adaptive(ctx, min_length: int = 10, max_distance: int = 50) -> None:
+    _check(_lib().aim_set_wfa_adaptive(ctx, int(min_length), int(max_distance)), "aim_set_wfa_adaptive")
 
 
 def aim_set_wfa_group(ctx, lanes: int) -> None:

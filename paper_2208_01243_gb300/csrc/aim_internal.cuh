@@ -120,6 +120,8 @@ struct WfaPlan {
     size_t meta_bytes;   // per-score (lo, hi, base, width) records, int4 each
     size_t runs_bytes;   // run staging
     size_t group_bytes;  // scratch of one pair in flight: meta + runs + history
+    int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
+    int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end
 };
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
 size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax);
@@ -144,6 +146,7 @@ struct WfaArgs {
     const uint32_t* bounds;    // bucket b covers queue positions [bounds[b], bounds[b+1]); null: one bucket of all
     uint32_t* counters;        // one claim counter per bucket, zero at launch
     int nbuckets;
+    int adapt_min_len, adapt_max_dist;   // WFA-adaptive pruning and source-following traceback (min_len < 0: off)
     int8_t group[kMaxBuckets]; // lanes per pair of each bucket
 };
 
@@ -244,6 +247,7 @@ struct aim_ctx {
     bool timing;
     aim::KernelTimes* times[2];   // 0: packer, 1: alignment kernels; created on first enable
     int wfa_group;                // lanes per pair for the WFA; 0: chosen from the plan
+    int adapt_min_len, adapt_max_dist;   // WFA-adaptive parameters
     void* tune_cache;             // autotuner choices (owned; see batch.cu)
 };
 

@@ -135,9 +135,13 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
     if (err != cudaSuccess) return cuda_status(err);
     int slot = -1;
-    if (algo == AIM_ALGO_WFA_AFFINE) {
+    if (algo == AIM_ALGO_WFA_AFFINE || algo == AIM_ALGO_WFA_ADAPTIVE) {
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
-        const aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
+        aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
+        if (algo == AIM_ALGO_WFA_ADAPTIVE) {
+            plan.adapt_min_len = ctx->adapt_min_len;
+            plan.adapt_max_dist = ctx->adapt_max_dist;
+        }
         int group = ctx->wfa_group ? ctx->wfa_group : aim::wfa_default_group(plan, P.max_length);
         // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
         while (group <= 32 && 8 * aim::wfa_warp_bytes(group, plan.group_bytes) > scratch_bytes)
@@ -172,7 +176,7 @@ bool common_args_ok(aim_ctx* ctx, const void* rl, const void* tl, uint32_t num_p
                     const aim_penalties_t* pen, int32_t* out_scores, uint32_t* out_cigars,
                     const uint64_t* cigar_offsets, uint8_t* out_flags) {
     if (!ctx || !pen) return false;
-    if (algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_WFA_AFFINE) return false;
+    if (algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_WFA_ADAPTIVE) return false;
     if (algo != AIM_ALGO_EDIT_NW && !penalties_ok(pen)) return false;
     if (algo == AIM_ALGO_EDIT_NW && pen->match != 0) return false;
     if (num_pairs == 0) return true;
@@ -225,6 +229,8 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     c->times[0] = c->times[1] = nullptr;
     c->wfa_group = 0;
     c->tune_cache = nullptr;
+    c->adapt_min_len = 10;
+    c->adapt_max_dist = 50;
     *out = c;
     return AIM_OK;
 }
@@ -249,6 +255,13 @@ int aim_set_wfa_group(aim_ctx* ctx, int lanes) {
                   lanes == 256))
         return AIM_ERR_ARG;
     ctx->wfa_group = lanes;
+    return AIM_OK;
+}
+
+int aim_set_wfa_adaptive(aim_ctx* ctx, int min_length, int max_distance) {
+    if (!ctx || min_length < 0 || max_distance < 0) return AIM_ERR_ARG;
+    ctx->adapt_min_len = min_length;
+    ctx->adapt_max_dist = max_distance;
     return AIM_OK;
 }
 

@@ -298,6 +298,33 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         st.windows += n_windows;
         grp.min_max(vlo, vhi);   // group-wide trimmed range
         const bool group_hit = grp.group_any(hit);
+        if (a.adapt_min_len >= 0) {
+            // WFA-adaptive: once the wavefront spans at least adapt_min_len diagonals, drop outer diagonals
+            // whose distance to the end cell, max(n - v, m - h), exceeds the smallest by more than adapt_max_dist
+            const bool prune = run && !group_hit && vlo <= vhi && vhi - vlo + 1 >= a.adapt_min_len;
+            int dmin = 1 << 30, dummy = -(1 << 30);
+            for (int it = 0; it < iters; ++it) {
+                const int k = lo + gl + it * G;
+                if (prune && k >= vlo && k <= vhi) {
+                    const int h = hist[base + k];
+                    if (h >= 0) dmin = min(dmin, max(n - (h - k), m - h));
+                }
+            }
+            grp.min_max(dmin, dummy);
+            int klo = 1 << 30, khi = -(1 << 30);
+            for (int it = 0; it < iters; ++it) {
+                const int k = lo + gl + it * G;
+                if (prune && k >= vlo && k <= vhi) {
+                    const int h = hist[base + k];
+                    if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
+                        klo = min(klo, k);
+                        khi = max(khi, k);
+                    }
+                }
+            }
+            grp.min_max(klo, khi);
+            if (prune) { vlo = klo; vhi = khi; }
+        }
         if (run) {
             if (gl == 0) {
                 const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
@@ -309,11 +336,55 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         grp.sync();
     }
 
-    // canonical traceback on each group's first lane; every step issues the loads of all four tight
-    // tests at once (two memory round trips per step instead of a chain of dependent ones)
+    // traceback on each group's first lane
     uint32_t nruns = 0;
     bool ok = true;
-    if (status == kDone && gl == 0) {
+    if (status == kDone && gl == 0 && a.adapt_min_len >= 0) {
+        // WFA-adaptive: follow the sources.  State M at offset h of (c, k): the matches run back to f0, whose
+        // source is the mismatch candidate, then I, then D; state I (value h): an extension I[c-E, k+1] == h
+        // before an opening M[c-OE, k+1] == h; state D likewise with D[c-E, k-1] + 1 and M[c-OE, k-1] + 1.
+        RunWriter wr;
+        wr.init(staged, a.runs_cap);
+        int state = 0, c = final_s, k = kend, h = m;
+        for (int guard = 0; ok; ++guard) {
+            if (guard > n + m + 1) { ok = false; break; }
+            if (state == 0) {
+                if (c == 0 && k == 0) { if (h > 0) wr.put(kOpMatch, (uint32_t)h); break; }
+                int mis = wf_get(hist, load_wf(meta, c - X), 0, k);
+                mis = mis >= 0 ? mis + 1 : kNeg16;
+                if (mis > m || mis - k > n) mis = kNeg16;
+                const Wf fc = load_wf(meta, c);
+                const int ins = wf_get(hist, fc, 1, k), del = wf_get(hist, fc, 2, k);
+                const int f0 = max(mis, max(ins, del));
+                if (f0 < 0 || f0 > h) { ok = false; break; }
+                if (h > f0) wr.put(kOpMatch, (uint32_t)(h - f0));
+                h = f0;
+                if (f0 == mis) { wr.put(kOpMismatch, 1); --h; c -= X; }
+                else if (f0 == ins) state = 1;
+                else state = 2;
+            } else if (state == 1) {
+                wr.put(kOpIns, 1);
+                if (wf_get(hist, load_wf(meta, c - E), 1, k + 1) == h) { c -= E; }
+                else if (wf_get(hist, load_wf(meta, c - OE), 0, k + 1) == h) { c -= OE; state = 0; }
+                else { ok = false; break; }
+                k += 1;
+            } else {
+                wr.put(kOpDel, 1);
+                const int ext = wf_get(hist, load_wf(meta, c - E), 2, k - 1);
+                const int opn = wf_get(hist, load_wf(meta, c - OE), 0, k - 1);
+                if (ext >= 0 && ext + 1 == h) { c -= E; }
+                else if (opn >= 0 && opn + 1 == h) { c -= OE; state = 0; }
+                else { ok = false; break; }
+                k -= 1; h -= 1;
+            }
+        }
+        wr.finish();
+        nruns = wr.n;
+        ok = ok && wr.n <= wr.cap;
+    }
+    // canonical traceback; every step issues the loads of all four tight tests at once (two memory round
+    // trips per step instead of a chain of dependent ones)
+    if (status == kDone && gl == 0 && a.adapt_min_len < 0) {
         const int* __restrict__ cmeta = meta;
         const int16_t* __restrict__ chist = hist;
         RunWriter wr;
@@ -482,6 +553,8 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     p.meta_bytes = align_up((size_t)(smax + 1) * 4 * sizeof(int), 16);
     p.runs_bytes = align_up((size_t)p.runs_cap * sizeof(uint32_t), 16);
     p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
+    p.adapt_min_len = -1;
+    p.adapt_max_dist = 0;
     return p;
 }
 
@@ -506,6 +579,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.scratch = scratch; a.warp_bytes = warp_bytes;
     a.meta_bytes = plan.meta_bytes; a.runs_bytes = plan.runs_bytes; a.runs_cap = (uint32_t)plan.runs_cap;
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
+    a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int8_t)(b < nbuckets ? groups[b] : 32);
     int bps = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel, 256, 0);

@@ -244,3 +244,42 @@ def test_paper_cost_schemes(aligner, oracle_lib, gen_lib, algo, pen, band):
     orc = oracle_results(p, pen, lim, band=band)
     dev = device_results(p, algo, pen, 6, band=band, aligner=aligner)
     assert_same(dev, orc, what=f"{algo} {pen}")
+
+
+def _adaptive_oracle(p, pen, lim, min_len, max_dist):
+    s, f, off, cig, lens = oracle.wfa_adaptive_batch(p, pen, lim, min_len=min_len, max_dist=max_dist)
+    return s, f, [cig[off[i]:off[i] + lens[i]].astype(np.uint32) for i in range(len(p))]
+
+
+@pytest.mark.parametrize("params", [(10, 50), (4, 5), (2, 1)])
+@pytest.mark.parametrize("lanes", [0, 4, 32, 256])
+def test_wfa_adaptive_matches_its_oracle(aligner, oracle_lib, gen_lib, params, lanes):
+    """WFA-adaptive (pruning + source-following traceback) equals the step-by-step CPU heuristic bit for bit."""
+    import paper_2208_01243_gb300 as aim
+    pu = gen.generate(gen.WFA_UNEVEN, 400)
+    ps = gen.generate(gen.WFA_150BP, 1_001)
+    p = gen.concat([pu, ps])
+    me = np.concatenate([gen.per_pair_max_edits(gen.WFA_UNEVEN, pu), np.full(len(ps), 6, np.int32)])
+    lim = np.array([oracle.limit_for(AFF, int(k)) for k in me], np.int64)
+    orc = _adaptive_oracle(p, AFF, lim, *params)
+    aim.aim_set_wfa_adaptive(aligner.ctx, *params)
+    aim.aim_set_wfa_group(aligner.ctx, lanes)
+    try:
+        dev = device_results(p, "wfa_adaptive", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    finally:
+        aim.aim_set_wfa_group(aligner.ctx, 0)
+        aim.aim_set_wfa_adaptive(aligner.ctx, 10, 50)
+    assert_same(dev, orc, what=f"wfa adaptive {params} lanes={lanes}")
+
+
+def test_wfa_adaptive_paper_costs_150bp(aligner, oracle_lib, gen_lib):
+    """The paper's Table 3 setting in shape: 150 bp, 2 % edits, costs x=3 o=4 e=1 (Section 2.4.4)."""
+    w = gen.Workload("wfa_adaptive_150bp_2pct", 7, 0, 150, 150, 0.02, 0.02, 0.0, "wfa_adaptive", (0, 3, 4, 1), 3)
+    p = gen.generate(w, 3_001)
+    pen = (0, 3, 4, 1)
+    lim = np.full(len(p), oracle.limit_for(pen, 3), np.int64)
+    orc = _adaptive_oracle(p, pen, lim, 10, 50)
+    dev = device_results(p, "wfa_adaptive", pen, 3, aligner=aligner)
+    assert_same(dev, orc, what="wfa adaptive 150bp paper costs")
+    exact = oracle_results(p, pen, lim)
+    assert (dev[0] == exact[0]).mean() > 0.99
