@@ -39,6 +39,13 @@ WORKLOADS = {"wfa_150bp": gen.WFA_150BP, "edit_nw_100bp": gen.EDIT_NW_100BP,
              "wfa_uneven_plain": gen.WFA_UNEVEN}
 ALGO_OF = {"wfa_150bp": "wfa", "edit_nw_100bp": "edit", "gotoh_250bp": "gotoh", "wfa_250bp": "wfa",
            "wfa_uneven": "wfa", "wfa_uneven_plain": "wfa"}
+# WFA-adaptive in the shapes of Table 3, with the UPMEM throughput the paper prints for each (alignments/s,
+# 2560 DPUs, host<->DPU transfer included)
+TABLE3_UPMEM = {(150, 2): 12.97e6, (150, 5): 7.03e6, (1000, 2): 1.10e6, (1000, 5): 434e3, (10000, 2): 66.9e3,
+                (10000, 5): 11.81e3}
+for (_len, _pct), _w in gen.TABLE3.items():
+    WORKLOADS[f"table3_{_len}bp_{_pct}pct"] = _w
+    ALGO_OF[f"table3_{_len}bp_{_pct}pct"] = "wfa_adaptive"
 
 # Algorithmic integer operations per unit of counted work (the roofline numerator):
 #   WFA wavefront entry: I~ one max, D~ one max + one add, mismatch candidate one add, f0 two max = 6
@@ -82,7 +89,7 @@ def runs_capacity(w, p, algo):
     me = gen.per_pair_max_edits(w, p).astype(np.int64)
     if algo == "edit":
         lim = me; minc = 1
-    else:
+    else:  # affine (exact or adaptive)
         lim = me * max(x, o + e); minc = min(x, o + e)
     cap = 2 * (lim // minc) + 1
     return np.minimum(cap, p.read_len.astype(np.int64) + p.target_len.astype(np.int64) + 1)
@@ -95,7 +102,7 @@ def config_of(name, w, n_pairs, algo):
          "unrelated_frac": w.unrelated_frac, "penalties": {"match": 0, "mismatch": w.penalties[1],
                                                           "gap_open": w.penalties[2], "gap_extend": w.penalties[3]},
          "max_edits": w.max_edits if w.max_edits is not None else f"ceil({w.max_edits_frac}*read_len)",
-         "band": w.band if algo != "wfa" or name == "wfa_250bp" else -1,
+         "band": w.band if algo not in ("wfa", "wfa_adaptive") or name == "wfa_250bp" else -1,
          "plain_form": "one launch per read-length group (8 log-spaced groups)" if name == "wfa_uneven" else None,
          "input": "ASCII pairs, 2-bit packed on device inside the step",
          "l2": "inputs larger than L2 (no flush needed)"}
@@ -173,18 +180,23 @@ def run_reference(args, w, algo):
         return 0
     oracle.build()
     cores = os.cpu_count() or 1
-    sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000}[algo]
+    sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000, "wfa_adaptive": 40_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 2_000
+    if algo == "wfa_adaptive":
+        sample = max(200, min(sample, 8_000_000 // max(w.len_max, 1)))
     pen = oracle.UNIT if algo == "edit" else w.penalties
-    band = w.band if algo != "wfa" or args.workload == "wfa_250bp" else -1
+    band = w.band if algo not in ("wfa", "wfa_adaptive") or args.workload == "wfa_250bp" else -1
     times = []
     for step in range(args.warmup + args.steps):
         p = gen.generate(w, sample, first=step * sample)
         me = gen.per_pair_max_edits(w, p)
         lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
         t0 = time.perf_counter()
-        oracle.align_batch(p, pen, lim, band=band, threads=cores)
+        if algo == "wfa_adaptive":
+            oracle.wfa_adaptive_batch(p, pen, lim, band=band, threads=cores)
+        else:
+            oracle.align_batch(p, pen, lim, band=band, threads=cores)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -207,19 +219,25 @@ def cpu_baseline(w, algo):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000}[algo]
+    sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000, "wfa_adaptive": 200_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 10_000
+    if algo == "wfa_adaptive":
+        sample = max(500, min(sample, 40_000_000 // max(w.len_max, 1)))
     p = gen.generate(w, sample)
     me = gen.per_pair_max_edits(w, p)
     lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
     pen = oracle.UNIT if algo == "edit" else w.penalties
     t0 = time.perf_counter()
-    oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores)
+    if algo == "wfa_adaptive":
+        oracle.wfa_adaptive_batch(p, pen, lim, threads=cores)
+        what = "step-by-step CPU WFA-adaptive"
+    else:
+        oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores)
+        what = "full-matrix DP + canonical traceback"
     dt = time.perf_counter() - t0
     return {"value": sample / dt, "unit": "alignments/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {sample} pairs of the workload, full-matrix DP + canonical traceback, "
-                      f"{dt:.1f} s wall on {cores} threads"}
+            "sample": f"first {sample} pairs of the workload, {what}, {dt:.1f} s wall on {cores} threads"}
 
 
 # ---------------------------------------------------------------- our arm
@@ -268,7 +286,7 @@ def run_ours(args, w, algo):
     n_pairs = args.pairs or w.pairs
     p = gen.generate(w, n_pairs, first=rank_first(rank, n_pairs))   # each rank: its own slice of the pair stream
     max_edits, per_pair = max_edits_args(w, p)
-    band = w.band if algo != "wfa" or args.workload == "wfa_250bp" else -1
+    band = w.band if algo not in ("wfa", "wfa_adaptive") or args.workload == "wfa_250bp" else -1
     pen_t = (0, 1, 0, 1) if algo == "edit" else w.penalties
     pen = aim.penalties(pen_t[1], pen_t[2], pen_t[3], band=band)
     max_len = int(max(p.read_len.max(), p.target_len.max()))
@@ -429,7 +447,7 @@ def run_ours(args, w, algo):
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
     peak_ops = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6
     launches = max(align_n, 1)
-    if algo == "wfa":
+    if algo in ("wfa", "wfa_adaptive"):
         ops = stats["wf_entries"] * OPS_WF_ENTRY + stats["extend_windows"] * OPS_EXT_WINDOW
         kernel = "wfa_kernel"
     else:
@@ -460,7 +478,8 @@ def run_ours(args, w, algo):
             "config": config_of(args.workload, w, n_pairs, algo),
             "form": "batched: bucketed queues + autotuned lanes per pair + CUDA graph replay" if batched
                     else "plain: one aim_align_batch_ascii call per step",
-            "cells_per_s": (stats["wf_entries"] if algo == "wfa" else stats["dp_cells"]) / launches / (ms / 1e3),
+            "cells_per_s": (stats["wf_entries"] if algo in ("wfa", "wfa_adaptive") else stats["dp_cells"])
+                           / launches / (ms / 1e3),
             "rejected_frac": float((res_flags & 1).mean()),
             "roofline": roof,
             "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
@@ -469,6 +488,13 @@ def run_ours(args, w, algo):
             "clocks": clk}
     if plain is not None:
         line["plain"] = plain
+    t3 = [key for key, ww in gen.TABLE3.items() if ww is w]
+    if t3:
+        ref = TABLE3_UPMEM[t3[0]]
+        line["vs_baseline"] = value / ref
+        line["baseline_note"] = (f"Table 3 (WFA-adaptive, {t3[0][0]} bp, {t3[0][1]} % edits): UPMEM {ref:.4g} "
+                                 "alignments/s on 2560 DPUs with host transfer included (compare e2e); real reads "
+                                 "there, seeded synthetic pairs of the same shape here")
     if batched and not args.no_serve and world == 1:
         line["serving"] = serving(args, local)
     if not args.no_cpu_baseline:

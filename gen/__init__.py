@@ -91,6 +91,23 @@ SERVE_LONG = Workload("serve_100_10000bp_1_10pct", 5, 0, 100, 10_000, 0.01, 0.10
                       "wfa", (0, 4, 6, 2), None, max_edits_frac=0.10)
 ALL = [EDIT_NW_100BP, WFA_150BP, GOTOH_WFA_250BP, WFA_UNEVEN, SERVE_LONG]
 
+# WFA-adaptive in the shapes of the paper's Table 3 (read length x edit rate), with the paper's costs
+# (x=3, o=4, e=1, Section 2.4.4) and thresholds at the edit rate: ceil(rate * length) edits.
+TABLE3 = {
+    (150, 2): Workload("wfa_adaptive_150bp_2pct_1M", 31, 1_000_000, 150, 150, 0.02, 0.02, 0.0, "wfa_adaptive",
+                       (0, 3, 4, 1), 3),
+    (150, 5): Workload("wfa_adaptive_150bp_5pct_1M", 32, 1_000_000, 150, 150, 0.05, 0.05, 0.0, "wfa_adaptive",
+                       (0, 3, 4, 1), 8),
+    (1000, 2): Workload("wfa_adaptive_1000bp_2pct_200k", 33, 200_000, 1000, 1000, 0.02, 0.02, 0.0, "wfa_adaptive",
+                        (0, 3, 4, 1), 20),
+    (1000, 5): Workload("wfa_adaptive_1000bp_5pct_200k", 34, 200_000, 1000, 1000, 0.05, 0.05, 0.0, "wfa_adaptive",
+                        (0, 3, 4, 1), 50),
+    (10000, 2): Workload("wfa_adaptive_10000bp_2pct_10k", 35, 10_000, 10_000, 10_000, 0.02, 0.02, 0.0,
+                         "wfa_adaptive", (0, 3, 4, 1), 200),
+    (10000, 5): Workload("wfa_adaptive_10000bp_5pct_4k", 36, 4_000, 10_000, 10_000, 0.05, 0.05, 0.0,
+                         "wfa_adaptive", (0, 3, 4, 1), 500),
+}
+
 
 @dataclass
 class Pairs:

@@ -187,6 +187,10 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
  * start; gap extension before gap opening), so it is a valid alignment of the
  * reported score but not necessarily the canonical one; the score can exceed
  * the optimum and a pair can be rejected when pruning loses the end cell.
+ * Scratch: a first pass sizes each pair's wavefront history (and its lanes per
+ * pair) for pruned wavefronts of about 4 (max_distance + min_length) + 64
+ * diagonals; pairs that outgrow it are aligned again in a second pass with
+ * the exact algorithm's worst-case scratch, so results never depend on it.
  */
 AIM_API int aim_set_wfa_adaptive(aim_ctx *ctx, int min_length, int max_distance);
 

@@ -122,7 +122,10 @@ struct WfaPlan {
     size_t group_bytes;  // scratch of one pair in flight: meta + runs + history
     int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
     int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end
+    int retry_only;      // launch aligns only the pairs a previous pass flagged AIM_F_STEP_CAP
 };
+// the plan with its history sized for wavefronts at most `width` diagonals wide (a compact first pass)
+WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width);
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
 size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax);
 // lanes per pair suited to the widest wavefront the plan allows (4, 8, 16, 32 or 256; 1 and 2 are valid too)
@@ -147,6 +150,7 @@ struct WfaArgs {
     uint32_t* counters;        // one claim counter per bucket, zero at launch
     int nbuckets;
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive pruning and source-following traceback (min_len < 0: off)
+    int retry_only;            // align only pairs whose flag is AIM_F_STEP_CAP (a second pass with larger scratch)
     int8_t group[kMaxBuckets]; // lanes per pair of each bucket
 };
 

@@ -138,17 +138,44 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
     if (algo == AIM_ALGO_WFA_AFFINE || algo == AIM_ALGO_WFA_ADAPTIVE) {
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
         aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
+        // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
+        auto fit_group = [&](const aim::WfaPlan& pl, int g0) {
+            int g = g0;
+            while (g <= 32 && 8 * aim::wfa_warp_bytes(g, pl.group_bytes) > scratch_bytes) g = g == 32 ? 256 : g * 2;
+            return 8 * aim::wfa_warp_bytes(g, pl.group_bytes) > scratch_bytes ? 0 : g;
+        };
         if (algo == AIM_ALGO_WFA_ADAPTIVE) {
             plan.adapt_min_len = ctx->adapt_min_len;
             plan.adapt_max_dist = ctx->adapt_max_dist;
+            // pruning keeps wavefronts narrow: a first pass sized and grouped for a typical pruned width, then
+            // a second pass with the full worst-case scratch for any pair that outgrew it
+            int64_t width = 4 * ((int64_t)plan.adapt_max_dist + plan.adapt_min_len) + 64;
+            width = std::min<int64_t>(width, 2 * (plan.smax / std::max(plan.e, 1)) + 3);   // never wider than exact
+            width = std::min<int64_t>(width, 2 * (int64_t)P.max_length + 1);
+            const aim::WfaPlan compact = aim::wfa_plan_compact(plan, width);
+            int g1 = ctx->wfa_group ? ctx->wfa_group : (width <= 64 ? 4 : width <= 128 ? 8 : width <= 256 ? 16 : 32);
+            g1 = fit_group(compact, g1);
+            int group = fit_group(plan, ctx->wfa_group ? ctx->wfa_group : aim::wfa_default_group(plan, P.max_length));
+            if (!g1 || !group) return AIM_ERR_NOMEM;
+            slot = time_begin(ctx, 1, st);
+            err = aim::launch_wfa(compact, g1, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
+            if (err == cudaSuccess && warps > 0) {
+                aim::WfaPlan retry = plan;
+                retry.retry_only = 1;
+                err = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
+                int w2 = 0;
+                if (err == cudaSuccess)
+                    err = aim::launch_wfa(retry, group, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st,
+                                          &w2);
+                if (err == cudaSuccess && w2 == 0) warps = 0;
+            }
+        } else {
+            const int group = fit_group(plan, ctx->wfa_group ? ctx->wfa_group
+                                                             : aim::wfa_default_group(plan, P.max_length));
+            if (!group) return AIM_ERR_NOMEM;
+            slot = time_begin(ctx, 1, st);
+            err = aim::launch_wfa(plan, group, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
         }
-        int group = ctx->wfa_group ? ctx->wfa_group : aim::wfa_default_group(plan, P.max_length);
-        // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
-        while (group <= 32 && 8 * aim::wfa_warp_bytes(group, plan.group_bytes) > scratch_bytes)
-            group = group == 32 ? 256 : group * 2;
-        if (8 * aim::wfa_warp_bytes(group, plan.group_bytes) > scratch_bytes) return AIM_ERR_NOMEM;
-        slot = time_begin(ctx, 1, st);
-        err = aim::launch_wfa(plan, group, P, r.lim, O, scratch, scratch_bytes, counter, ctx->num_sms, st, &warps);
     } else {
         const bool unit = algo == AIM_ALGO_EDIT_NW;
         int64_t b = P.max_length;

@@ -208,7 +208,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0;
     const uint64_t *Pw = nullptr, *Tw = nullptr;
     uint32_t nwP = 0, nwT = 0;
-    if (q < qend) {
+    if (q < qend && a.retry_only && a.O.flags[a.order ? a.order[q] : q] != AIM_F_STEP_CAP) {
+        // second pass: this pair already has its result
+    } else if (q < qend) {
         pi = a.order ? a.order[q] : q;
         n = (int)a.P.read_len[pi];
         m = (int)a.P.target_len[pi];
@@ -555,6 +557,15 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
     p.adapt_min_len = -1;
     p.adapt_max_dist = 0;
+    p.retry_only = 0;
+    return p;
+}
+
+WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width) {
+    WfaPlan p = full;
+    const size_t compact = 3 * (size_t)(full.smax + 1) * (size_t)std::max<int64_t>(width, 1) + 3;
+    if (compact < p.hist_elems) p.hist_elems = compact;
+    p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
     return p;
 }
 
@@ -580,6 +591,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.meta_bytes = plan.meta_bytes; a.runs_bytes = plan.runs_bytes; a.runs_cap = (uint32_t)plan.runs_cap;
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
     a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
+    a.retry_only = plan.retry_only;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int8_t)(b < nbuckets ? groups[b] : 32);
     int bps = 0;
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel, 256, 0);
