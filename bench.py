@@ -47,7 +47,7 @@ for (_len, _pct), _w in gen.TABLE3.items():
     WORKLOADS[f"table3_{_len}bp_{_pct}pct"] = _w
     ALGO_OF[f"table3_{_len}bp_{_pct}pct"] = "wfa_adaptive"
 
-# Algorithmic integer operations per unit of counted work (the roofline numerator; see DESIGN.md):
+# Algorithmic integer operations per unit of counted work (the roofline numerator):
 #   WFA wavefront entry: I~ one max, D~ one max + one add, mismatch candidate one add, f0 two max = 6
 #   WFA extend window (32 bases): two 2-word funnel shifts (3 ops each), xor, clz, halve, cap, advance v and h = 12
 #   Gotoh DP cell: 7 adds + 6 mins + 1 compare = 14;  unit-cost DP cell: 3 adds + 2 mins = 5

@@ -107,7 +107,7 @@ def align(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int = -1, li
     return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
 
 
-# WFA-adaptive parameters (the build's reading; the paper gives none): prune when a wavefront spans at
+# WFA-adaptive parameters (our reading; the paper gives none): prune when a wavefront spans at
 # least ADAPT_MIN_LEN diagonals, dropping outer diagonals more than ADAPT_MAX_DIST behind the closest to the end.
 ADAPT_MIN_LEN = 10
 ADAPT_MAX_DIST = 50

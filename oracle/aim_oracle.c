@@ -215,7 +215,7 @@ int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32
  * WFA-adaptive (Section 2.4.4: "a heuristic variant of WFA" that "reduces the
  * number of the spanned diagonals by eliminating outer diagonals that are
  * unlikely to lead to an optimal alignment").  The paper gives no parameters;
- * this is the build's reading, written out step by step:
+ * this is our reading, written out step by step:
  *
  *   Scores run in units of g = gcd(x, o, e) (X = x/g, OE = (o+e)/g, E = e/g).
  *   Wavefront s spans diagonals [lo_s, hi_s]; for each k in the candidate

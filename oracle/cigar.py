@@ -3,7 +3,7 @@
 A CIGAR is a list of uint32 runs, len << 4 | BAM code ('=' 7, 'X' 8, 'I' 1,
 'D' 2).  I consumes a read base, D a target base (read as query, target as
 reference).  The paper asks for the score and the alignment operations of
-every pair (Section 2.2, Steps 4 and 5); this encoding is the build's reading.
+every pair (Section 2.2, Steps 4 and 5); this encoding is our reading.
 """
 from __future__ import annotations
 

@@ -1,6 +1,6 @@
 """ORACLE -- test infrastructure only.  The 2-bit sequence layout, base by base.
 
-Layout (the build's reading of the packed storage named for the workloads):
+Layout (our reading of the packed 2-bit storage):
 A, C, G, T -> 0, 1, 2, 3; base j of a sequence sits in word j // 32 at bits
 [63 - 2*(j % 32) - 1, 63 - 2*(j % 32)], so the first base is in the top two
 bits; every sequence starts on a word boundary; unused low bits are zero.
