@@ -68,7 +68,7 @@ class Workload:
     rate_min: float
     rate_max: float
     unrelated_frac: float
-    algo: str                      # "edit" | "gotoh" | "wfa" | "gotoh+wfa"
+    algo: str                      # "edit" | "gotoh" | "wfa" | "gotoh+wfa" | "wfa_adaptive" | "genasm"
     penalties: tuple               # (match, mismatch, gap_open, gap_extend)
     max_edits: int | None          # scalar threshold, or None when it is per pair
     max_edits_frac: float | None = None   # per-pair threshold ceil(frac * read length)
@@ -108,6 +108,21 @@ TABLE3 = {
                          "wfa_adaptive", (0, 3, 4, 1), 500),
 }
 
+
+# GenASM (Section 2.4.3) at the paper's read lengths and edit levels (1 % and 5 %), unit costs, threshold
+# k = ceil(rate * length) edits.
+GENASM = {
+    (100, 1): Workload("genasm_100bp_1pct_1M", 41, 1_000_000, 100, 100, 0.01, 0.01, 0.0, "genasm", (0, 1, 0, 1), 1),
+    (100, 5): Workload("genasm_100bp_5pct_1M", 42, 1_000_000, 100, 100, 0.05, 0.05, 0.0, "genasm", (0, 1, 0, 1), 5),
+    (150, 1): Workload("genasm_150bp_1pct_1M", 43, 1_000_000, 150, 150, 0.01, 0.01, 0.0, "genasm", (0, 1, 0, 1), 2),
+    (150, 5): Workload("genasm_150bp_5pct_1M", 44, 1_000_000, 150, 150, 0.05, 0.05, 0.0, "genasm", (0, 1, 0, 1), 8),
+    (250, 1): Workload("genasm_250bp_1pct_1M", 45, 1_000_000, 250, 250, 0.01, 0.01, 0.0, "genasm", (0, 1, 0, 1), 3),
+    (250, 5): Workload("genasm_250bp_5pct_1M", 46, 1_000_000, 250, 250, 0.05, 0.05, 0.0, "genasm", (0, 1, 0, 1), 13),
+    (1000, 1): Workload("genasm_1000bp_1pct_200k", 47, 200_000, 1000, 1000, 0.01, 0.01, 0.0, "genasm",
+                        (0, 1, 0, 1), 10),
+    (1000, 5): Workload("genasm_1000bp_5pct_200k", 48, 200_000, 1000, 1000, 0.05, 0.05, 0.0, "genasm",
+                        (0, 1, 0, 1), 50),
+}
 
 @dataclass
 class Pairs:

@@ -9,8 +9,10 @@ Contents:
   aim_oracle.c  full-matrix 3-state DP (Gotoh; NW edit distance as the unit-cost
                 special case) with the canonical backward state-set traceback,
                 plus a textbook one-state Levenshtein (Sections 2.4.1, 2.4.2),
-                and the WFA-adaptive heuristic written out step by step
-                (Section 2.4.4; exact WFA when pruning is off)
+                the WFA-adaptive heuristic written out step by step
+                (Section 2.4.4; exact WFA when pruning is off), and GenASM's
+                windowed bit-vector distance with its forward traceback
+                (Section 2.4.3), from the suffix edit-distance table
   brute.py      brute-force enumeration of every op string on tiny pairs
   cigar.py      decode / re-cost / reconstruct helpers for CIGAR runs
   pack.py       the 2-bit layout written out per base (pins the device packer)
@@ -73,6 +75,9 @@ def _load():
                                             ctypes.POINTER(u32)]
         lib.oracle_wfa_adaptive_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, i32, i32, p, p, p, p,
                                                   p, ctypes.c_int]
+        lib.oracle_genasm.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i64, i32, i32, ctypes.POINTER(i32),
+                                      ctypes.POINTER(ctypes.c_uint8), p, u32, ctypes.POINTER(u32)]
+        lib.oracle_genasm_batch.argtypes = [p, p, p, p, p, p, u64, p, i32, i32, p, p, p, p, p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -147,6 +152,44 @@ def wfa_adaptive_batch(pairs, penalties, limits: np.ndarray, band: int = -1, min
                                       max_dist, P(scores), P(flags), P(cig), P(off), P(lens), threads)
     if r:
         raise RuntimeError(f"oracle_wfa_adaptive_batch failed: {r}")
+    return scores, flags, off, cig, lens
+
+
+# GenASM window and overlap (our reading; the paper gives none): one 64-bit word per status vector.
+GENASM_W = 64
+GENASM_O = 24
+
+
+def genasm(read: bytes, target: bytes, k: int = 1 << 62, W: int = GENASM_W, O: int = GENASM_O):
+    """One pair through the windowed GenASM -> (score, flags, [runs]); k < 0 or huge: no threshold."""
+    lib = _load()
+    sc = ctypes.c_int32(); fl = ctypes.c_uint8(); nc = ctypes.c_uint32()
+    cap = len(read) + len(target) + 1
+    buf = np.zeros(cap, np.uint32)
+    k = (1 << 62) if k < 0 else int(k)
+    r = lib.oracle_genasm(bytes(read), len(read), bytes(target), len(target), k, W, O, ctypes.byref(sc),
+                          ctypes.byref(fl), ctypes.c_void_p(buf.ctypes.data), cap, ctypes.byref(nc))
+    if r:
+        raise RuntimeError(f"oracle_genasm failed: {r}")
+    return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
+
+
+def genasm_batch(pairs, limits: np.ndarray, W: int = GENASM_W, O: int = GENASM_O, threads: int | None = None):
+    """gen.Pairs through the windowed GenASM -> (scores, flags, cigar_off, cigars, cigar_lens)."""
+    lib = _load()
+    n = len(pairs)
+    threads = threads or os.cpu_count() or 1
+    lim = np.ascontiguousarray(limits, dtype=np.int64)
+    scores = np.empty(n, np.int32); flags = np.empty(n, np.uint8); lens = np.zeros(n, np.uint32)
+    cap = pairs.read_len.astype(np.uint64) + pairs.target_len.astype(np.uint64) + 1
+    off = np.zeros(n + 1, np.uint64); off[1:] = np.cumsum(cap, dtype=np.uint64)
+    cig = np.zeros(int(off[-1]), np.uint32)
+    P = lambda a: ctypes.c_void_p(a.ctypes.data)
+    r = lib.oracle_genasm_batch(P(pairs.reads), P(pairs.read_off), P(pairs.read_len), P(pairs.targets),
+                                P(pairs.target_off), P(pairs.target_len), n, P(lim), W, O, P(scores), P(flags),
+                                P(cig), P(off), P(lens), threads)
+    if r:
+        raise RuntimeError(f"oracle_genasm_batch failed: {r}")
     return scores, flags, off, cig, lens
 
 

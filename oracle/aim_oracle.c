@@ -6,10 +6,10 @@
  *
  * What it computes (per pair of read P[0..n) and target T[0..m)):
  *
- *   Exact global alignment under gap-affine costs (Section 2.4.2, SWG with
- *   three tables M, I, D, "resembles NW but uses an affine gap model"); NW
- *   edit distance (Section 2.4.1) is the same DP with mismatch 1, open 0,
- *   extend 1.  The recurrences are the textbook Gotoh ones (the paper names
+ *   Exact global alignment under gap-affine costs (Section 2.4.2: SWG, three
+ *   tables M, I, D; NW's scheme with separate costs for opening and for
+ *   extending a gap); NW edit distance (Section 2.4.1) is the same DP with
+ *   mismatch 1, open 0, extend 1.  The recurrences are the textbook Gotoh ones (the paper names
  *   the method but does not print them), written out over the full matrix:
  *
  *     M(v,h) = min(M,I,D)(v-1,h-1) + (P[v-1]==T[h-1] ? 0 : x)
@@ -19,7 +19,7 @@
  *     Cells with |h-v| > band are infinite when a band is given.
  *     score = min(M,I,D)(n,m)
  *
- *   Threshold (Section 1, "edit distance threshold"): the pair is rejected
+ *   Threshold (Section 1: every pair is aligned under an edit limit): the pair is rejected
  *   iff score > limit (or |n-m| > band); a rejected pair reports score -1,
  *   flag 1 and no CIGAR.
  *
@@ -212,10 +212,10 @@ int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32
 }
 
 /* ---------------------------------------------------------------------------
- * WFA-adaptive (Section 2.4.4: "a heuristic variant of WFA" that "reduces the
- * number of the spanned diagonals by eliminating outer diagonals that are
- * unlikely to lead to an optimal alignment").  The paper gives no parameters;
- * this is our reading, written out step by step:
+ * WFA-adaptive (Section 2.4.4: a heuristic form of the WFA that keeps its
+ * wavefronts narrow by dropping the outer diagonals least likely to lie on an
+ * optimal path).  The paper gives no parameters; this is our reading, written
+ * out step by step:
  *
  *   Scores run in units of g = gcd(x, o, e) (X = x/g, OE = (o+e)/g, E = e/g).
  *   Wavefront s spans diagonals [lo_s, hi_s]; for each k in the candidate
@@ -464,4 +464,175 @@ int oracle_wfa_adaptive_batch(const char *reads, const uint64_t *read_off, const
     for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
     free(th);
     return aj.base.err;
+}
+
+/* ---------------------------------------------------------------------------
+ * GenASM (Section 2.4.3): an edit-distance aligner built on the bitap
+ * algorithm, with a traceback added, under a threshold of k edits.  The paper
+ * names the method and its working data (a bit mask per pattern character,
+ * status bit-vectors, one intermediate vector per kind of edit) but prints
+ * neither the algorithm nor its parameters.  Our reading, step by step:
+ *
+ *   The pair is aligned window by window from its start.  At read position i
+ *   and target position j a window holds wp = min(W, n-i) read bases and
+ *   wt = min(W, m-j) target bases.  The read ends inside it when n-i <= W,
+ *   the target when m-j <= W; the window is final when both do.
+ *
+ *   Window distance.  For a in [0, wp] and c in [0, wt], f(a, c) is the least
+ *   number of edits of a path from (a, c) to the window's far edge.  A side
+ *   whose sequence goes on past the window is a free end: the path may stop
+ *   as soon as that window is used up, leaving the rest to the next window.
+ *   A side whose sequence ends inside the window is not: bases left on the
+ *   other side then cost one gap edit each.  (In the final window this is the
+ *   global alignment of the two rests.)  Written out as the suffix
+ *   edit-distance recurrence:
+ *     f(wp, c) = read ends ? wt - c : 0      f(a, wt) = target ends ? wp - a : 0
+ *     f(a, c)  = min(f(a+1, c+1) + [read base != target base], f(a+1, c) + 1, f(a, c+1) + 1)
+ *   A bitap status vector of distance level d holds, for every read suffix,
+ *   the bit [f(a, c) <= d]; the window distance is d = f(0, 0).  Any way the
+ *   alignment goes on from (i, j) crosses the window's far edge, so it makes
+ *   at least d more edits: a window whose distance exceeds the edits left
+ *   (k minus the edits so far) rejects the pair at once, which is the same
+ *   outcome as finishing it (an early exit; the distance levels of a window
+ *   never need to go past the edits left).
+ *
+ *   Traceback, forward from (0, 0) with budget d: take the first op of this
+ *   list whose successor still fits the budget (an edit spends one):
+ *     after an I, I first; after a D, D first (gap extension before anything
+ *     else: the affine-gap preference); then M (bases equal, f(a+1, c+1) <= d),
+ *     X (bases differ, f(a+1, c+1) <= d-1), I (f(a+1, c) <= d-1),
+ *     D (f(a, c+1) <= d-1).
+ *   With the read window used up only D remains, with the target window used
+ *   up only I.  A non-final window stops once W-O read bases or W-O target
+ *   bases have been consumed in it (or at its corner); the final window runs
+ *   to its corner.  Then i += a, j += c and the next window starts; the last
+ *   op so far counts as the previous op.
+ *
+ *   When one sequence is used up, the rest of the other is one gap.  The
+ *   score is the number of edits of the alignment; as soon as the edits so
+ *   far exceed k the pair is rejected (score -1, flag 1, no CIGAR).
+ *
+ * W = 64 (one machine word per status vector) and O = 24 are our defaults.
+ * Pinned by: with both sequences inside one window the score is the edit
+ * distance (against the separate Levenshtein routine and brute force) and the
+ * CIGAR the first optimal op string in the order above (brute force over all
+ * op strings); hand-worked multi-window examples; closed forms; and validity
+ * invariants at any size (tests/test_oracle_genasm.py).
+ * --------------------------------------------------------------------------- */
+
+/* one window: fill f ((wp+1) x (wt+1), row a, column c) */
+static void genasm_window_table(const char *R, int wp, const char *Tt, int wt, int end_r, int end_t, int32_t *f) {
+#define F(a, c) f[(size_t)(a) * (size_t)(wt + 1) + (size_t)(c)]
+    for (int c = 0; c <= wt; ++c) F(wp, c) = end_r ? wt - c : 0;
+    for (int a = 0; a <= wp; ++a) F(a, wt) = end_t ? wp - a : 0;
+    for (int a = wp - 1; a >= 0; --a)
+        for (int c = wt - 1; c >= 0; --c)
+            F(a, c) = min3(F(a + 1, c + 1) + (R[a] != Tt[c]), F(a + 1, c) + 1, F(a, c + 1) + 1);
+#undef F
+}
+
+int oracle_genasm(const char *P, uint32_t n, const char *T, uint32_t m, int64_t k, int32_t W, int32_t O,
+                  int32_t *score, uint8_t *flags, uint32_t *cigar, uint32_t cap, uint32_t *ncig) {
+    *score = -1; *flags = 0; *ncig = 0;
+    if (W < 1 || W > 64 || O < 0 || O >= W) return -1;
+    int32_t *f = (int32_t *)malloc((size_t)(W + 1) * (size_t)(W + 1) * sizeof(int32_t));
+    char *ops = (char *)malloc((size_t)n + m + 1);
+    if (!f || !ops) { free(f); free(ops); return -3; }
+    uint32_t i = 0, j = 0, nops = 0;
+    int64_t used = 0;
+    char prev = 0;
+    int rejected = 0;
+    while (i < n && j < m) {
+        int wp = (int)((n - i) < (uint32_t)W ? (n - i) : (uint32_t)W);
+        int wt = (int)((m - j) < (uint32_t)W ? (m - j) : (uint32_t)W);
+        int end_r = (n - i) <= (uint32_t)W, end_t = (m - j) <= (uint32_t)W, final = end_r && end_t;
+        genasm_window_table(P + i, wp, T + j, wt, end_r, end_t, f);
+#define F(a, c) f[(size_t)(a) * (size_t)(wt + 1) + (size_t)(c)]
+        int32_t d = F(0, 0);
+        if (d > k - used) { rejected = 1; break; }
+        int a = 0, c = 0;
+        for (;;) {
+            if (!final && (a >= W - O || c >= W - O)) break;
+            if (a == wp && c == wt) break;
+            char op;
+            if (a == wp) op = 'D';
+            else if (c == wt) op = 'I';
+            else if (prev == 'I' && d >= 1 && F(a + 1, c) <= d - 1) op = 'I';
+            else if (prev == 'D' && d >= 1 && F(a, c + 1) <= d - 1) op = 'D';
+            else if (P[i + a] == T[j + c] && F(a + 1, c + 1) <= d) op = 'M';
+            else if (P[i + a] != T[j + c] && d >= 1 && F(a + 1, c + 1) <= d - 1) op = 'X';
+            else if (d >= 1 && F(a + 1, c) <= d - 1) op = 'I';
+            else if (d >= 1 && F(a, c + 1) <= d - 1) op = 'D';
+            else { free(f); free(ops); return -5; /* cannot happen: f(a, c) <= d */ }
+            ops[nops++] = op;
+            prev = op;
+            if (op != 'M') { --d; ++used; }
+            if (op == 'M' || op == 'X') { ++a; ++c; }
+            else if (op == 'I') ++a;
+            else ++c;
+        }
+#undef F
+        i += (uint32_t)a; j += (uint32_t)c;
+        if (used > k) { rejected = 1; break; }
+    }
+    if (!rejected) {
+        /* one sequence is used up: the rest of the other is one gap */
+        for (; i < n; ++i) { ops[nops++] = 'I'; ++used; }
+        for (; j < m; ++j) { ops[nops++] = 'D'; ++used; }
+        if (used > k) rejected = 1;
+    }
+    if (rejected) { *flags = 1; free(f); free(ops); return 0; }
+    *score = (int32_t)used;
+    uint32_t runs = 0;
+    for (uint32_t q = 0; q < nops;) {
+        char op = ops[q]; uint32_t len = 0;
+        while (q < nops && ops[q] == op) { ++len; ++q; }
+        if (cigar && runs < cap) cigar[runs] = (len << 4) | bam_code(op);
+        ++runs;
+    }
+    *ncig = runs;
+    if (cigar && runs > cap) *flags |= 2;
+    free(f); free(ops);
+    return 0;
+}
+
+/* ---- batch driver for GenASM (same layout as oracle_align_batch; x, o, e unused) ---- */
+
+typedef struct {
+    batch_job base;
+    int32_t W, O;
+} genasm_job;
+
+static void *genasm_worker(void *arg) {
+    genasm_job *gj = (genasm_job *)arg;
+    batch_job *j = &gj->base;
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&j->next, 1, __ATOMIC_RELAXED);
+        if (i >= (int64_t)j->num_pairs) break;
+        uint32_t *cig = NULL, cap = 0;
+        if (j->cigars) { cig = j->cigars + j->cigar_off[i]; cap = (uint32_t)(j->cigar_off[i + 1] - j->cigar_off[i]); }
+        int r = oracle_genasm(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
+                              j->target_len[i], j->limit[i], gj->W, gj->O, &j->scores[i], &j->flags[i], cig, cap,
+                              &j->cigar_lens[i]);
+        if (r) j->err = r;
+    }
+    return NULL;
+}
+
+int oracle_genasm_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len, const char *targets,
+                        const uint64_t *target_off, const uint32_t *target_len, uint64_t num_pairs,
+                        const int64_t *limit, int32_t W, int32_t O, int32_t *scores, uint8_t *flags,
+                        uint32_t *cigars, const uint64_t *cigar_off, uint32_t *cigar_lens, int threads) {
+    genasm_job gj = {{reads, targets, read_off, target_off, read_len, target_len, num_pairs, 0, 0, 0, -1, limit,
+                      scores, flags, cigars, cigar_off, cigar_lens, 0, 0}, W, O};
+    if (threads < 1) threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    if (!th) return -3;
+    int started = 0;
+    for (int t = 0; t < threads; ++t)
+        if (pthread_create(&th[t], NULL, genasm_worker, &gj) == 0) ++started;
+    if (started == 0) genasm_worker(&gj);
+    for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+    free(th);
+    return gj.base.err;
 }

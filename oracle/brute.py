@@ -53,3 +53,26 @@ def best(read: bytes, target: bytes, penalties, band: int = -1):
     if found is None:
         return None, None
     return found[0][0], found[1]
+
+
+# GenASM traceback order (Section 2.4.3, our reading): after an I the I comes first, after a D the D; then M, X, I, D.
+_GENASM_ORDER = {"I": "IMXD", "D": "DMXI"}
+
+
+def _genasm_before(a: str, b: str) -> bool:
+    """a precedes b: at their first difference, a's op comes earlier in the order that the op before it sets."""
+    p = next(q for q in range(min(len(a), len(b))) if a[q] != b[q])
+    order = _GENASM_ORDER.get(a[p - 1] if p else "", "MXID")
+    return order.index(a[p]) < order.index(b[p])
+
+
+def genasm_first(read: bytes, target: bytes):
+    """(edit distance, the first optimal op string in the GenASM traceback order), by enumeration."""
+    found = None
+    for ops in _strings(len(read), len(target)):
+        c = cost(ops, read, target, (0, 1, 0, 1))
+        if c is None:
+            continue
+        if found is None or c < found[0] or (c == found[0] and _genasm_before(ops, found[1])):
+            found = (c, ops)
+    return found
