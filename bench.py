@@ -46,12 +46,17 @@ TABLE3_UPMEM = {(150, 2): 12.97e6, (150, 5): 7.03e6, (1000, 2): 1.10e6, (1000, 5
 for (_len, _pct), _w in gen.TABLE3.items():
     WORKLOADS[f"table3_{_len}bp_{_pct}pct"] = _w
     ALGO_OF[f"table3_{_len}bp_{_pct}pct"] = "wfa_adaptive"
+# GenASM at the paper's read lengths and edit levels (unit costs, k = ceil(rate * length))
+for (_len, _pct), _w in gen.GENASM.items():
+    WORKLOADS[f"genasm_{_len}bp_{_pct}pct"] = _w
+    ALGO_OF[f"genasm_{_len}bp_{_pct}pct"] = "genasm"
 
 # Algorithmic integer operations per unit of counted work (the roofline numerator):
 #   WFA wavefront entry: I~ one max, D~ one max + one add, mismatch candidate one add, f0 two max = 6
 #   WFA extend window (32 bases): two 2-word funnel shifts (3 ops each), xor, clz, halve, cap, advance v and h = 12
 #   Gotoh DP cell: 7 adds + 6 mins + 1 compare = 14;  unit-cost DP cell: 3 adds + 2 mins = 5
-OPS_WF_ENTRY, OPS_EXT_WINDOW, OPS_GOTOH_CELL, OPS_UNIT_CELL = 6, 12, 14, 5
+#   GenASM status vector (64 bits): two shifts, one AND, five ORs on 64-bit words, two 32-bit ops each = 16
+OPS_WF_ENTRY, OPS_EXT_WINDOW, OPS_GOTOH_CELL, OPS_UNIT_CELL, OPS_BITAP_WORD = 6, 12, 14, 5, 16
 INT32_LANES_PER_SM = 128
 
 
@@ -87,7 +92,7 @@ def runs_capacity(w, p, algo):
     """CIGAR run capacity per pair: every edit run costs at least min(x, o+e) (unit: 1), runs alternate."""
     _, x, o, e = w.penalties
     me = gen.per_pair_max_edits(w, p).astype(np.int64)
-    if algo == "edit":
+    if algo in ("edit", "genasm"):
         lim = me; minc = 1
     else:  # affine (exact or adaptive)
         lim = me * max(x, o + e); minc = min(x, o + e)
@@ -180,21 +185,24 @@ def run_reference(args, w, algo):
         return 0
     oracle.build()
     cores = os.cpu_count() or 1
-    sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000, "wfa_adaptive": 40_000}[algo]
+    sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000, "wfa_adaptive": 40_000, "genasm": 60_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 2_000
-    if algo == "wfa_adaptive":
+    if algo in ("wfa_adaptive", "genasm"):
         sample = max(200, min(sample, 8_000_000 // max(w.len_max, 1)))
-    pen = oracle.UNIT if algo == "edit" else w.penalties
+    pen = oracle.UNIT if algo in ("edit", "genasm") else w.penalties
     band = w.band if algo not in ("wfa", "wfa_adaptive") or args.workload == "wfa_250bp" else -1
     times = []
     for step in range(args.warmup + args.steps):
         p = gen.generate(w, sample, first=step * sample)
         me = gen.per_pair_max_edits(w, p)
-        lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
+        lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo in ("edit", "genasm")) for k in me],
+                       np.int64)
         t0 = time.perf_counter()
         if algo == "wfa_adaptive":
             oracle.wfa_adaptive_batch(p, pen, lim, band=band, threads=cores)
+        elif algo == "genasm":
+            oracle.genasm_batch(p, lim, threads=cores)
         else:
             oracle.align_batch(p, pen, lim, band=band, threads=cores)
         dt = time.perf_counter() - t0
@@ -208,7 +216,9 @@ def run_reference(args, w, algo):
             "config": config_of(args.workload, w, sample, algo),
             "cpu_baseline": {"value": value, "unit": "alignments/s", "cores": cores, "kind": "oracle",
                              "sample": f"{sample} pairs per step (pairs drawn from the workload's seeded stream), "
-                                       f"full-matrix DP with canonical traceback on {cores} host threads"},
+                                       + ("windowed suffix edit-distance tables with the forward traceback"
+                                          if algo == "genasm" else "full-matrix DP with canonical traceback")
+                                       + f" on {cores} host threads"},
             "e2e": {"value": value, "unit": "alignments/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -219,19 +229,22 @@ def cpu_baseline(w, algo):
     import oracle
     oracle.build()
     cores = os.cpu_count() or 1
-    sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000, "wfa_adaptive": 200_000}[algo]
+    sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000, "wfa_adaptive": 200_000, "genasm": 400_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 10_000
-    if algo == "wfa_adaptive":
+    if algo in ("wfa_adaptive", "genasm"):
         sample = max(500, min(sample, 40_000_000 // max(w.len_max, 1)))
     p = gen.generate(w, sample)
     me = gen.per_pair_max_edits(w, p)
-    lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo == "edit") for k in me], np.int64)
-    pen = oracle.UNIT if algo == "edit" else w.penalties
+    lim = np.array([oracle.limit_for(w.penalties, int(k), unit=algo in ("edit", "genasm")) for k in me], np.int64)
+    pen = oracle.UNIT if algo in ("edit", "genasm") else w.penalties
     t0 = time.perf_counter()
     if algo == "wfa_adaptive":
         oracle.wfa_adaptive_batch(p, pen, lim, threads=cores)
         what = "step-by-step CPU WFA-adaptive"
+    elif algo == "genasm":
+        oracle.genasm_batch(p, lim, threads=cores)
+        what = "windowed suffix edit-distance tables + forward traceback"
     else:
         oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores)
         what = "full-matrix DP + canonical traceback"
@@ -287,7 +300,7 @@ def run_ours(args, w, algo):
     p = gen.generate(w, n_pairs, first=rank_first(rank, n_pairs))   # each rank: its own slice of the pair stream
     max_edits, per_pair = max_edits_args(w, p)
     band = w.band if algo not in ("wfa", "wfa_adaptive") or args.workload == "wfa_250bp" else -1
-    pen_t = (0, 1, 0, 1) if algo == "edit" else w.penalties
+    pen_t = (0, 1, 0, 1) if algo in ("edit", "genasm") else w.penalties
     pen = aim.penalties(pen_t[1], pen_t[2], pen_t[3], band=band)
     max_len = int(max(p.read_len.max(), p.target_len.max()))
     cap = runs_capacity(w, p, algo)
@@ -450,6 +463,9 @@ def run_ours(args, w, algo):
     if algo in ("wfa", "wfa_adaptive"):
         ops = stats["wf_entries"] * OPS_WF_ENTRY + stats["extend_windows"] * OPS_EXT_WINDOW
         kernel = "wfa_kernel"
+    elif algo == "genasm":
+        ops = stats["bitap_words"] * OPS_BITAP_WORD
+        kernel = "genasm_kernel"
     else:
         ops = stats["dp_cells"] * (OPS_UNIT_CELL if algo == "edit" else OPS_GOTOH_CELL)
         kernel = "dp_kernel"
@@ -478,7 +494,8 @@ def run_ours(args, w, algo):
             "config": config_of(args.workload, w, n_pairs, algo),
             "form": "batched: bucketed queues + autotuned lanes per pair + CUDA graph replay" if batched
                     else "plain: one aim_align_batch_ascii call per step",
-            "cells_per_s": (stats["wf_entries"] if algo in ("wfa", "wfa_adaptive") else stats["dp_cells"])
+            "cells_per_s": (stats["wf_entries"] if algo in ("wfa", "wfa_adaptive")
+                            else stats["bitap_words"] if algo == "genasm" else stats["dp_cells"])
                            / launches / (ms / 1e3),
             "rejected_frac": float((res_flags & 1).mean()),
             "roofline": roof,

@@ -14,9 +14,11 @@
  *   AIM_ALGO_GOTOH_BANDED  gap-affine global DP with three tables M, I, D
  *                          (Section 2.4.2, "SWG"; read as global alignment), banded.
  *   AIM_ALGO_WFA_AFFINE    gap-affine wavefront algorithm (Section 2.4.4), exact.
- *   AIM_ALGO_WFA_ADAPTIVE  WFA-adaptive (Section 2.4.4: prunes outer diagonals unlikely
- *                          to lead to an optimal alignment), a heuristic; see
+ *   AIM_ALGO_WFA_ADAPTIVE  WFA-adaptive (Section 2.4.4: keeps wavefronts narrow by
+ *                          dropping outer diagonals), a heuristic; see
  *                          aim_set_wfa_adaptive for the rule and its CIGAR.
+ *   AIM_ALGO_GENASM        GenASM (Section 2.4.3): bit-parallel (bitap) edit distance
+ *                          with a traceback, in windows; see aim_set_genasm_window.
  * The three exact algorithms compute the same optimum for the same costs; the
  * CIGAR is the canonical one (below), so they agree bit for bit.
  *
@@ -86,7 +88,8 @@ typedef enum {
     AIM_ALGO_EDIT_NW = 0,
     AIM_ALGO_GOTOH_BANDED = 1,
     AIM_ALGO_WFA_AFFINE = 2,
-    AIM_ALGO_WFA_ADAPTIVE = 3   /* heuristic: see aim_set_wfa_adaptive */
+    AIM_ALGO_WFA_ADAPTIVE = 3,  /* heuristic: see aim_set_wfa_adaptive */
+    AIM_ALGO_GENASM = 4         /* windowed bitap edit distance: see aim_set_genasm_window */
 } aim_algo_t;
 
 typedef struct {
@@ -151,7 +154,7 @@ AIM_API int aim_pack_2bit(aim_ctx *ctx, const uint8_t *ascii, const uint64_t *ch
  *                              (cigar_offsets has num_pairs + 1 entries)
  *   out_cigar_lens             optional: runs per pair (the full count even on overflow)
  *   out_flags                  uint8 per pair (AIM_F_*)
- * Limits: AIM_ALGO_WFA_AFFINE needs max_length <= 32000; the DP algorithms
+ * Limits: the wavefront algorithms need max_length <= 32000; the DP algorithms
  * need an effective band <= 127 (edit distance: min(band, limit); Gotoh:
  * min(band, (limit - o) / e)), else AIM_ERR_UNSUPPORTED.
  */
@@ -193,6 +196,33 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
  * the exact algorithm's worst-case scratch, so results never depend on it.
  */
 AIM_API int aim_set_wfa_adaptive(aim_ctx *ctx, int min_length, int max_distance);
+
+/*
+ * GenASM (AIM_ALGO_GENASM; Section 2.4.3: the bitap algorithm with a traceback
+ * added, under a limit of k edits).  The paper prints no algorithm; this is
+ * the library's reading.  Unit edit costs: the penalties are ignored (match
+ * must be 0), k is the threshold of the threshold rule above (max_score if
+ * >= 0, else max_edits or the per-pair array), and a band is not supported
+ * (pen->band >= 0 gives AIM_ERR_UNSUPPORTED).  Any max_length is accepted.
+ *
+ * The pair is aligned in windows of `window` bases (1..64: one 64-bit word per
+ * bitap status vector; default 64) that overlap by `overlap` bases (0..window-1,
+ * default 24).  A window's distance is its edit distance to the window's far
+ * edge, where an edge is free if its sequence goes on past the window (the
+ * last window, holding both ends, is a global alignment).  A forward traceback
+ * then takes, at each step, the first op that still fits the window's
+ * distance: after an I, I first; after a D, D first (gap extension before
+ * anything else, the affine-gap preference); then M, X, I, D.  A window that is
+ * not the last stops once window - overlap read or target bases have been
+ * consumed.  When one sequence is used up, the rest of the other is one gap.
+ * The score is the number of edits of the whole alignment; a pair is rejected
+ * iff it exceeds k.  Inside one window this is the exact edit distance; across
+ * windows the score can exceed it.
+ *
+ * Work counter [4] (aim_stats_read) counts the 64-bit status vectors computed
+ * (one distance level at one target position of one window).
+ */
+AIM_API int aim_set_genasm_window(aim_ctx *ctx, int window, int overlap);
 
 /*
  * Batched form (wavefront algorithm): pairs of uneven length and error rate
@@ -291,11 +321,12 @@ AIM_API int aim_set_wfa_group(aim_ctx *ctx, int lanes);
  *   [1] 32-base windows compared by the WFA extend
  *   [2] DP cells computed (in-band cells actually swept, up to early exit)
  *   [3] pairs aligned (every pair a kernel finished, any flag)
+ *   [4] GenASM status vectors computed (one distance level at one target position of one window)
  * aim_stats_reset is asynchronous on `stream`; aim_stats_read synchronises
- * the device and copies the four counters to host memory `out`.
+ * the device and copies the five counters to host memory `out`.
  */
 AIM_API int aim_stats_reset(aim_ctx *ctx, aim_stream_t stream);
-AIM_API int aim_stats_read(aim_ctx *ctx, uint64_t *out /* host, 4 entries */);
+AIM_API int aim_stats_read(aim_ctx *ctx, uint64_t *out /* host, 5 entries */);
 
 /*
  * Kernel timing.  While enabled, every call records a CUDA event pair on its

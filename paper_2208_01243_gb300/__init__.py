@@ -17,9 +17,9 @@ from .build import LIB
 
 AIM_OK, AIM_ERR_ARG, AIM_ERR_INPUT, AIM_ERR_NOMEM, AIM_ERR_CUDA, AIM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 AIM_F_REJECTED, AIM_F_CIGAR_OVERFLOW, AIM_F_BAD_PAIR, AIM_F_STEP_CAP = 1, 2, 4, 8
-AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE, AIM_ALGO_WFA_ADAPTIVE = 0, 1, 2, 3
+AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE, AIM_ALGO_WFA_ADAPTIVE, AIM_ALGO_GENASM = 0, 1, 2, 3, 4
 ALGO = {"edit": AIM_ALGO_EDIT_NW, "gotoh": AIM_ALGO_GOTOH_BANDED, "wfa": AIM_ALGO_WFA_AFFINE,
-        "wfa_adaptive": AIM_ALGO_WFA_ADAPTIVE}
+        "wfa_adaptive": AIM_ALGO_WFA_ADAPTIVE, "genasm": AIM_ALGO_GENASM}
 
 
 class aim_penalties_t(ctypes.Structure):
@@ -69,6 +69,7 @@ def _lib():
                                              p, p, p, p, p]
         lib.aim_set_wfa_group.argtypes = [p, ctypes.c_int]
         lib.aim_set_wfa_adaptive.argtypes = [p, ctypes.c_int, ctypes.c_int]
+        lib.aim_set_genasm_window.argtypes = [p, ctypes.c_int, ctypes.c_int]
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
@@ -273,6 +274,10 @@ def aim_server_destroy(server) -> None:
     _check(_lib().aim_server_destroy(server), "aim_server_destroy")
 
 
+def aim_set_genasm_window(ctx, window: int = 64, overlap: int = 24) -> None:
+    _check(_lib().aim_set_genasm_window(ctx, int(window), int(overlap)), "aim_set_genasm_window")
+
+
 def aim_set_wfa_adaptive(ctx, min_length: int = 10, max_distance: int = 50) -> None:
     _check(_lib().aim_set_wfa_adaptive(ctx, int(min_length), int(max_distance)), "aim_set_wfa_adaptive")
 
@@ -287,9 +292,10 @@ def aim_stats_reset(ctx, stream=None) -> None:
 
 def aim_stats_read(ctx) -> dict:
     import numpy as np
-    out = np.zeros(4, np.uint64)
+    out = np.zeros(5, np.uint64)
     _check(_lib().aim_stats_read(ctx, ctypes.c_void_p(out.ctypes.data)), "aim_stats_read")
-    return {"wf_entries": int(out[0]), "extend_windows": int(out[1]), "dp_cells": int(out[2]), "pairs": int(out[3])}
+    return {"wf_entries": int(out[0]), "extend_windows": int(out[1]), "dp_cells": int(out[2]), "pairs": int(out[3]),
+            "bitap_words": int(out[4])}
 
 
 def aim_timing_enable(ctx, on: bool = True) -> None:

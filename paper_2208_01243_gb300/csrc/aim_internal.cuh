@@ -164,6 +164,14 @@ cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const
                        uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
                        int* warps_used);
 
+// GenASM (windowed bitap): scratch per warp for windows of W bases and `levels` distance levels per lane
+size_t genasm_warp_bytes(int W, int levels);
+// distance levels a window can need under the largest threshold (rounded up to whole register blocks)
+int genasm_levels(int W, int64_t max_limit);
+cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, const OutView& Ov, int64_t max_limit,
+                          uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
+                          int* warps_used);
+
 }  // namespace aim
 
 namespace aim {
@@ -239,7 +247,8 @@ __device__ __forceinline__ void warp_stat_add(unsigned long long* stats, int slo
 namespace aim {
 constexpr int kTimedLaunches = 4096;
 constexpr size_t kHeaderBytes = 256;   // launch counter and work counters at the start of the workspace
-constexpr size_t kStatsOffset = 64;    // four uint64 work counters
+constexpr size_t kStatsOffset = 64;    // five uint64 work counters
+constexpr int kStats = 5;
 struct KernelTimes;
 }  // namespace aim
 
@@ -252,6 +261,7 @@ struct aim_ctx {
     aim::KernelTimes* times[2];   // 0: packer, 1: alignment kernels; created on first enable
     int wfa_group;                // lanes per pair for the WFA; 0: chosen from the plan
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive parameters
+    int genasm_w, genasm_o;       // GenASM window and overlap
     void* tune_cache;             // autotuner choices (owned; see batch.cu)
 };
 

@@ -95,7 +95,7 @@ bool penalties_ok(const aim_penalties_t* p) {
 namespace aim {
 // The threshold rule of aim.h: max_score overrides; else max_edits (x unit cost, or x max(x, o+e)).
 int resolve(int algo, const aim_penalties_t* pen, int32_t max_edits, const int32_t* per_pair, Resolved* r) {
-    const bool unit = algo == AIM_ALGO_EDIT_NW;
+    const bool unit = algo == AIM_ALGO_EDIT_NW || algo == AIM_ALGO_GENASM;
     r->costs = unit ? aim::Costs{1, 0, 1} : aim::Costs{pen->mismatch, pen->gap_open, pen->gap_extend};
     const int32_t edit_cost = unit ? 1 : std::max(r->costs.x, r->costs.o + r->costs.e);
     r->lim.per_pair = nullptr;
@@ -135,7 +135,15 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
     cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st);
     if (err != cudaSuccess) return cuda_status(err);
     int slot = -1;
-    if (algo == AIM_ALGO_WFA_AFFINE || algo == AIM_ALGO_WFA_ADAPTIVE) {
+    if (algo == AIM_ALGO_GENASM) {
+        if (pen->band >= 0) return AIM_ERR_UNSUPPORTED;
+        if (aim::genasm_warp_bytes(ctx->genasm_w, aim::genasm_levels(ctx->genasm_w, r.max_limit)) + 256 >
+            scratch_bytes)
+            return AIM_ERR_NOMEM;
+        slot = time_begin(ctx, 1, st);
+        err = aim::launch_genasm(ctx->genasm_w, ctx->genasm_o, P, r.lim, O, r.max_limit, scratch, scratch_bytes,
+                                 counter, ctx->num_sms, st, &warps);
+    } else if (algo == AIM_ALGO_WFA_AFFINE || algo == AIM_ALGO_WFA_ADAPTIVE) {
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
         aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
         // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
@@ -203,9 +211,10 @@ bool common_args_ok(aim_ctx* ctx, const void* rl, const void* tl, uint32_t num_p
                     const aim_penalties_t* pen, int32_t* out_scores, uint32_t* out_cigars,
                     const uint64_t* cigar_offsets, uint8_t* out_flags) {
     if (!ctx || !pen) return false;
-    if (algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_WFA_ADAPTIVE) return false;
-    if (algo != AIM_ALGO_EDIT_NW && !penalties_ok(pen)) return false;
-    if (algo == AIM_ALGO_EDIT_NW && pen->match != 0) return false;
+    if (algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_GENASM) return false;
+    const bool unit = algo == AIM_ALGO_EDIT_NW || algo == AIM_ALGO_GENASM;
+    if (!unit && !penalties_ok(pen)) return false;
+    if (unit && pen->match != 0) return false;
     if (num_pairs == 0) return true;
     if (!rl || !tl || !out_scores || !out_flags) return false;
     if ((out_cigars == nullptr) != (cigar_offsets == nullptr)) return false;
@@ -258,6 +267,8 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     c->tune_cache = nullptr;
     c->adapt_min_len = 10;
     c->adapt_max_dist = 50;
+    c->genasm_w = 64;
+    c->genasm_o = 24;
     *out = c;
     return AIM_OK;
 }
@@ -292,10 +303,17 @@ int aim_set_wfa_adaptive(aim_ctx* ctx, int min_length, int max_distance) {
     return AIM_OK;
 }
 
+int aim_set_genasm_window(aim_ctx* ctx, int window, int overlap) {
+    if (!ctx || window < 1 || window > 64 || overlap < 0 || overlap >= window) return AIM_ERR_ARG;
+    ctx->genasm_w = window;
+    ctx->genasm_o = overlap;
+    return AIM_OK;
+}
+
 int aim_stats_reset(aim_ctx* ctx, aim_stream_t stream) {
     if (!ctx) return AIM_ERR_ARG;
     DeviceGuard g(ctx->device);
-    return cuda_status(cudaMemsetAsync(stats_of(ctx), 0, 4 * sizeof(uint64_t), (cudaStream_t)stream));
+    return cuda_status(cudaMemsetAsync(stats_of(ctx), 0, aim::kStats * sizeof(uint64_t), (cudaStream_t)stream));
 }
 
 int aim_stats_read(aim_ctx* ctx, uint64_t* out) {
@@ -303,7 +321,7 @@ int aim_stats_read(aim_ctx* ctx, uint64_t* out) {
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_status(e);
-    return cuda_status(cudaMemcpy(out, stats_of(ctx), 4 * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+    return cuda_status(cudaMemcpy(out, stats_of(ctx), aim::kStats * sizeof(uint64_t), cudaMemcpyDeviceToHost));
 }
 
 int aim_timing_enable(aim_ctx* ctx, int on) {
