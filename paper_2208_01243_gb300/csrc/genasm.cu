@@ -19,14 +19,16 @@
 //           | A_{d-1}(t+1)                                   D (target base)
 // which is the suffix edit-distance recurrence one distance level at a time.
 // Bits above wp-1 carry no meaning; shifts only move them further up.  The
-// window distance is the first d with bit wp-1 of A_d(0) set.
+// window distance is the first d with bit wp-1 of A_d(0) set.  A window whose
+// distance exceeds the edits left ends the pair: any way the alignment goes on
+// crosses the window's far edge, so the count only grows.
 //
-// Levels are computed in blocks of four, target position by target position
-// (t descending), so that a block keeps its four current vectors in registers
-// and reads only the top level of the block below from memory.  Every vector
-// is stored: the traceback needs level d-1 at two target positions per edit.
-// A window whose distance exceeds the edits left ends the pair: any way the
-// alignment goes on crosses the window's far edge, so the count only grows.
+// Sweeps.  Levels are computed in blocks of four, target position by target
+// position (t descending): a block keeps its four vectors in registers and
+// reads only the top level of the block below, A_{L0-1}(t), from a per-lane
+// carry row that it overwrites in place with its own top level.  The first
+// block needs no carry; when it does not reach the window's start, it is swept
+// again to fill the carry row and the following blocks run from it.
 //
 // Traceback, forward from (0, 0) with budget d (the window distance): after an
 // I, I first; after a D, D first; then M, X, I, D, each only when the rest still
@@ -34,23 +36,34 @@
 // values of neighbouring cells differ by at most one).  Match runs are taken
 // with 32-base XOR compares.  A non-final window stops once W-O read or W-O
 // target bases have been consumed in it; the final window runs to its corner.
+// The traceback reads level d-1 at target positions c and c+1 only, for c up
+// to W-O in a non-final window, and only near the diagonal: a path with d
+// edits never strays more than d diagonals.  So the stored copy of A_d(t) is
+// kept for t up to the last position the traceback can read, and, when no
+// window can need more than 14 levels, only as the 32 bits from 16 below the
+// diagonal position wp-1-t (or from bit 0).
 //
-// Scratch: per warp, levels x (W+1) x 32 words, lane-interleaved so that the
-// 32 lanes of a step store one contiguous 256-byte row.
+// Scratch per warp, lane-interleaved (32 lanes of a step store one contiguous
+// row): the carry row, (W+1) x 32 words, then levels x (W+1) x 32 stored
+// vectors (32 or 64 bits each).
+#include <type_traits>
+
 #include "aim_internal.cuh"
 
 namespace aim {
 namespace {
 
-constexpr int kGenasmBlock = 4;     // distance levels per register block
+constexpr int kGenasmBlock = 4;         // distance levels per register block
+constexpr int kBandLevels = 14;         // widest window distance a 32-bit band serves
 
 struct GenasmArgs {
     PairsView P;
     LimitView L;
     OutView O;
-    uint64_t* scratch;
+    uint8_t* scratch;
+    size_t warp_bytes;              // carry row + stored levels of one warp
+    size_t carry_bytes;             // offset of the stored levels inside a warp's scratch
     int W, overlap;
-    int levels;                     // level slots per lane (a multiple of kGenasmBlock)
     uint32_t nwarps;
     uint32_t* counter;
 };
@@ -58,6 +71,22 @@ struct GenasmArgs {
 constexpr uint32_t kNoOp = 0;
 
 __device__ __forceinline__ uint64_t low_bits(int d) { return d >= 64 ? ~0ull : ((1ull << d) - 1ull); }
+
+// The stored copy of A_d(t): the whole word, or the 32 bits from band_start(wp, t) up, which hold every bit
+// the traceback can ask for (within 16 of the diagonal position wp-1-t, never below bit 0).
+__device__ __forceinline__ int band_start(int wp, int t) { return max(wp - 17 - t, 0); }
+template <typename Band>
+__device__ __forceinline__ Band band_of(uint64_t v, int s);
+template <>
+__device__ __forceinline__ uint64_t band_of<uint64_t>(uint64_t v, int) { return v; }
+template <>
+__device__ __forceinline__ uint32_t band_of<uint32_t>(uint64_t v, int s) {   // bits s..s+31, s in [0, 47]
+    const uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+    return s < 32 ? __funnelshift_r(lo, hi, (uint32_t)s) : (hi >> (s - 32));
+}
+// bit b of a stored copy whose band starts at bit s
+__device__ __forceinline__ bool band_bit(uint64_t x, int b, int) { return (x >> b) & 1ull; }
+__device__ __forceinline__ bool band_bit(uint32_t x, int b, int s) { return (x >> (b - s)) & 1u; }
 
 // 32 even bits (bit 2s) of x -> bits s of the result
 __device__ __forceinline__ uint32_t even_bits(uint64_t x) {
@@ -89,13 +118,107 @@ __device__ __forceinline__ int match_run(const uint64_t* rw, uint32_t nrw, uint3
     return run < cap ? run : cap;
 }
 
-__global__ void __launch_bounds__(128, 8) genasm_kernel(GenasmArgs a) {
+struct Window {
+    uint64_t eq[4];     // read bases of the window, one mask per base code
+    uint64_t t0, t1;    // target bases 0..31 and 32..63 of the window
+    int wp, wt;
+    int tmax;           // last target position the traceback can read
+    bool end_r, end_t;
+};
+
+// One sweep of the four levels L0..L0+3 over t = wt..0.  FREE_R: the read goes on past the window (the
+// empty read suffix costs nothing); BANDS: store the levels for the traceback (positions up to w.tmax);
+// CARRY_OUT: overwrite the carry row with level L0+3; CARRY_IN: read level L0-1 from the carry row.
+template <typename Band, bool FREE_R, bool BANDS, bool CARRY_OUT, bool CARRY_IN>
+__device__ __forceinline__ void sweep(const Window& w, int L0, Band* lv, size_t lstride, uint64_t* carry,
+                                      uint64_t (&cur)[kGenasmBlock]) {
+    const int wp = w.wp, wt = w.wt;
+    const uint64_t edge = w.end_t ? 0ull : ~0ull;   // A_d(wt) = edge | low d bits
+#pragma unroll
+    for (int q = 0; q < kGenasmBlock; ++q) {
+        cur[q] = edge | low_bits(L0 + q);
+        if (BANDS && wt <= w.tmax)
+            lv[(size_t)(L0 + q) * lstride + (size_t)wt * 32] = band_of<Band>(cur[q], band_start(wp, wt));
+    }
+    if (CARRY_OUT) carry[(size_t)wt * 32] = cur[kGenasmBlock - 1];
+    uint64_t lo_old = CARRY_IN ? (edge | low_bits(L0 - 1)) : 0ull;   // A_{L0-1}(t+1)
+    auto step = [&](const int t, auto keep_tag) {
+        constexpr bool KEEP = decltype(keep_tag)::value;
+        const uint64_t tword = t < 32 ? w.t0 : w.t1;
+        const uint32_t code = (uint32_t)(tword >> (62 - 2 * (t & 31))) & 3u;
+        const uint64_t e01 = (code & 1) ? w.eq[1] : w.eq[0], e23 = (code & 1) ? w.eq[3] : w.eq[2];
+        const uint64_t eqc = (code & 2) ? e23 : e01;
+        const uint64_t lo_new = CARRY_IN ? carry[(size_t)t * 32] : 0ull;   // A_{L0-1}(t)
+        // the empty read suffix at t+1 fits level d iff the wt-t-1 target bases left fit: e(t+1, d) = [x <= q],
+        // e(t+1, d-1) = [x + 1 <= q] (which covers e(t, d-1) too); on a free read edge both are 1
+        const int x = wt - t - 1 - L0;
+        const int s = KEEP ? band_start(wp, t) : 0;
+        uint64_t b_old = lo_old, b_new = lo_new;
+#pragma unroll
+        for (int q = 0; q < kGenasmBlock; ++q) {
+            const uint64_t old = cur[q];
+            const uint64_t e1 = (FREE_R || x <= q) ? 1ull : 0ull;
+            uint64_t v = ((old << 1) | e1) & eqc;
+            if (CARRY_IN || q > 0) {
+                const uint64_t e2 = (FREE_R || x + 1 <= q) ? 1ull : 0ull;
+                v |= ((b_old | b_new) << 1) | e2 | b_old;
+            }
+            cur[q] = v;
+            if (KEEP) lv[(size_t)(L0 + q) * lstride + (size_t)t * 32] = band_of<Band>(v, s);
+            b_old = old;
+            b_new = v;
+        }
+        if (CARRY_OUT) carry[(size_t)t * 32] = cur[kGenasmBlock - 1];
+        lo_old = lo_new;
+    };
+    // positions past the last one the traceback can read are computed but not stored
+    const int split = BANDS ? min(w.tmax, wt - 1) : -1;
+    for (int t = wt - 1; t > split; --t) step(t, std::false_type{});
+    if (BANDS)
+        for (int t = split; t >= 0; --t) step(t, std::true_type{});
+}
+
+// The window's distance (the first level whose bit wp-1 is set at t = 0), or -1 if it exceeds lmax.
+template <typename Band, bool FREE_R>
+__device__ __forceinline__ int window_distance(const Window& w, int lmax, Band* lv, size_t lstride, uint64_t* carry,
+                                               unsigned long long& cells) {
+    uint64_t cur[kGenasmBlock];
+    int found = -1;
+    auto check = [&](int L0) {
+#pragma unroll
+        for (int q = 0; q < kGenasmBlock; ++q)
+            if (found < 0 && L0 + q <= lmax && ((cur[q] >> (w.wp - 1)) & 1ull)) found = L0 + q;
+    };
+    sweep<Band, FREE_R, true, false, false>(w, 0, lv, lstride, carry, cur);
+    cells += (unsigned long long)kGenasmBlock * w.wt;
+    check(0);
+    if (found < 0 && lmax >= kGenasmBlock) {
+        sweep<Band, FREE_R, false, true, false>(w, 0, lv, lstride, carry, cur);   // fill the carry row
+        for (int L0 = kGenasmBlock; found < 0 && L0 <= lmax; L0 += kGenasmBlock) {
+            if (L0 + kGenasmBlock <= lmax) sweep<Band, FREE_R, true, true, true>(w, L0, lv, lstride, carry, cur);
+            else sweep<Band, FREE_R, true, false, true>(w, L0, lv, lstride, carry, cur);
+            cells += (unsigned long long)kGenasmBlock * w.wt;
+            check(L0);
+        }
+    }
+    return found;
+}
+
+// 6 blocks of 128 threads per SM (80 registers) measured faster than 8 (64 registers, with spills)
+#ifndef AIM_GENASM_MIN_BLOCKS
+#define AIM_GENASM_MIN_BLOCKS 6
+#endif
+
+template <typename Band>
+__global__ void __launch_bounds__(128, AIM_GENASM_MIN_BLOCKS) genasm_kernel(GenasmArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
     const int W = a.W, stop = a.W - a.overlap;
-    const size_t row = (size_t)(W + 1) * 32;                     // words per level
-    uint64_t* S = a.scratch + (size_t)gwarp * a.levels * row + lane;
+    const size_t lstride = (size_t)(W + 1) * 32;                  // stored entries per level
+    uint8_t* slot = a.scratch + (size_t)gwarp * a.warp_bytes;
+    uint64_t* carry = reinterpret_cast<uint64_t*>(slot) + lane;
+    Band* lv = reinterpret_cast<Band*>(slot + a.carry_bytes) + lane;
     unsigned long long st_cells = 0, st_pairs = 0;
 
     for (;;) {
@@ -130,62 +253,27 @@ __global__ void __launch_bounds__(128, 8) genasm_kernel(GenasmArgs a) {
         int64_t used = 0;
         bool rejected = false;
         while (i < n && j < m) {
-            const int wp = (int)min(n - i, (uint32_t)W), wt = (int)min(m - j, (uint32_t)W);
-            const bool end_r = n - i <= (uint32_t)W, end_t = m - j <= (uint32_t)W, fin = end_r && end_t;
+            Window w;
+            w.wp = (int)min(n - i, (uint32_t)W);
+            w.wt = (int)min(m - j, (uint32_t)W);
+            w.end_r = n - i <= (uint32_t)W;
+            w.end_t = m - j <= (uint32_t)W;
+            const bool fin = w.end_r && w.end_t;
+            const int wp = w.wp, wt = w.wt;
+            w.tmax = fin ? wt : min(stop, wt);
             // read window masks: bit wp-1-a is read base i+a
             const uint64_t r0 = window32(rw, nrw, i), r1 = window32(rw, nrw, i + 32);
-            uint64_t eq[4];
 #pragma unroll
             for (uint32_t c = 0; c < 4; ++c)
-                eq[c] = (((uint64_t)match_bits(r0, c) << 32) | match_bits(r1, c)) >> (64 - wp);
-            const uint64_t t0 = window32(tw, ntw, j), t1 = window32(tw, ntw, j + 32);
+                w.eq[c] = (((uint64_t)match_bits(r0, c) << 32) | match_bits(r1, c)) >> (64 - wp);
+            w.t0 = window32(tw, ntw, j);
+            w.t1 = window32(tw, ntw, j + 32);
 
             // distance levels, blocks of four, until the window's start is reached
             const int64_t left = k - used;
             const int lmax = (int)(left < (int64_t)max(wp, wt) ? left : (int64_t)max(wp, wt));
-            const uint64_t edge = end_t ? 0ull : ~0ull;       // A_d(wt) = edge | low d bits
-            int found = -1;
-            for (int L0 = 0; found < 0 && L0 <= lmax; L0 += kGenasmBlock) {
-                uint64_t cur[kGenasmBlock];
-#pragma unroll
-                for (int q = 0; q < kGenasmBlock; ++q) {
-                    cur[q] = edge | low_bits(L0 + q);
-                    S[((size_t)(L0 + q) * (W + 1) + wt) * 32] = cur[q];
-                }
-                uint64_t lo_old = L0 ? (edge | low_bits(L0 - 1)) : 0ull;   // A_{L0-1}(t+1)
-                const uint64_t* below = L0 ? S + (size_t)(L0 - 1) * row : S;   // level L0-1 (read only when L0 > 0)
-                for (int t = wt - 1; t >= 0; --t) {
-                    const uint64_t tword = t < 32 ? t0 : t1;
-                    const uint32_t code = (uint32_t)(tword >> (62 - 2 * (t & 31))) & 3u;
-                    const uint64_t e01 = (code & 1) ? eq[1] : eq[0], e23 = (code & 1) ? eq[3] : eq[2];
-                    const uint64_t eqc = (code & 2) ? e23 : e01;
-                    const uint64_t lo_new = L0 ? below[(size_t)t * 32] : 0ull;   // A_{L0-1}(t)
-                    const int r = wt - t;                                         // target bases t..wt-1
-                    uint64_t b_old = lo_old, b_new = lo_new;
-#pragma unroll
-                    for (int q = 0; q < kGenasmBlock; ++q) {
-                        const int d = L0 + q;
-                        const uint64_t old = cur[q];
-                        // e(t+1, d) = [f(wp, t+1) <= d]: free edge, or the r-1 target bases left fit in d
-                        const uint64_t e1 = (!end_r || r - 1 <= d) ? 1ull : 0ull;
-                        uint64_t v = ((old << 1) | e1) & eqc;
-                        if (d > 0) {
-                            // e(t+1, d-1) covers e(t, d-1) too (fewer bases left at t+1)
-                            const uint64_t e2 = (!end_r || r <= d) ? 1ull : 0ull;
-                            v |= ((b_old | b_new) << 1) | e2 | b_old;
-                        }
-                        cur[q] = v;
-                        S[((size_t)d * (W + 1) + t) * 32] = v;
-                        b_old = old;
-                        b_new = v;
-                    }
-                    lo_old = lo_new;
-                }
-                st_cells += (unsigned long long)kGenasmBlock * wt;
-#pragma unroll
-                for (int q = 0; q < kGenasmBlock; ++q)
-                    if (found < 0 && L0 + q <= lmax && ((cur[q] >> (wp - 1)) & 1ull)) found = L0 + q;
-            }
+            const int found = w.end_r ? window_distance<Band, false>(w, lmax, lv, lstride, carry, st_cells)
+                                      : window_distance<Band, true>(w, lmax, lv, lstride, carry, st_cells);
             if (found < 0) { rejected = true; break; }
 
             // traceback
@@ -206,12 +294,13 @@ __global__ void __launch_bounds__(128, 8) genasm_kernel(GenasmArgs a) {
                     const int b = wp - 1 - ta;
                     bool fI = false, fD = false, fX = false;
                     if (d > 0) {
-                        const uint64_t* lv = S + (size_t)(d - 1) * row;
-                        const uint64_t at_c = lv[(size_t)tc * 32], at_c1 = lv[(size_t)(tc + 1) * 32];
-                        const bool e_c = !end_r || wt - tc <= d - 1, e_c1 = !end_r || wt - tc - 1 <= d - 1;
-                        fI = b >= 1 ? ((at_c >> (b - 1)) & 1ull) : e_c;
-                        fD = (at_c1 >> b) & 1ull;
-                        fX = b >= 1 ? ((at_c1 >> (b - 1)) & 1ull) : e_c1;
+                        const Band* ld = lv + (size_t)(d - 1) * lstride;
+                        const Band at_c = ld[(size_t)tc * 32], at_c1 = ld[(size_t)(tc + 1) * 32];
+                        const int p_c = band_start(wp, tc), p_c1 = band_start(wp, tc + 1);
+                        const bool e_c = !w.end_r || wt - tc <= d - 1, e_c1 = !w.end_r || wt - tc - 1 <= d - 1;
+                        fI = b >= 1 ? band_bit(at_c, b - 1, p_c) : e_c;
+                        fD = band_bit(at_c1, b, p_c1);
+                        fX = b >= 1 ? band_bit(at_c1, b - 1, p_c1) : e_c1;
                     }
                     if (prev == kOpIns && fI) op = kOpIns;
                     else if (prev == kOpDel && fD) op = kOpDel;
@@ -253,13 +342,21 @@ __global__ void __launch_bounds__(128, 8) genasm_kernel(GenasmArgs a) {
     warp_stat_add(a.O.stats, 3, st_pairs, lane);
 }
 
-}  // namespace
-
-size_t genasm_warp_bytes(int W, int levels) { return (size_t)levels * (W + 1) * 32 * sizeof(uint64_t); }
-
-int genasm_levels(int W, int64_t max_limit) {
+// distance levels a window can need under the largest threshold, in whole register blocks
+int levels_for(int W, int64_t max_limit) {
     const int64_t top = max_limit < W ? max_limit : W;   // a window's distance never exceeds W
     return (int)((top + 1 + kGenasmBlock - 1) / kGenasmBlock * kGenasmBlock);
+}
+
+bool banded(int W, int64_t max_limit) { return (max_limit < W ? max_limit : W) <= kBandLevels; }
+
+size_t carry_bytes_for(int W) { return align_up((size_t)(W + 1) * 32 * sizeof(uint64_t), 256); }
+
+}  // namespace
+
+size_t genasm_warp_bytes(int W, int64_t max_limit) {
+    const size_t band = banded(W, max_limit) ? sizeof(uint32_t) : sizeof(uint64_t);
+    return carry_bytes_for(W) + align_up((size_t)levels_for(W, max_limit) * (W + 1) * 32 * band, 256);
 }
 
 cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, const OutView& Ov, int64_t max_limit,
@@ -270,25 +367,30 @@ cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, 
     GenasmArgs a;
     a.P = P; a.L = L; a.O = Ov;
     a.W = W; a.overlap = O;
-    a.levels = genasm_levels(W, max_limit);
     a.counter = counter;
-    // scratch rows must start on 256-byte boundaries for whole-row stores
+    a.carry_bytes = carry_bytes_for(W);
+    a.warp_bytes = genasm_warp_bytes(W, max_limit);
+    // warp slots start on 256-byte boundaries so that every stored row is one aligned segment
     uint8_t* base = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<size_t>(scratch), 256));
     const size_t skip = (size_t)(base - scratch);
     if (skip >= scratch_bytes) return cudaSuccess;
-    a.scratch = reinterpret_cast<uint64_t*>(base);
+    a.scratch = base;
+    const bool band = banded(W, max_limit);
     int bps = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, genasm_kernel, 128, 0);
+    cudaError_t err = band ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, genasm_kernel<uint32_t>, 128, 0)
+                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, genasm_kernel<uint64_t>, 128, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     size_t warps = (size_t)num_sms * bps * 4;
-    const size_t fit = (scratch_bytes - skip) / genasm_warp_bytes(W, a.levels);
+    const size_t fit = (scratch_bytes - skip) / a.warp_bytes;
     if (warps > fit) warps = fit;
     const size_t need = ((size_t)P.num_pairs + 31) / 32;
     if (warps > need) warps = need;
     if (warps == 0) return cudaSuccess;
     a.nwarps = (uint32_t)warps;
-    genasm_kernel<<<(unsigned)((warps + 3) / 4), 128, 0, st>>>(a);
+    const unsigned blocks = (unsigned)((warps + 3) / 4);
+    if (band) genasm_kernel<uint32_t><<<blocks, 128, 0, st>>>(a);
+    else genasm_kernel<uint64_t><<<blocks, 128, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
 }
