@@ -165,7 +165,7 @@ cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const
                        int* warps_used);
 
 // GenASM (windowed bitap): scratch per warp for windows of W bases under the largest threshold max_limit
-size_t genasm_warp_bytes(int W, int64_t max_limit);
+size_t genasm_warp_bytes(int W, int64_t max_limit, uint32_t max_length);
 cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, const OutView& Ov, int64_t max_limit,
                           uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
                           int* warps_used);

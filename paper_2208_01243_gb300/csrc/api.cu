@@ -137,7 +137,8 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
     int slot = -1;
     if (algo == AIM_ALGO_GENASM) {
         if (pen->band >= 0) return AIM_ERR_UNSUPPORTED;
-        if (aim::genasm_warp_bytes(ctx->genasm_w, r.max_limit) + 256 > scratch_bytes) return AIM_ERR_NOMEM;
+        if (aim::genasm_warp_bytes(ctx->genasm_w, r.max_limit, P.max_length) + 256 > scratch_bytes)
+            return AIM_ERR_NOMEM;
         slot = time_begin(ctx, 1, st);
         err = aim::launch_genasm(ctx->genasm_w, ctx->genasm_o, P, r.lim, O, r.max_limit, scratch, scratch_bytes,
                                  counter, ctx->num_sms, st, &warps);

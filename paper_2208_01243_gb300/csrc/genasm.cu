@@ -23,12 +23,11 @@
 // distance exceeds the edits left ends the pair: any way the alignment goes on
 // crosses the window's far edge, so the count only grows.
 //
-// Sweeps.  Levels are computed in blocks of four, target position by target
-// position (t descending): a block keeps its four vectors in registers and
+// Sweeps.  Levels are computed in blocks of four or eight, target position by
+// target position (t descending): a block keeps its vectors in registers and
 // reads only the top level of the block below, A_{L0-1}(t), from a per-lane
-// carry row that it overwrites in place with its own top level.  The first
-// block needs no carry; when it does not reach the window's start, it is swept
-// again to fill the carry row and the following blocks run from it.
+// carry row that it overwrites in place with its own top level (written only
+// when another block may follow).
 //
 // Traceback, forward from (0, 0) with budget d (the window distance): after an
 // I, I first; after a D, D first; then M, X, I, D, each only when the rest still
@@ -53,7 +52,10 @@
 namespace aim {
 namespace {
 
-constexpr int kGenasmBlock = 4;         // distance levels per register block
+// distance levels per register block, one size per call: blocks of 8 when the threshold allows about two or
+// more edits per window (then most windows would need a second block of 4, and a whole warp waits for the
+// sweeps any one of its lanes needs), blocks of 4 otherwise
+constexpr int kSmallBlock = 4, kBigBlock = 8;
 constexpr int kBandLevels = 14;         // widest window distance a 32-bit band serves
 
 struct GenasmArgs {
@@ -64,6 +66,7 @@ struct GenasmArgs {
     size_t warp_bytes;              // carry row + stored levels of one warp
     size_t carry_bytes;             // offset of the stored levels inside a warp's scratch
     int W, overlap;
+    bool big_blocks;                // blocks of kBigBlock levels (else kSmallBlock)
     uint32_t nwarps;
     uint32_t* counter;
 };
@@ -126,21 +129,21 @@ struct Window {
     bool end_r, end_t;
 };
 
-// One sweep of the four levels L0..L0+3 over t = wt..0.  FREE_R: the read goes on past the window (the
+// One sweep of the B levels L0..L0+B-1 over t = wt..0.  FREE_R: the read goes on past the window (the
 // empty read suffix costs nothing); BANDS: store the levels for the traceback (positions up to w.tmax);
-// CARRY_OUT: overwrite the carry row with level L0+3; CARRY_IN: read level L0-1 from the carry row.
-template <typename Band, bool FREE_R, bool BANDS, bool CARRY_OUT, bool CARRY_IN>
+// CARRY_OUT: overwrite the carry row with level L0+B-1; CARRY_IN: read level L0-1 from the carry row.
+template <int B, typename Band, bool FREE_R, bool BANDS, bool CARRY_OUT, bool CARRY_IN>
 __device__ __forceinline__ void sweep(const Window& w, int L0, Band* lv, size_t lstride, uint64_t* carry,
-                                      uint64_t (&cur)[kGenasmBlock]) {
+                                      uint64_t (&cur)[B]) {
     const int wp = w.wp, wt = w.wt;
     const uint64_t edge = w.end_t ? 0ull : ~0ull;   // A_d(wt) = edge | low d bits
 #pragma unroll
-    for (int q = 0; q < kGenasmBlock; ++q) {
+    for (int q = 0; q < B; ++q) {
         cur[q] = edge | low_bits(L0 + q);
         if (BANDS && wt <= w.tmax)
             lv[(size_t)(L0 + q) * lstride + (size_t)wt * 32] = band_of<Band>(cur[q], band_start(wp, wt));
     }
-    if (CARRY_OUT) carry[(size_t)wt * 32] = cur[kGenasmBlock - 1];
+    if (CARRY_OUT) carry[(size_t)wt * 32] = cur[B - 1];
     uint64_t lo_old = CARRY_IN ? (edge | low_bits(L0 - 1)) : 0ull;   // A_{L0-1}(t+1)
     auto step = [&](const int t, auto keep_tag) {
         constexpr bool KEEP = decltype(keep_tag)::value;
@@ -155,7 +158,7 @@ __device__ __forceinline__ void sweep(const Window& w, int L0, Band* lv, size_t 
         const int s = KEEP ? band_start(wp, t) : 0;
         uint64_t b_old = lo_old, b_new = lo_new;
 #pragma unroll
-        for (int q = 0; q < kGenasmBlock; ++q) {
+        for (int q = 0; q < B; ++q) {
             const uint64_t old = cur[q];
             const uint64_t e1 = (FREE_R || x <= q) ? 1ull : 0ull;
             uint64_t v = ((old << 1) | e1) & eqc;
@@ -168,7 +171,7 @@ __device__ __forceinline__ void sweep(const Window& w, int L0, Band* lv, size_t 
             b_old = old;
             b_new = v;
         }
-        if (CARRY_OUT) carry[(size_t)t * 32] = cur[kGenasmBlock - 1];
+        if (CARRY_OUT) carry[(size_t)t * 32] = cur[B - 1];
         lo_old = lo_new;
     };
     // positions past the last one the traceback can read are computed but not stored
@@ -178,35 +181,41 @@ __device__ __forceinline__ void sweep(const Window& w, int L0, Band* lv, size_t 
         for (int t = split; t >= 0; --t) step(t, std::true_type{});
 }
 
-// The window's distance (the first level whose bit wp-1 is set at t = 0), or -1 if it exceeds lmax.
-template <typename Band, bool FREE_R>
-__device__ __forceinline__ int window_distance(const Window& w, int lmax, Band* lv, size_t lstride, uint64_t* carry,
-                                               unsigned long long& cells) {
-    uint64_t cur[kGenasmBlock];
+// Levels from L0 on in blocks of B until one reaches the window's start (or lmax is passed); the first
+// block (L0 = 0) reads no carry.  Returns the window's distance or -1.
+template <int B, typename Band, bool FREE_R>
+__device__ __forceinline__ int blocks_from(const Window& w, int lmax, Band* lv, size_t lstride, uint64_t* carry) {
+    uint64_t cur[B];
     int found = -1;
-    auto check = [&](int L0) {
-#pragma unroll
-        for (int q = 0; q < kGenasmBlock; ++q)
-            if (found < 0 && L0 + q <= lmax && ((cur[q] >> (w.wp - 1)) & 1ull)) found = L0 + q;
-    };
-    sweep<Band, FREE_R, true, false, false>(w, 0, lv, lstride, carry, cur);
-    cells += (unsigned long long)kGenasmBlock * w.wt;
-    check(0);
-    if (found < 0 && lmax >= kGenasmBlock) {
-        sweep<Band, FREE_R, false, true, false>(w, 0, lv, lstride, carry, cur);   // fill the carry row
-        for (int L0 = kGenasmBlock; found < 0 && L0 <= lmax; L0 += kGenasmBlock) {
-            if (L0 + kGenasmBlock <= lmax) sweep<Band, FREE_R, true, true, true>(w, L0, lv, lstride, carry, cur);
-            else sweep<Band, FREE_R, true, false, true>(w, L0, lv, lstride, carry, cur);
-            cells += (unsigned long long)kGenasmBlock * w.wt;
-            check(L0);
+    for (int L0 = 0; found < 0 && L0 <= lmax; L0 += B) {
+        // a block fills the carry row whenever another may follow: lanes of a warp move together, so one lane
+        // that needs the next block makes the whole warp wait for it
+        const bool more = L0 + B <= lmax;
+        if (L0 == 0) {
+            if (more) sweep<B, Band, FREE_R, true, true, false>(w, 0, lv, lstride, carry, cur);
+            else sweep<B, Band, FREE_R, true, false, false>(w, 0, lv, lstride, carry, cur);
+        } else {
+            if (more) sweep<B, Band, FREE_R, true, true, true>(w, L0, lv, lstride, carry, cur);
+            else sweep<B, Band, FREE_R, true, false, true>(w, L0, lv, lstride, carry, cur);
         }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+            if (found < 0 && L0 + q <= lmax && ((cur[q] >> (w.wp - 1)) & 1ull)) found = L0 + q;
     }
     return found;
 }
 
-// 6 blocks of 128 threads per SM (80 registers) measured faster than 8 (64 registers, with spills)
+// The window's distance (the first level whose bit wp-1 is set at t = 0), or -1 if it exceeds lmax.
+template <typename Band, bool FREE_R>
+__device__ __forceinline__ int window_distance(const Window& w, int lmax, bool big, Band* lv, size_t lstride,
+                                               uint64_t* carry) {
+    return big ? blocks_from<kBigBlock, Band, FREE_R>(w, lmax, lv, lstride, carry)
+               : blocks_from<kSmallBlock, Band, FREE_R>(w, lmax, lv, lstride, carry);
+}
+
+// 5 blocks of 128 threads per SM (96 registers) measured faster than 6 (80) or 8 (64, with spills)
 #ifndef AIM_GENASM_MIN_BLOCKS
-#define AIM_GENASM_MIN_BLOCKS 6
+#define AIM_GENASM_MIN_BLOCKS 5
 #endif
 
 template <typename Band>
@@ -269,11 +278,13 @@ __global__ void __launch_bounds__(128, AIM_GENASM_MIN_BLOCKS) genasm_kernel(Gena
             w.t0 = window32(tw, ntw, j);
             w.t1 = window32(tw, ntw, j + 32);
 
-            // distance levels, blocks of four, until the window's start is reached
+            // distance levels, in blocks, until the window's start is reached
             const int64_t left = k - used;
             const int lmax = (int)(left < (int64_t)max(wp, wt) ? left : (int64_t)max(wp, wt));
-            const int found = w.end_r ? window_distance<Band, false>(w, lmax, lv, lstride, carry, st_cells)
-                                      : window_distance<Band, true>(w, lmax, lv, lstride, carry, st_cells);
+            const int found = w.end_r ? window_distance<Band, false>(w, lmax, a.big_blocks, lv, lstride, carry)
+                                      : window_distance<Band, true>(w, lmax, a.big_blocks, lv, lstride, carry);
+            // work of a plain bitap: levels 0..d (0..lmax when the window is over the budget) at every position
+            st_cells += (unsigned long long)((found < 0 ? lmax : found) + 1) * wt;
             if (found < 0) { rejected = true; break; }
 
             // traceback
@@ -342,10 +353,17 @@ __global__ void __launch_bounds__(128, AIM_GENASM_MIN_BLOCKS) genasm_kernel(Gena
     warp_stat_add(a.O.stats, 3, st_pairs, lane);
 }
 
+// blocks of kBigBlock levels when the threshold allows about two or more edits per window of W bases
+bool big_blocks_for(int W, int64_t max_limit, uint32_t max_length) {
+    const int64_t len = max_length > (uint32_t)W ? (int64_t)max_length : (int64_t)W;
+    return max_limit >= kSmallBlock && max_limit * W >= 2 * len;
+}
+
 // distance levels a window can need under the largest threshold, in whole register blocks
-int levels_for(int W, int64_t max_limit) {
+int levels_for(int W, int64_t max_limit, bool big) {
     const int64_t top = max_limit < W ? max_limit : W;   // a window's distance never exceeds W
-    return (int)((top + 1 + kGenasmBlock - 1) / kGenasmBlock * kGenasmBlock);
+    const int B = big ? kBigBlock : kSmallBlock;
+    return (int)((top + 1 + B - 1) / B * B);
 }
 
 bool banded(int W, int64_t max_limit) { return (max_limit < W ? max_limit : W) <= kBandLevels; }
@@ -354,9 +372,10 @@ size_t carry_bytes_for(int W) { return align_up((size_t)(W + 1) * 32 * sizeof(ui
 
 }  // namespace
 
-size_t genasm_warp_bytes(int W, int64_t max_limit) {
+size_t genasm_warp_bytes(int W, int64_t max_limit, uint32_t max_length) {
     const size_t band = banded(W, max_limit) ? sizeof(uint32_t) : sizeof(uint64_t);
-    return carry_bytes_for(W) + align_up((size_t)levels_for(W, max_limit) * (W + 1) * 32 * band, 256);
+    const int levels = levels_for(W, max_limit, big_blocks_for(W, max_limit, max_length));
+    return carry_bytes_for(W) + align_up((size_t)levels * (W + 1) * 32 * band, 256);
 }
 
 cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, const OutView& Ov, int64_t max_limit,
@@ -369,7 +388,8 @@ cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, 
     a.W = W; a.overlap = O;
     a.counter = counter;
     a.carry_bytes = carry_bytes_for(W);
-    a.warp_bytes = genasm_warp_bytes(W, max_limit);
+    a.big_blocks = big_blocks_for(W, max_limit, P.max_length);
+    a.warp_bytes = genasm_warp_bytes(W, max_limit, P.max_length);
     // warp slots start on 256-byte boundaries so that every stored row is one aligned segment
     uint8_t* base = reinterpret_cast<uint8_t*>(align_up(reinterpret_cast<size_t>(scratch), 256));
     const size_t skip = (size_t)(base - scratch);
