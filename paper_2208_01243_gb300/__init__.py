@@ -405,6 +405,8 @@ def upload(*arrays, device: int = 0):
     out = []
     for a in arrays:
         a = np.ascontiguousarray(a)
+        if not a.flags.writeable:    # torch wraps only writable arrays; the copy to the device reads it once
+            a = a.copy()
         if a.dtype == np.uint64:
             a = a.view(np.int64)
         elif a.dtype == np.uint32:

@@ -1,8 +1,16 @@
 // 2-bit packer: ASCII A/C/G/T -> 0/1/2/3, first base in the top two bits of each 64-bit word.
 //
-// One warp per sequence; each lane converts one byte per 32-base word and the
-// warp ORs the lanes' 2-bit codes together (two 32-bit halves).  Lane w%32
-// keeps word w and the warp stores 32 words at a time with one coalesced store.
+// Fixed slots (every sequence at word i * stride, the form the ASCII entry points use): one thread per output
+// word.  It reads the word's 32 bytes as aligned 4-byte loads (each load holds at least one byte of the word, so
+// none crosses into another page), lines them up with funnel shifts, and converts four bytes at a time:
+// ((c >> 1) ^ (c >> 2)) & 3 maps A, C, G, T (0x41, 0x43, 0x47, 0x54) to 0, 1, 2, 3; a 4-byte compare against the
+// four letters flags anything else; one multiply gathers the four 2-bit codes into a byte, first base on top.
+//
+// Explicit word offsets (aim_pack_2bit): one warp per sequence; each lane converts one byte per 32-base word
+// and the warp ORs the lanes' 2-bit codes together (two 32-bit halves).  Lane w%32 keeps word w and the warp
+// stores 32 words at a time with one coalesced store.
+#include <type_traits>
+
 #include "aim_internal.cuh"
 
 namespace aim {
@@ -56,6 +64,60 @@ __global__ void __launch_bounds__(256) pack_kernel(const uint8_t* __restrict__ a
     }
 }
 
+// four ASCII bytes (first in the low byte) -> their 2-bit codes, first base in bits 7..6; *bad: a byte in `keep`
+// (0xff per byte to look at) that is not A, C, G or T
+__device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t keep, bool& bad) {
+    const uint32_t ok = __vcmpeq4(x, 0x41414141u) | __vcmpeq4(x, 0x43434343u) | __vcmpeq4(x, 0x47474747u) |
+                        __vcmpeq4(x, 0x54545454u);
+    bad |= (~ok & keep) != 0;
+    const uint32_t codes = ((x >> 1) ^ (x >> 2)) & 0x03030303u & keep;
+    // byte k holds code k; times 2^30 + 2^20 + 2^10 + 1 puts code k at bits 30-2k..31-2k with no carries
+    return (codes * 0x40100401u) >> 24;
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(256) pack_words_kernel(const uint8_t* __restrict__ ascii,
+                                                         const uint64_t* __restrict__ char_off,
+                                                         const uint32_t* __restrict__ len, uint32_t count,
+                                                         uint64_t* __restrict__ packed, uint32_t stride,
+                                                         uint8_t* __restrict__ bad) {
+    using Index = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
+    const Index total = (Index)count * stride;
+    for (Index g = (Index)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (Index)gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)(g / stride);
+        const uint32_t w = (uint32_t)(g - (Index)i * stride);
+        const uint32_t L = __ldg(len + i);
+        const uint32_t nw = (L + 31) >> 5;
+        if (nw > stride) {   // longer than the fixed per-sequence slot: flag, write nothing
+            if (bad && w == 0) bad[i] = 1;
+            continue;
+        }
+        if (w >= nw) continue;
+        // first byte of this word; alignment is taken from the address itself (the buffer may start anywhere)
+        const uintptr_t at = reinterpret_cast<uintptr_t>(ascii) + __ldg(char_off + i) + 32ull * w;
+        const uint32_t nb = min(32u, L - 32u * w);              // bytes of this word
+        const uint32_t* base = reinterpret_cast<const uint32_t*>(at & ~(uintptr_t)3);
+        const uint32_t sh = 8u * (uint32_t)(at & 3);
+        const uint32_t last = (uint32_t)(((at & 3) + nb - 1) >> 2);     // last aligned word holding a byte
+        uint32_t u[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) u[q] = (uint32_t)q <= last ? __ldg(base + q) : 0u;
+        bool b = false;
+        uint32_t hi = 0, lo = 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const uint32_t x = __funnelshift_r(u[q], u[q + 1], sh);
+            const int have = (int)nb - 4 * q;                       // bytes of this group inside the word
+            const uint32_t keep = have >= 4 ? 0xffffffffu : have <= 0 ? 0u : ((1u << (8 * have)) - 1u);
+            const uint32_t byte = pack4(x, keep, b);
+            if (q < 4) hi |= byte << (24 - 8 * q);
+            else lo |= byte << (24 - 8 * (q - 4));
+        }
+        packed[g] = ((uint64_t)hi << 32) | lo;
+        if (bad && b) bad[i] = 1;
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const uint32_t* len, uint32_t count,
@@ -65,6 +127,24 @@ cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const ui
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (!word_off && word_stride > 0 && word_stride <= 0xffffffffull) {
+        // fixed slots: one thread per word; bad flags start at 0 and threads that see a bad byte set them
+        if (bad) {
+            const cudaError_t e = cudaMemsetAsync(bad, 0, count, st);
+            if (e != cudaSuccess) return e;
+        }
+        const uint64_t total = (uint64_t)count * word_stride;
+        uint64_t blocks = (total + 255) / 256;
+        const uint64_t cap = (uint64_t)sms * 32;   // grid-stride beyond 32 blocks of 256 per SM
+        if (blocks > cap) blocks = cap;
+        if (total <= 0xffffffffull)
+            pack_words_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(ascii, char_off, len, count, packed,
+                                                                        (uint32_t)word_stride, bad);
+        else
+            pack_words_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(ascii, char_off, len, count, packed,
+                                                                       (uint32_t)word_stride, bad);
+        return cudaGetLastError();
+    }
     const uint32_t warps_needed = count;
     uint32_t blocks = (warps_needed + 7) / 8;
     const uint32_t cap = (uint32_t)sms * 8;   // 8 blocks of 8 warps per SM, grid-stride beyond that

@@ -185,6 +185,57 @@ def test_device_packer_matches_layout(aligner):
     assert list(bad.cpu().numpy()) == [0] * (len(seqs) - 1) + [1]
 
 
+@pytest.mark.parametrize("shift", [0, 1, 2, 3])
+def test_ascii_path_odd_buffer_addresses_and_bad_bytes(aligner, oracle_lib, shift):
+    """The fixed-slot packer behind the ASCII entry point: input buffers starting at any byte address, lengths
+    across partial 4-byte groups and words, and a non-ACGT byte at every position class flags the pair."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    rng = np.random.default_rng(40 + shift)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    reads, targets, bad = [], [], []
+    for L in list(range(0, 70)) + [95, 96, 97, 127, 128, 129, 200]:
+        r = bytearray(rng.choice(acgt, L).tobytes())
+        t = bytearray(r)
+        if L and rng.random() < 0.5:
+            t[int(rng.integers(L))] = int(rng.choice(acgt))
+        b = False
+        if L and L % 5 == 0:   # a bad byte in the read or the target, anywhere
+            which = r if L % 10 == 0 else t
+            which[int(rng.integers(L))] = int(rng.choice(np.frombuffer(b"Nacgt.", np.uint8)))
+            b = True
+        reads.append(bytes(r)); targets.append(bytes(t)); bad.append(b)
+    p = gen.from_strings(reads, targets)
+    n = len(p)
+    dev = torch.device("cuda", 0)
+
+    def shifted(a):
+        buf = torch.zeros(len(a) + shift + 8, dtype=torch.uint8, device=dev)
+        buf[shift:shift + len(a)] = torch.from_numpy(a).to(dev)
+        return buf[shift:]                      # a view whose data pointer is `shift` bytes past an aligned one
+    rd, td = shifted(p.reads), shifted(p.targets)
+    rl, tl, ro, to = aim.upload(p.read_len, p.target_len, p.read_off, p.target_off)
+    cap = (p.read_len.astype(np.int64) + p.target_len.astype(np.int64) + 1)
+    off = np.zeros(n + 1, np.int64); off[1:] = np.cumsum(cap)
+    coff = aim.upload(off)[0]
+    scores = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    lens = torch.zeros(n, dtype=torch.int32, device=dev)
+    cig = torch.zeros(int(off[-1]), dtype=torch.int32, device=dev)
+    aim.aim_align_batch_ascii(aligner.ctx, rd, td, ro, to, rl, tl, 200, "edit", aim.penalties(1, 0, 1), 100, None,
+                              scores, cig, coff, lens, flags)
+    torch.cuda.synchronize()
+    s_, f_ = scores.cpu().numpy(), flags.cpu().numpy()
+    cg = cig.cpu().numpy().view(np.uint32); ln = lens.cpu().numpy()
+    for i in range(n):
+        if bad[i]:
+            assert (s_[i], f_[i]) == (-1, oracle.F_BAD_PAIR), i
+            continue
+        sc, fl, runs = oracle.align(p.read(i), p.target(i), oracle.UNIT)
+        assert (s_[i], f_[i]) == (sc, fl), i
+        assert list(cg[off[i]:off[i] + ln[i]]) == runs, i
+
+
 def test_results_independent_of_batch_composition(aligner, gen_lib):
     """Each pair's result is the same alone, in a shuffled batch and with a small workspace."""
     p = gen.generate(gen.WFA_UNEVEN, 600)
