@@ -331,10 +331,13 @@ def run_ours(args, w, algo):
                                   max_edits, d.get("pp"), out["scores"], out["cigars"], coff_d, out["lens"],
                                   out["flags"], scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=True)
         groups, counts = aim.aim_batch_info(plan)
+        first_pass, full_pass, n_compact = aim.aim_batch_passes(plan)
 
         def step(src=None):
             aim.aim_batch_run(plan)
-        launches_per_step = 6          # kernels per replay: 2 pack, bucket count/scan/scatter, alignment
+        # kernels per replay: 2 pack, bucket count/scan/scatter, alignment; a compact first pass adds the second
+        # pass's count/scan/scatter and alignment
+        launches_per_step = 6 + (4 if n_compact else 0)
     else:
         def step(src=None):
             src = src or d
@@ -416,6 +419,8 @@ def run_ours(args, w, algo):
                  "launches_per_step": len(gd) * 3, "length_groups": len(gd), "results_identical": same,
                  "batched_over_plain": pms / ms,
                  "batched_lanes_per_bucket": {str(k): g for k, (g, c) in enumerate(zip(groups, counts)) if c},
+                 "batched_compact_first_pass": {str(k): [f, g] for k, (f, g, c) in
+                                                enumerate(zip(first_pass, full_pass, counts)) if c and f},
                  "batched_pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c}}
         del gd
 

@@ -255,8 +255,24 @@ AIM_API int aim_batch_plan(aim_ctx *ctx, const uint8_t *reads, const uint8_t *ta
                            const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
                            size_t scratch_bytes, int autotune, aim_batch **out);
 AIM_API int aim_batch_run(aim_batch *batch, aim_stream_t stream);
-/* Per bucket (32): lanes per pair in use and pairs seen at planning; returns the bucket count. */
+/* Per bucket (32): lanes per pair of its first pass and pairs seen at planning; returns the bucket count. */
 AIM_API int aim_batch_info(aim_batch *batch, int *groups /* host[32] */, uint32_t *counts /* host[32] */);
+/*
+ * Two passes.  A bucket's full scratch is its worst case, which for long pairs
+ * under a loose threshold leaves room for one pair per warp, while most pairs
+ * end far below their threshold.  A bucket can therefore run a compact first
+ * pass (fewer lanes per pair, a history of about 16 diagonals per lane) and
+ * leave the pairs that outgrow it to a second pass with the full scratch; the
+ * plan then builds the second pass's queues on the device from the first
+ * pass's flags.  Results are the same either way (both passes are the exact
+ * algorithm).  aim_batch_passes reports, per bucket, the first-pass lanes (0:
+ * one pass only) and the full-pass lanes; it returns the number of buckets with
+ * a compact first pass.  aim_set_batch_compact sets how later plans of the
+ * context choose: 0 (default) by timed trials when autotuning, 1 always where
+ * the scratch allows, 2 never.
+ */
+AIM_API int aim_batch_passes(aim_batch *batch, int *first_pass /* host[32] */, int *full_pass /* host[32] */);
+AIM_API int aim_set_batch_compact(aim_ctx *ctx, int mode);
 AIM_API int aim_batch_destroy(aim_batch *batch);
 
 /*

@@ -70,6 +70,8 @@ def _lib():
         lib.aim_set_wfa_group.argtypes = [p, ctypes.c_int]
         lib.aim_set_wfa_adaptive.argtypes = [p, ctypes.c_int, ctypes.c_int]
         lib.aim_set_genasm_window.argtypes = [p, ctypes.c_int, ctypes.c_int]
+        lib.aim_set_batch_compact.argtypes = [p, ctypes.c_int]
+        lib.aim_batch_passes.argtypes = [p, p, p]
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
@@ -272,6 +274,21 @@ def aim_server_stats(server) -> dict:
 
 def aim_server_destroy(server) -> None:
     _check(_lib().aim_server_destroy(server), "aim_server_destroy")
+
+
+def aim_set_batch_compact(ctx, mode: int = 0) -> None:
+    """Batch plans of this context: 0 tuner decides on compact first passes, 1 always, 2 never."""
+    _check(_lib().aim_set_batch_compact(ctx, int(mode)), "aim_set_batch_compact")
+
+
+def aim_batch_passes(plan) -> tuple[list[int], list[int], int]:
+    """(first-pass lanes per bucket (0: one pass), full-pass lanes per bucket, buckets with a compact pass)."""
+    import numpy as np
+    first = np.zeros(32, np.int32); full = np.zeros(32, np.int32)
+    n = _lib().aim_batch_passes(plan, ctypes.c_void_p(first.ctypes.data), ctypes.c_void_p(full.ctypes.data))
+    if n < 0:
+        _check(n, "aim_batch_passes")
+    return first.tolist(), full.tolist(), int(n)
 
 
 def aim_set_genasm_window(ctx, window: int = 64, overlap: int = 24) -> None:

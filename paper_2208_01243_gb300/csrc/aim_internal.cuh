@@ -260,6 +260,7 @@ struct aim_ctx {
     int wfa_group;                // lanes per pair for the WFA; 0: chosen from the plan
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive parameters
     int genasm_w, genasm_o;       // GenASM window and overlap
+    int batch_compact;            // batch plans: 0 tuner decides on compact first passes, 1 always, 2 never
     void* tune_cache;             // autotuner choices (owned; see batch.cu)
 };
 

@@ -268,6 +268,7 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     c->adapt_max_dist = 50;
     c->genasm_w = 64;
     c->genasm_o = 24;
+    c->batch_compact = 0;
     *out = c;
     return AIM_OK;
 }
@@ -299,6 +300,12 @@ int aim_set_wfa_adaptive(aim_ctx* ctx, int min_length, int max_distance) {
     if (!ctx || min_length < 0 || max_distance < 0) return AIM_ERR_ARG;
     ctx->adapt_min_len = min_length;
     ctx->adapt_max_dist = max_distance;
+    return AIM_OK;
+}
+
+int aim_set_batch_compact(aim_ctx* ctx, int mode) {
+    if (!ctx || mode < 0 || mode > 2) return AIM_ERR_ARG;
+    ctx->batch_compact = mode;
     return AIM_OK;
 }
 

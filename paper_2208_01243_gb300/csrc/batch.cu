@@ -17,6 +17,16 @@
 // its pairs large enough to fill the device several times try the group sizes that suit its width class (so
 // that no lane walks more than about 64 diagonals per score step; the widest
 // class may also use a whole block per pair) and keep the fastest; choices are cached in the context per (costs, band, bucket).
+//
+// Two passes.  A bucket's scratch is sized for its worst case, which for long
+// pairs under a loose threshold only fits one pair per warp.  Most pairs end
+// far below their threshold and need a fraction of that history, so the tuner
+// also times a compact first pass: fewer lanes per pair and a history capped
+// at 16 diagonals per lane on average, followed by a second pass, with the
+// bucket's full scratch, over the pairs that outgrew the cap (the first pass
+// flags them AIM_F_STEP_CAP; a count/scan/scatter over those flags builds the
+// second pass's queues on the device).  Both passes run the exact algorithm,
+// so results do not depend on which pairs were retried.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -55,13 +65,18 @@ __device__ __forceinline__ int bucket_of(const PairsView& P, const LimitView& L,
     return (kWorkClasses - 1 - kc) * kWidthClasses + (kWidthClasses - 1 - wc);
 }
 
+// `capped` (optional): count and scatter only the pairs whose flag is AIM_F_STEP_CAP (the second pass's queues)
+__device__ __forceinline__ bool queued(const uint8_t* capped, uint32_t i) {
+    return capped == nullptr || capped[i] == AIM_F_STEP_CAP;
+}
+
 __global__ void __launch_bounds__(256) bucket_count_kernel(PairsView P, LimitView L, BucketParams bp,
-                                                           uint32_t* counts) {
+                                                           uint32_t* counts, const uint8_t* capped) {
     __shared__ uint32_t h[kBuckets];
     if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
     __syncthreads();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < P.num_pairs; i += gridDim.x * blockDim.x)
-        atomicAdd(&h[bucket_of(P, L, bp, i)], 1u);
+        if (queued(capped, i)) atomicAdd(&h[bucket_of(P, L, bp, i)], 1u);
     __syncthreads();
     if (threadIdx.x < kBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
 }
@@ -84,7 +99,7 @@ __global__ void bucket_scan_kernel(const uint32_t* counts, uint32_t* bounds, uin
 
 __global__ void __launch_bounds__(256) bucket_scatter_kernel(PairsView P, LimitView L, BucketParams bp,
                                                              const uint32_t* bounds, uint32_t* fill,
-                                                             uint32_t* order) {
+                                                             uint32_t* order, const uint8_t* capped) {
     __shared__ uint32_t h[kBuckets], base[kBuckets];
     for (uint32_t chunk = blockIdx.x * blockDim.x; chunk < P.num_pairs; chunk += gridDim.x * blockDim.x) {
         if (threadIdx.x < kBuckets) h[threadIdx.x] = 0;
@@ -92,7 +107,7 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(PairsView P, LimitV
         const uint32_t i = chunk + threadIdx.x;
         int b = -1;
         uint32_t r = 0;
-        if (i < P.num_pairs) {
+        if (i < P.num_pairs && queued(capped, i)) {
             b = bucket_of(P, L, bp, i);
             r = atomicAdd(&h[b], 1u);
         }
@@ -124,6 +139,15 @@ size_t bucket_group_bytes(const WfaPlan& plan, int b, uint32_t max_length) {
     return align_up(plan.meta_bytes + plan.runs_bytes + hist * sizeof(int16_t), 16);
 }
 
+constexpr int kCompactDiagonalsPerLane = 16;   // first-pass history: wavefronts of about 16 diagonals per lane
+
+// scratch one pair of bucket b gets in a compact first pass with G lanes per pair
+size_t bucket_compact_bytes(const WfaPlan& plan, int b, int G, uint32_t max_length) {
+    const size_t full = bucket_group_bytes(plan, b, max_length);
+    const size_t compact = wfa_plan_compact(plan, (int64_t)kCompactDiagonalsPerLane * G).group_bytes;
+    return std::min(full, compact);
+}
+
 int default_group_for_bucket(int b) {
     const int wc = kWidthClasses - 1 - b % kWidthClasses;
     return wc == 0 ? 4 : wc == 1 ? 8 : wc == 2 ? 16 : 32;
@@ -151,8 +175,12 @@ struct aim_batch {
     uint8_t *br, *bt;
     uint32_t *counts, *bounds, *fill, *claims, *trial_bounds, *order;
     uint8_t* scratch;
-    size_t scratch_bytes, warp_bytes;
-    int groups[aim::kBuckets];
+    size_t scratch_bytes, warp_bytes;   // warp_bytes: the full-scratch pass
+    int groups[aim::kBuckets];          // lanes per pair with the bucket's full scratch
+    int groups1[aim::kBuckets];         // lanes per pair of a compact first pass (0: the bucket runs in one pass)
+    bool two_pass;
+    size_t warp_bytes1;                 // the first pass's scratch per warp when two_pass
+    uint32_t *rcounts, *rbounds, *rfill, *rclaims, *rorder;   // second-pass queues
     uint32_t host_counts[aim::kBuckets];
     aim::BucketParams bp;
     cudaStream_t stream;
@@ -167,9 +195,10 @@ namespace aim {
 namespace {
 
 using TuneKey = std::tuple<int, int, int, int, int, int64_t>;   // x, o, e, band, bucket, smax
-std::map<TuneKey, int>& tune_cache(aim_ctx* ctx) {
-    if (!ctx->tune_cache) ctx->tune_cache = new std::map<TuneKey, int>();
-    return *static_cast<std::map<TuneKey, int>*>(ctx->tune_cache);
+using TuneChoice = std::pair<int, int>;                         // full-scratch lanes, compact first-pass lanes
+std::map<TuneKey, TuneChoice>& tune_cache(aim_ctx* ctx) {
+    if (!ctx->tune_cache) ctx->tune_cache = new std::map<TuneKey, TuneChoice>();
+    return *static_cast<std::map<TuneKey, TuneChoice>*>(ctx->tune_cache);
 }
 
 // packing and bucketing on `st`
@@ -182,24 +211,76 @@ cudaError_t enqueue_prepare(aim_batch* b, cudaStream_t st) {
     e = cudaMemsetAsync(b->counts, 0, kBuckets * sizeof(uint32_t), st);
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)std::min<uint64_t>((b->num_pairs + 255) / 256, (uint64_t)b->ctx->num_sms * 8);
-    bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->counts);
+    bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->counts, nullptr);
     bucket_scan_kernel<<<1, 32, 0, st>>>(b->counts, b->bounds, b->fill, b->claims);
-    bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->bounds, b->fill, b->order);
+    bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->bounds, b->fill, b->order, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t enqueue_align(aim_batch* b, cudaStream_t st, int* warps) {
-    return launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, b->groups, kBuckets, b->warp_bytes,
-                              b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, warps);
+    if (!b->two_pass)
+        return launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, b->groups, kBuckets,
+                                  b->warp_bytes, b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, warps);
+    int g1[kBuckets];
+    for (int k = 0; k < kBuckets; ++k) g1[k] = b->groups1[k] ? b->groups1[k] : b->groups[k];
+    cudaError_t e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, g1, kBuckets,
+                                       b->warp_bytes1, b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st,
+                                       warps);
+    if (e != cudaSuccess || *warps == 0) return e;
+    // second pass: queues of the pairs the first pass flagged, then the full scratch
+    e = cudaMemsetAsync(b->rcounts, 0, kBuckets * sizeof(uint32_t), st);
+    if (e != cudaSuccess) return e;
+    const unsigned blocks = (unsigned)std::min<uint64_t>((b->num_pairs + 255) / 256, (uint64_t)b->ctx->num_sms * 8);
+    bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->rcounts, b->O.flags);
+    bucket_scan_kernel<<<1, 32, 0, st>>>(b->rcounts, b->rbounds, b->rfill, b->rclaims);
+    bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->rbounds, b->rfill, b->rorder, b->O.flags);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    WfaPlan retry = b->plan;
+    retry.retry_only = 1;
+    int w2 = 0;
+    e = launch_wfa_buckets(retry, b->P, b->r.lim, b->O, b->rorder, b->rbounds, b->groups, kBuckets, b->warp_bytes,
+                           b->scratch, b->scratch_bytes, b->rclaims, b->ctx->num_sms, st, &w2);
+    if (e == cudaSuccess && w2 == 0) *warps = 0;
+    return e;
+}
+
+// one timed trial launch over order positions tb[0]..tb[1] with G lanes per pair and warp_bytes of scratch
+cudaError_t trial(aim_batch* b, const WfaPlan& plan, const uint32_t tb[2], int G, size_t wb, cudaEvent_t t0,
+                  cudaEvent_t t1, float* ms) {
+    cudaStream_t st = b->stream;
+    cudaError_t e = cudaMemcpyAsync(b->trial_bounds, tb, 2 * sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->claims, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaEventRecord(t0, st);
+    int w = 0;
+    if (e == cudaSuccess)
+        e = launch_wfa_buckets(plan, b->P, b->r.lim, b->O, b->order, b->trial_bounds, &G, 1, wb, b->scratch,
+                               b->scratch_bytes, b->claims, b->ctx->num_sms, st, &w);
+    if (e == cudaSuccess) e = cudaEventRecord(t1, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, t0, t1);
+    return e;
+}
+
+// a compact first pass with G1 lanes for bucket k: it must save scratch, use no more lanes than the full pass,
+// and fit the device several times over
+bool compact_allowed(const aim_batch* b, int k, int G1, int g_full) {
+    const size_t full = bucket_group_bytes(b->plan, k, b->max_length);
+    const size_t need = bucket_compact_bytes(b->plan, k, G1, b->max_length);
+    if (need >= full || G1 > g_full) return false;
+    const size_t min_warps = (size_t)b->ctx->num_sms * 8;
+    return wfa_warp_bytes(G1, need) * min_warps <= b->scratch_bytes &&
+           wfa_warp_bytes(g_full, full) <= b->scratch_bytes;
 }
 
 int autotune(aim_batch* b) {
-    cudaStream_t st = b->stream;
     cudaEvent_t t0, t1;
     if (cudaEventCreate(&t0) != cudaSuccess || cudaEventCreate(&t1) != cudaSuccess) return AIM_ERR_CUDA;
     uint32_t bounds[kBuckets + 1];
     cudaError_t e = cudaMemcpy(bounds, b->bounds, sizeof(bounds), cudaMemcpyDeviceToHost);
     const size_t min_warps = (size_t)b->ctx->num_sms * 8;
+    WfaPlan retry = b->plan;
+    retry.retry_only = 1;
     for (int k = 0; k < kBuckets && e == cudaSuccess; ++k) {
         const uint32_t count = b->host_counts[k];
         if (!count) continue;
@@ -207,6 +288,7 @@ int autotune(aim_batch* b) {
         // latency of a handful of pairs
         const uint32_t sample = std::min<uint32_t>(count, (uint32_t)std::max<size_t>(4096, 16 * min_warps * 4));
         const uint32_t tb[2] = {bounds[k], bounds[k] + sample};
+        const size_t full = bucket_group_bytes(b->plan, k, b->max_length);
         float best = 1e30f;
         int best_g = b->groups[k];
         // lanes per pair worth trying for this width class: at most ~64 diagonals per lane and score step
@@ -215,25 +297,32 @@ int autotune(aim_batch* b) {
         const int gmax = wc == 0 ? 8 : wc == 1 ? 16 : wc == 2 ? 32 : 256;
         for (int G : kCandidates) {
             if (G < gmin || G > gmax) continue;
-            const size_t wb = wfa_warp_bytes(G, bucket_group_bytes(b->plan, k, b->max_length));
+            const size_t wb = wfa_warp_bytes(G, full);
             if (wb * min_warps > b->scratch_bytes) continue;
             float ms = 0.f;
-            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
-                e = cudaMemcpyAsync(b->trial_bounds, tb, sizeof(tb), cudaMemcpyHostToDevice, st);
-                if (e == cudaSuccess) e = cudaMemsetAsync(b->claims, 0, sizeof(uint32_t), st);
-                if (e == cudaSuccess) e = cudaEventRecord(t0, st);
-                int w = 0;
-                if (e == cudaSuccess)
-                    e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->trial_bounds, &G, 1, wb,
-                                           b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, &w);
-                if (e == cudaSuccess) e = cudaEventRecord(t1, st);
-                if (e == cudaSuccess) e = cudaEventSynchronize(t1);
-                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t0, t1);
-            }
+            for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = trial(b, b->plan, tb, G, wb, t0, t1, &ms);
             if (e == cudaSuccess && ms < best) { best = ms; best_g = G; }
         }
+        // compact first pass with fewer lanes, then the full-scratch pass over the pairs that outgrew it
+        int best_g1 = 0;
+        if (b->ctx->batch_compact != 2) {
+            const size_t wb_full = wfa_warp_bytes(best_g, full);
+            for (int G1 : {4, 8, 16, 32}) {
+                if (!compact_allowed(b, k, G1, best_g)) continue;
+                const size_t wb = wfa_warp_bytes(G1, bucket_compact_bytes(b->plan, k, G1, b->max_length));
+                if (b->ctx->batch_compact == 1) { best_g1 = G1; break; }   // forced: the fewest lanes that fit
+                float ms1 = 0.f, ms2 = 0.f;
+                for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                    e = trial(b, b->plan, tb, G1, wb, t0, t1, &ms1);
+                    if (e == cudaSuccess) e = trial(b, retry, tb, best_g, wb_full, t0, t1, &ms2);
+                }
+                if (e == cudaSuccess && ms1 + ms2 < best) { best = ms1 + ms2; best_g1 = G1; }
+            }
+        }
         b->groups[k] = best_g;
-        tune_cache(b->ctx)[TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, b->pen.band, k, b->plan.smax)] = best_g;
+        b->groups1[k] = best_g1;
+        tune_cache(b->ctx)[TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, b->pen.band, k, b->plan.smax)] =
+            TuneChoice(best_g, best_g1);
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -253,7 +342,7 @@ void free_batch(aim_batch* b) {
 
 }  // namespace
 
-void free_tune_cache(void* cache) { delete static_cast<std::map<TuneKey, int>*>(cache); }
+void free_tune_cache(void* cache) { delete static_cast<std::map<TuneKey, TuneChoice>*>(cache); }
 
 }  // namespace aim
 
@@ -290,22 +379,23 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     b->reads = reads; b->targets = targets; b->read_coff = read_char_offsets; b->target_coff = target_char_offsets;
     b->stride = ((uint64_t)max_length + 31) / 32;
 
-    // groups: cached choice, else the width-class default
+    // groups: cached choice, else the width-class default in one pass
     for (int k = 0; k < kBuckets; ++k) {
         b->groups[k] = default_group_for_bucket(k);
+        b->groups1[k] = 0;
         if (ctx->tune_cache) {
             auto& c = tune_cache(ctx);
             auto it = c.find(TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, pen->band, k, b->plan.smax));
-            if (it != c.end()) b->groups[k] = it->second;
+            if (it != c.end()) { b->groups[k] = it->second.first; b->groups1[k] = it->second.second; }
         }
     }
     // owned memory: packed sequences, flags, bucket arrays, order, scratch
     const size_t seq_bytes = align_up((size_t)num_pairs * b->stride * 8, 256);
     const size_t flag_bytes = align_up(num_pairs, 256);
-    const size_t small_bytes = align_up(5 * (kBuckets + 1) * sizeof(uint32_t), 256);
+    const size_t small_bytes = align_up(9 * (kBuckets + 1) * sizeof(uint32_t), 256);
     const size_t order_bytes = align_up((size_t)num_pairs * sizeof(uint32_t), 256);
     b->scratch_bytes = scratch_bytes ? scratch_bytes : ctx->ws_bytes;
-    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + order_bytes + b->scratch_bytes;
+    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 2 * order_bytes + b->scratch_bytes;
     cudaError_t e = cudaMalloc(&b->mem, b->mem_bytes);
     if (e != cudaSuccess) { cudaGetLastError(); free_batch(b); return AIM_ERR_NOMEM; }
     uint8_t* p = b->mem;
@@ -316,7 +406,10 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     uint32_t* sm = reinterpret_cast<uint32_t*>(p); p += small_bytes;
     b->counts = sm; b->bounds = sm + (kBuckets + 1); b->fill = sm + 2 * (kBuckets + 1);
     b->claims = sm + 3 * (kBuckets + 1); b->trial_bounds = sm + 4 * (kBuckets + 1);
+    b->rcounts = sm + 5 * (kBuckets + 1); b->rbounds = sm + 6 * (kBuckets + 1);
+    b->rfill = sm + 7 * (kBuckets + 1); b->rclaims = sm + 8 * (kBuckets + 1);
     b->order = reinterpret_cast<uint32_t*>(p); p += order_bytes;
+    b->rorder = reinterpret_cast<uint32_t*>(p); p += order_bytes;
     b->scratch = p;
     b->P = PairsView{b->pr, b->pt, nullptr, nullptr, read_lengths, target_lengths, b->br, b->bt, num_pairs, max_length};
     b->P.stride = b->stride;
@@ -332,16 +425,41 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     if (autotune) {
         rc = aim::autotune(b);
         if (rc) { free_batch(b); return rc; }
+    } else if (ctx->batch_compact != 0) {
+        // without trials: forced compact first passes where they fit, or none
+        for (int k = 0; k < kBuckets; ++k) {
+            b->groups1[k] = 0;
+            if (ctx->batch_compact != 1 || !b->host_counts[k]) continue;
+            for (int G1 : {4, 8, 16, 32})
+                if (compact_allowed(b, k, G1, b->groups[k])) { b->groups1[k] = G1; break; }
+        }
     }
     // buckets empty at planning keep one pair per warp, so their worst case does not shrink the grid
     for (int k = 0; k < kBuckets; ++k)
-        if (!b->host_counts[k]) b->groups[k] = 32;
-    // scratch per warp: the largest need over all buckets (a replay may see a different mix)
+        if (!b->host_counts[k]) { b->groups[k] = 32; b->groups1[k] = 0; }
+    // scratch per warp of the full pass: the largest need over all buckets (a replay may see a different mix)
     size_t wb = 0;
     for (int k = 0; k < kBuckets; ++k)
         wb = std::max(wb, wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k, max_length)));
     b->warp_bytes = wb;
     if (wb > b->scratch_bytes) { free_batch(b); return AIM_ERR_NOMEM; }
+    // with a compact first pass, its scratch per warp covers the buckets seen at planning; a pair of another
+    // bucket that does not fit is flagged and aligned again by the full pass like any other
+    b->two_pass = false;
+    for (int k = 0; k < kBuckets; ++k) b->two_pass |= b->groups1[k] != 0;
+    b->warp_bytes1 = wb;
+    if (b->two_pass) {
+        size_t wb1 = 0;
+        for (int k = 0; k < kBuckets; ++k) {
+            if (!b->host_counts[k]) continue;
+            wb1 = std::max(wb1, b->groups1[k] ? wfa_warp_bytes(b->groups1[k], bucket_compact_bytes(b->plan, k,
+                                                                                               b->groups1[k],
+                                                                                               max_length))
+                                              : wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k,
+                                                                                                max_length)));
+        }
+        b->warp_bytes1 = std::max<size_t>(wb1, 16);
+    }
 
     // record prepare + align as a graph; the two event records bracket the alignment kernel
     if (cudaEventCreate(&b->ev_start) != cudaSuccess || cudaEventCreate(&b->ev_stop) != cudaSuccess) {
@@ -401,8 +519,22 @@ int aim_batch_run(aim_batch* b, aim_stream_t stream) {
 
 int aim_batch_info(aim_batch* b, int* groups, uint32_t* counts) {
     if (!b || !groups || !counts) return AIM_ERR_ARG;
-    for (int k = 0; k < aim::kBuckets; ++k) { groups[k] = b->groups[k]; counts[k] = b->host_counts[k]; }
+    for (int k = 0; k < aim::kBuckets; ++k) {
+        groups[k] = b->groups1[k] ? b->groups1[k] : b->groups[k];
+        counts[k] = b->host_counts[k];
+    }
     return aim::kBuckets;
+}
+
+int aim_batch_passes(aim_batch* b, int* first_pass, int* full_pass) {
+    if (!b || !first_pass || !full_pass) return AIM_ERR_ARG;
+    int compact = 0;
+    for (int k = 0; k < aim::kBuckets; ++k) {
+        first_pass[k] = b->groups1[k];
+        full_pass[k] = b->groups[k];
+        compact += b->groups1[k] != 0;
+    }
+    return compact;
 }
 
 int aim_batch_destroy(aim_batch* b) {

@@ -19,7 +19,7 @@ def _mixed(n_uneven=2_500, n_short=2_003):
     return p, me
 
 
-def _batched(p, me, autotune, runs=2, scratch=0):
+def _batched(p, me, autotune, runs=2, scratch=0, compact=0, passes=None):
     import torch
     import paper_2208_01243_gb300 as aim
     n = len(p)
@@ -28,6 +28,7 @@ def _batched(p, me, autotune, runs=2, scratch=0):
     reads, targets, ro, to, rl, tl, cd, pp = aim.upload(p.reads, p.targets, p.read_off, p.target_off, p.read_len,
                                                         p.target_len, coff, me.astype(np.int32))
     al = aim.Aligner(0, 1 << 30)
+    aim.aim_set_batch_compact(al.ctx, compact)
     dev = rl.device
     scores = torch.full((n,), -7, dtype=torch.int32, device=dev)
     flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
@@ -37,6 +38,8 @@ def _batched(p, me, autotune, runs=2, scratch=0):
     plan = aim.aim_batch_plan(al.ctx, reads, targets, ro, to, rl, tl, ml, aim.penalties(4, 6, 2), int(me.max()), pp,
                               scores, cig, cd, lens, flags, scratch_bytes=scratch, autotune=autotune)
     groups, counts = aim.aim_batch_info(plan)
+    if passes is not None:
+        passes.append(aim.aim_batch_passes(plan))
     outs = []
     for _ in range(runs):
         scores.fill_(-7); flags.fill_(255)
@@ -66,6 +69,29 @@ def test_batched_equals_plain_and_oracle(oracle_lib, gen_lib, autotune):
     sub = gen.concat([gen.from_strings([p.read(i)], [p.target(i)]) for i in idx])
     lim = np.array([oracle.limit_for(AFF, int(me[i])) for i in idx], np.int64)
     assert_same(outs[-1], oracle_results(sub, AFF, lim), idx=idx, what="batched vs oracle")
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_compact_first_pass_gives_the_plain_results(oracle_lib, gen_lib, autotune):
+    """Compact first passes forced on every bucket that allows one, with the fewest lanes that fit (so many pairs
+    outgrow them): the second pass re-aligns exactly those, and every replay equals the plain form bit for bit."""
+    import __graft_entry__
+    __graft_entry__.build()
+    p, me = _mixed(6_000, 2_003)
+    passes = []
+    outs, groups, counts = _batched(p, me, autotune, compact=1, passes=passes, scratch=4 << 30)
+    first, full, n_compact = passes[0]
+    assert n_compact > 0 and any(f and f < g for f, g in zip(first, full))
+    plain = device_results(p, "wfa", AFF, int(me.max()), per_pair=me)
+    for o in outs:
+        assert (o[1] & 8).sum() == 0                 # no pair left flagged after the full pass
+        assert np.array_equal(o[0], plain[0]) and np.array_equal(o[1], plain[1])
+        assert all(np.array_equal(x, y) for x, y in zip(o[2], plain[2]))
+    # never: one pass, the same results
+    passes = []
+    outs2, _, _ = _batched(p, me, autotune, runs=1, compact=2, passes=passes, scratch=4 << 30)
+    assert passes[0][2] == 0
+    assert np.array_equal(outs2[0][0], plain[0]) and np.array_equal(outs2[0][1], plain[1])
 
 
 def test_batched_replay_sees_new_contents(gen_lib):
