@@ -138,6 +138,11 @@ struct Group<G, false> {
     __device__ bool any_running(bool x) const { return __any_sync(kFull, x); }
     __device__ int iterations(int w) const { return (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G)); }
     __device__ void min_max(int& lo, int& hi) const {
+        if constexpr (G == 32) {   // the whole warp is one group: one warp-wide reduction each
+            lo = __reduce_min_sync(kFull, lo);
+            hi = __reduce_max_sync(kFull, hi);
+            return;
+        }
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             lo = min(lo, __shfl_xor_sync(kFull, lo, o));
