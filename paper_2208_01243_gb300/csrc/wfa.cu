@@ -193,7 +193,9 @@ struct Counters {
 
 // One step of the warp's work: groups g = 0 .. 32/G - 1 align the pairs at
 // order positions q0 + g (those < qend).  All lanes must call this together.
-template <int G>
+// ADAPT: WFA-adaptive pruning and the source-following traceback (a kernel of its own, so the exact
+// algorithm carries none of its registers).
+template <int G, bool ADAPT>
 __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
                              Counters& st) {
     const Group<G> grp(lane);
@@ -305,7 +307,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         st.windows += n_windows;
         grp.min_max(vlo, vhi);   // group-wide trimmed range
         const bool group_hit = grp.group_any(hit);
-        if (a.adapt_min_len >= 0) {
+        if constexpr (ADAPT) {
             // WFA-adaptive: once the wavefront spans at least adapt_min_len diagonals, drop outer diagonals
             // whose distance to the end cell, max(n - v, m - h), exceeds the smallest by more than adapt_max_dist
             const bool prune = run && !group_hit && vlo <= vhi && vhi - vlo + 1 >= a.adapt_min_len;
@@ -346,7 +348,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     // traceback on each group's first lane
     uint32_t nruns = 0;
     bool ok = true;
-    if (status == kDone && gl == 0 && a.adapt_min_len >= 0) {
+    if (ADAPT && status == kDone && gl == 0) {
         // WFA-adaptive: follow the sources.  State M at offset h of (c, k): the matches run back to f0, whose
         // source is the mismatch candidate, then I, then D; state I (value h): an extension I[c-E, k+1] == h
         // before an opening M[c-OE, k+1] == h; state D likewise with D[c-E, k-1] + 1 and M[c-OE, k-1] + 1.
@@ -391,7 +393,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     }
     // canonical traceback; every step issues the loads of all four tight tests at once (two memory round
     // trips per step instead of a chain of dependent ones)
-    if (status == kDone && gl == 0 && a.adapt_min_len < 0) {
+    if (!ADAPT && status == kDone && gl == 0) {
         const int* __restrict__ cmeta = meta;
         const int16_t* __restrict__ chist = hist;
         RunWriter wr;
@@ -459,7 +461,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     __syncwarp();
 }
 
-template <int G>
+template <int G, bool ADAPT>
 __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
@@ -473,7 +475,7 @@ __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t
             const uint32_t pos = s_pos;
             __syncthreads();
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G>(a, block_slot, begin + pos, end, lane, st);
+            align_groups<G, ADAPT>(a, block_slot, begin + pos, end, lane, st);
         }
     } else {
         constexpr int P = 32 / G;
@@ -482,7 +484,7 @@ __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t
             if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
             pos = __shfl_sync(kFull, pos, 0);
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G>(a, warp_slot, begin + pos, end, lane, st);
+            align_groups<G, ADAPT>(a, warp_slot, begin + pos, end, lane, st);
         }
     }
 }
@@ -491,6 +493,7 @@ __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t
 #define AIM_WFA_MIN_BLOCKS 4
 #endif
 
+template <bool ADAPT>
 __global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -499,13 +502,13 @@ __global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a)
     Counters st{0, 0, 0};
     for (int b = 0; b < a.nbuckets; ++b) {
         switch (a.group[b]) {
-            case 1: run_bucket<1>(a, b, warp_slot, lane, st); break;
-            case 2: run_bucket<2>(a, b, warp_slot, lane, st); break;
-            case 4: run_bucket<4>(a, b, warp_slot, lane, st); break;
-            case 8: run_bucket<8>(a, b, warp_slot, lane, st); break;
-            case 16: run_bucket<16>(a, b, warp_slot, lane, st); break;
-            case 32: run_bucket<32>(a, b, warp_slot, lane, st); break;
-            default: run_bucket<256>(a, b, warp_slot, lane, st); break;
+            case 1: run_bucket<1, ADAPT>(a, b, warp_slot, lane, st); break;
+            case 2: run_bucket<2, ADAPT>(a, b, warp_slot, lane, st); break;
+            case 4: run_bucket<4, ADAPT>(a, b, warp_slot, lane, st); break;
+            case 8: run_bucket<8, ADAPT>(a, b, warp_slot, lane, st); break;
+            case 16: run_bucket<16, ADAPT>(a, b, warp_slot, lane, st); break;
+            case 32: run_bucket<32, ADAPT>(a, b, warp_slot, lane, st); break;
+            default: run_bucket<256, ADAPT>(a, b, warp_slot, lane, st); break;
         }
     }
     warp_stat_add(a.O.stats, 0, st.cells, lane);
@@ -599,7 +602,9 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.retry_only = plan.retry_only;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int8_t)(b < nbuckets ? groups[b] : 32);
     int bps = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel, 256, 0);
+    const bool adapt = plan.adapt_min_len >= 0;
+    cudaError_t err = adapt ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<true>, 256, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<false>, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     // whole blocks of 8 warps (a 256-lane group uses all of them)
@@ -614,7 +619,8 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     warps = warps / 8 * 8;
     if (warps == 0) return cudaSuccess;
     a.nwarps = (uint32_t)warps;
-    wfa_kernel<<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
+    if (adapt) wfa_kernel<true><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
+    else wfa_kernel<false><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
 }
