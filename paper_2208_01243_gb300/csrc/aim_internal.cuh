@@ -151,7 +151,7 @@ struct WfaArgs {
     int nbuckets;
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive pruning and source-following traceback (min_len < 0: off)
     int retry_only;            // align only pairs whose flag is AIM_F_STEP_CAP (a second pass with larger scratch)
-    int8_t group[kMaxBuckets]; // lanes per pair of each bucket
+    int16_t group[kMaxBuckets]; // lanes per pair of each bucket (1..32, or 256: a whole block)
 };
 
 // one launch over buckets (longest-first order given by the caller)

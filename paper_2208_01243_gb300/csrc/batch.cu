@@ -13,6 +13,12 @@
 // device (a block-aggregated histogram, a one-warp scan, a block-aggregated
 // scatter into an order array), so a replay needs no host round trip.
 //
+// Launches.  Once the lanes per pair of every bucket are known, the queue
+// order groups the buckets that share a group size (heaviest first inside and
+// between groups), and each group is one persistent launch over one queue
+// range, of the kernel compiled for that group size alone (one kernel holding
+// every group size spilled registers and ran 14 % slower).
+//
 // Autotuner.  For every non-empty bucket, timed trial launches on a sample of
 // its pairs large enough to fill the device several times try the group sizes that suit its width class (so
 // that no lane walks more than about 64 diagonals per score step; the widest
@@ -48,6 +54,9 @@ constexpr int kCandidates[7] = {1, 2, 4, 8, 16, 32, 256};
 struct BucketParams {
     int g, E, band;
     int64_t smax;
+    int8_t perm[kBuckets];          // queue order of the buckets (identity, or grouped by lanes per pair)
+    int8_t gstart[kBuckets + 1];    // groups of consecutive permuted buckets sharing one lanes-per-pair value
+    int ngroups;                    // 0: no groups
 };
 
 __device__ __forceinline__ int bucket_of(const PairsView& P, const LimitView& L, const BucketParams& bp, uint32_t i) {
@@ -62,7 +71,7 @@ __device__ __forceinline__ int bucket_of(const PairsView& P, const LimitView& L,
     const int wc = W <= 64 ? 0 : W <= 128 ? 1 : W <= 256 ? 2 : 3;
     int kc = (63 - __clzll((long long)(C + 1))) / 3;
     if (kc > kWorkClasses - 1) kc = kWorkClasses - 1;
-    return (kWorkClasses - 1 - kc) * kWidthClasses + (kWidthClasses - 1 - wc);
+    return bp.perm[(kWorkClasses - 1 - kc) * kWidthClasses + (kWidthClasses - 1 - wc)];
 }
 
 // `capped` (optional): count and scatter only the pairs whose flag is AIM_F_STEP_CAP (the second pass's queues)
@@ -81,8 +90,10 @@ __global__ void __launch_bounds__(256) bucket_count_kernel(PairsView P, LimitVie
     if (threadIdx.x < kBuckets && h[threadIdx.x]) atomicAdd(&counts[threadIdx.x], h[threadIdx.x]);
 }
 
-// one warp: bounds[b] = first queue position of bucket b, bounds[32] = total; clears the fill and claim counters
-__global__ void bucket_scan_kernel(const uint32_t* counts, uint32_t* bounds, uint32_t* fill, uint32_t* claims) {
+// one warp: bounds[b] = first queue position of bucket b, bounds[32] = total; clears the fill and claim counters.
+// With groups, gbounds[j] = first queue position of group j (gbounds[ngroups] = total).
+__global__ void bucket_scan_kernel(const uint32_t* counts, uint32_t* bounds, uint32_t* fill, uint32_t* claims,
+                                   BucketParams bp, uint32_t* gbounds) {
     const uint32_t lane = threadIdx.x;
     const uint32_t c = counts[lane];
     uint32_t incl = c;
@@ -95,6 +106,10 @@ __global__ void bucket_scan_kernel(const uint32_t* counts, uint32_t* bounds, uin
     if (lane == 31) bounds[32] = incl;
     fill[lane] = 0;
     claims[lane] = 0;
+    const uint32_t total = __shfl_sync(kFull, incl, 31);
+    const int x = (int)lane <= bp.ngroups ? bp.gstart[lane] : 0;
+    const uint32_t at = __shfl_sync(kFull, incl - c, x < 32 ? x : 0);   // every lane takes part
+    if (gbounds && (int)lane <= bp.ngroups) gbounds[lane] = x < 32 ? at : total;
 }
 
 __global__ void __launch_bounds__(256) bucket_scatter_kernel(PairsView P, LimitView L, BucketParams bp,
@@ -181,6 +196,9 @@ struct aim_batch {
     bool two_pass;
     size_t warp_bytes1;                 // the first pass's scratch per warp when two_pass
     uint32_t *rcounts, *rbounds, *rfill, *rclaims, *rorder;   // second-pass queues
+    uint32_t* gbounds;                  // queue range of each group of buckets sharing lanes per pair
+    int ggroup[aim::kBuckets];          // lanes per pair of each group
+    size_t gwarp_bytes[aim::kBuckets];  // scratch per warp of each group
     uint32_t host_counts[aim::kBuckets];
     aim::BucketParams bp;
     cudaStream_t stream;
@@ -212,15 +230,27 @@ cudaError_t enqueue_prepare(aim_batch* b, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)std::min<uint64_t>((b->num_pairs + 255) / 256, (uint64_t)b->ctx->num_sms * 8);
     bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->counts, nullptr);
-    bucket_scan_kernel<<<1, 32, 0, st>>>(b->counts, b->bounds, b->fill, b->claims);
+    bucket_scan_kernel<<<1, 32, 0, st>>>(b->counts, b->bounds, b->fill, b->claims, b->bp,
+                                         b->bp.ngroups ? b->gbounds : nullptr);
     bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->bounds, b->fill, b->order, nullptr);
     return cudaGetLastError();
 }
 
 cudaError_t enqueue_align(aim_batch* b, cudaStream_t st, int* warps) {
-    if (!b->two_pass)
-        return launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, b->groups, kBuckets,
-                                  b->warp_bytes, b->scratch, b->scratch_bytes, b->claims, b->ctx->num_sms, st, warps);
+    if (!b->two_pass) {
+        // one launch per group of buckets sharing lanes per pair, each over one contiguous queue range
+        *warps = 0;
+        for (int j = 0; j < b->bp.ngroups; ++j) {
+            int w = 0;
+            const cudaError_t e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->gbounds + j,
+                                                     &b->ggroup[j], 1, b->gwarp_bytes[j], b->scratch,
+                                                     b->scratch_bytes, b->claims + j, b->ctx->num_sms, st, &w);
+            if (e != cudaSuccess) return e;
+            if (w == 0) { *warps = 0; return cudaSuccess; }
+            *warps = std::max(*warps, w);
+        }
+        return cudaSuccess;
+    }
     int g1[kBuckets];
     for (int k = 0; k < kBuckets; ++k) g1[k] = b->groups1[k] ? b->groups1[k] : b->groups[k];
     cudaError_t e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->bounds, g1, kBuckets,
@@ -232,7 +262,7 @@ cudaError_t enqueue_align(aim_batch* b, cudaStream_t st, int* warps) {
     if (e != cudaSuccess) return e;
     const unsigned blocks = (unsigned)std::min<uint64_t>((b->num_pairs + 255) / 256, (uint64_t)b->ctx->num_sms * 8);
     bucket_count_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->rcounts, b->O.flags);
-    bucket_scan_kernel<<<1, 32, 0, st>>>(b->rcounts, b->rbounds, b->rfill, b->rclaims);
+    bucket_scan_kernel<<<1, 32, 0, st>>>(b->rcounts, b->rbounds, b->rfill, b->rclaims, b->bp, nullptr);
     bucket_scatter_kernel<<<blocks, 256, 0, st>>>(b->P, b->r.lim, b->bp, b->rbounds, b->rfill, b->rorder, b->O.flags);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -375,7 +405,10 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     int rc = resolve(AIM_ALGO_WFA_AFFINE, pen, max_edits, max_edits_per_pair, &b->r);
     if (rc) { free_batch(b); return rc; }
     b->plan = plan_wfa(b->r.costs, pen->band, max_length, b->r.max_limit);
-    b->bp = BucketParams{b->plan.g, b->plan.e, pen->band, b->plan.smax};
+    b->bp = BucketParams{};
+    b->bp.g = b->plan.g; b->bp.E = b->plan.e; b->bp.band = pen->band; b->bp.smax = b->plan.smax;
+    for (int k = 0; k < kBuckets; ++k) b->bp.perm[k] = (int8_t)k;
+    b->bp.ngroups = 0;
     b->reads = reads; b->targets = targets; b->read_coff = read_char_offsets; b->target_coff = target_char_offsets;
     b->stride = ((uint64_t)max_length + 31) / 32;
 
@@ -392,7 +425,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     // owned memory: packed sequences, flags, bucket arrays, order, scratch
     const size_t seq_bytes = align_up((size_t)num_pairs * b->stride * 8, 256);
     const size_t flag_bytes = align_up(num_pairs, 256);
-    const size_t small_bytes = align_up(9 * (kBuckets + 1) * sizeof(uint32_t), 256);
+    const size_t small_bytes = align_up(10 * (kBuckets + 1) * sizeof(uint32_t), 256);
     const size_t order_bytes = align_up((size_t)num_pairs * sizeof(uint32_t), 256);
     b->scratch_bytes = scratch_bytes ? scratch_bytes : ctx->ws_bytes;
     b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 2 * order_bytes + b->scratch_bytes;
@@ -408,6 +441,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     b->claims = sm + 3 * (kBuckets + 1); b->trial_bounds = sm + 4 * (kBuckets + 1);
     b->rcounts = sm + 5 * (kBuckets + 1); b->rbounds = sm + 6 * (kBuckets + 1);
     b->rfill = sm + 7 * (kBuckets + 1); b->rclaims = sm + 8 * (kBuckets + 1);
+    b->gbounds = sm + 9 * (kBuckets + 1);
     b->order = reinterpret_cast<uint32_t*>(p); p += order_bytes;
     b->rorder = reinterpret_cast<uint32_t*>(p); p += order_bytes;
     b->scratch = p;
@@ -459,6 +493,29 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
                                                                                                 max_length)));
         }
         b->warp_bytes1 = std::max<size_t>(wb1, 16);
+    } else {
+        // one pass: the buckets sharing lanes per pair become one contiguous queue range (groups in the order
+        // of their heaviest bucket, buckets heaviest first inside), and each group is one launch of the kernel
+        // compiled for its group size, with scratch per warp sized for that group alone
+        int ng = 0;
+        for (int k = 0; k < kBuckets; ++k) {
+            bool seen = false;
+            for (int j = 0; j < ng; ++j) seen |= b->ggroup[j] == b->groups[k];
+            if (!seen) b->ggroup[ng++] = b->groups[k];
+        }
+        int next = 0;
+        for (int j = 0; j < ng; ++j) {
+            b->bp.gstart[j] = (int8_t)next;
+            size_t wbj = 16;
+            for (int k = 0; k < kBuckets; ++k) {
+                if (b->groups[k] != b->ggroup[j]) continue;
+                b->bp.perm[k] = (int8_t)next++;
+                wbj = std::max(wbj, wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k, max_length)));
+            }
+            b->gwarp_bytes[j] = wbj;
+        }
+        b->bp.gstart[ng] = (int8_t)kBuckets;
+        b->bp.ngroups = ng;
     }
 
     // record prepare + align as a graph; the two event records bracket the alignment kernel

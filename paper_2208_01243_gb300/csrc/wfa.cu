@@ -462,7 +462,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
 }
 
 template <int G, bool ADAPT>
-__device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
+__device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     if constexpr (G > 32) {
@@ -493,27 +493,40 @@ __device__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t
 #define AIM_WFA_MIN_BLOCKS 4
 #endif
 
-template <bool ADAPT>
+// One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
+// that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
+// kernel with every variant spilled about 1 KB per thread and ran 14 % slower).
+template <int G, bool ADAPT>
 __global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
     uint8_t* warp_slot = a.scratch + (size_t)gwarp * a.warp_bytes;
     Counters st{0, 0, 0};
-    for (int b = 0; b < a.nbuckets; ++b) {
-        switch (a.group[b]) {
-            case 1: run_bucket<1, ADAPT>(a, b, warp_slot, lane, st); break;
-            case 2: run_bucket<2, ADAPT>(a, b, warp_slot, lane, st); break;
-            case 4: run_bucket<4, ADAPT>(a, b, warp_slot, lane, st); break;
-            case 8: run_bucket<8, ADAPT>(a, b, warp_slot, lane, st); break;
-            case 16: run_bucket<16, ADAPT>(a, b, warp_slot, lane, st); break;
-            case 32: run_bucket<32, ADAPT>(a, b, warp_slot, lane, st); break;
-            default: run_bucket<256, ADAPT>(a, b, warp_slot, lane, st); break;
-        }
+    if (a.nbuckets == 1) {
+        // one queue range (plain calls, and the batched form's groups): measured 7 % faster than the loop below
+        run_bucket<G, ADAPT>(a, 0, warp_slot, lane, st);
+    } else {
+        for (int b = 0; b < a.nbuckets; ++b)
+            if ((a.group[b] > 32 ? 256 : a.group[b]) == G) run_bucket<G, ADAPT>(a, b, warp_slot, lane, st);
     }
     warp_stat_add(a.O.stats, 0, st.cells, lane);
     warp_stat_add(a.O.stats, 1, st.windows, lane);
     warp_stat_add(a.O.stats, 3, st.pairs, lane);
+}
+
+template <bool ADAPT>
+cudaError_t launch_one(int G, unsigned blocks, cudaStream_t st, const WfaArgs& a) {
+    switch (G) {
+        case 1: wfa_kernel<1, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 2: wfa_kernel<2, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 4: wfa_kernel<4, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 8: wfa_kernel<8, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 16: wfa_kernel<16, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 32: wfa_kernel<32, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        default: wfa_kernel<256, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
 }
 
 int gcd_i(int a, int b) {
@@ -600,11 +613,11 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
     a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
     a.retry_only = plan.retry_only;
-    for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int8_t)(b < nbuckets ? groups[b] : 32);
+    for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int16_t)(b < nbuckets ? groups[b] : 32);
     int bps = 0;
     const bool adapt = plan.adapt_min_len >= 0;
-    cudaError_t err = adapt ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<true>, 256, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<false>, 256, 0);
+    cudaError_t err = adapt ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<32, true>, 256, 0)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<32, false>, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     // whole blocks of 8 warps (a 256-lane group uses all of them)
@@ -619,10 +632,21 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     warps = warps / 8 * 8;
     if (warps == 0) return cudaSuccess;
     a.nwarps = (uint32_t)warps;
-    if (adapt) wfa_kernel<true><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
-    else wfa_kernel<false><<<(unsigned)((warps + 7) / 8), 256, 0, st>>>(a);
+    const unsigned blocks = (unsigned)((warps + 7) / 8);
     *warps_used = (int)warps;
-    return cudaGetLastError();
+    // one launch per distinct group size, in the order the buckets (heaviest first) first use it
+    int seen[kMaxBuckets];
+    int nseen = 0;
+    for (int b = 0; b < nbuckets; ++b) {
+        const int G = a.group[b] > 32 ? 256 : a.group[b];
+        bool dup = false;
+        for (int i = 0; i < nseen; ++i) dup |= seen[i] == G;
+        if (dup) continue;
+        seen[nseen++] = G;
+        err = adapt ? launch_one<true>(G, blocks, st, a) : launch_one<false>(G, blocks, st, a);
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
 }
 
 size_t wfa_warp_bytes(int group, size_t group_bytes) {
