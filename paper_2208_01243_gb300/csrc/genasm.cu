@@ -66,7 +66,7 @@ struct GenasmArgs {
     size_t warp_bytes;              // carry row + stored levels of one warp
     size_t carry_bytes;             // offset of the stored levels inside a warp's scratch
     int W, overlap;
-    bool big_blocks;                // blocks of kBigBlock levels (else kSmallBlock)
+    bool big_blocks;                // blocks of kBigBlock levels (else kSmallBlock): picks the kernel instance
     uint32_t nwarps;
     uint32_t* counter;
 };
@@ -206,11 +206,9 @@ __device__ __forceinline__ int blocks_from(const Window& w, int lmax, Band* lv, 
 }
 
 // The window's distance (the first level whose bit wp-1 is set at t = 0), or -1 if it exceeds lmax.
-template <typename Band, bool FREE_R>
-__device__ __forceinline__ int window_distance(const Window& w, int lmax, bool big, Band* lv, size_t lstride,
-                                               uint64_t* carry) {
-    return big ? blocks_from<kBigBlock, Band, FREE_R>(w, lmax, lv, lstride, carry)
-               : blocks_from<kSmallBlock, Band, FREE_R>(w, lmax, lv, lstride, carry);
+template <int B, typename Band, bool FREE_R>
+__device__ __forceinline__ int window_distance(const Window& w, int lmax, Band* lv, size_t lstride, uint64_t* carry) {
+    return blocks_from<B, Band, FREE_R>(w, lmax, lv, lstride, carry);
 }
 
 // 5 blocks of 128 threads per SM (96 registers) measured faster than 6 (80) or 8 (64, with spills)
@@ -218,7 +216,8 @@ __device__ __forceinline__ int window_distance(const Window& w, int lmax, bool b
 #define AIM_GENASM_MIN_BLOCKS 5
 #endif
 
-template <typename Band>
+// B: distance levels per register block, a kernel instance per block size (one call uses one)
+template <typename Band, int B>
 __global__ void __launch_bounds__(128, AIM_GENASM_MIN_BLOCKS) genasm_kernel(GenasmArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -281,8 +280,8 @@ __global__ void __launch_bounds__(128, AIM_GENASM_MIN_BLOCKS) genasm_kernel(Gena
             // distance levels, in blocks, until the window's start is reached
             const int64_t left = k - used;
             const int lmax = (int)(left < (int64_t)max(wp, wt) ? left : (int64_t)max(wp, wt));
-            const int found = w.end_r ? window_distance<Band, false>(w, lmax, a.big_blocks, lv, lstride, carry)
-                                      : window_distance<Band, true>(w, lmax, a.big_blocks, lv, lstride, carry);
+            const int found = w.end_r ? window_distance<B, Band, false>(w, lmax, lv, lstride, carry)
+                                      : window_distance<B, Band, true>(w, lmax, lv, lstride, carry);
             // work of a plain bitap: levels 0..d (0..lmax when the window is over the budget) at every position
             st_cells += (unsigned long long)((found < 0 ? lmax : found) + 1) * wt;
             if (found < 0) { rejected = true; break; }
@@ -396,9 +395,13 @@ cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, 
     if (skip >= scratch_bytes) return cudaSuccess;
     a.scratch = base;
     const bool band = banded(W, max_limit);
+    // the four kernel instances: stored copies as 32-bit bands or whole words, blocks of 4 or 8 levels
+    void (*kernel)(GenasmArgs) = band ? (a.big_blocks ? genasm_kernel<uint32_t, kBigBlock>
+                                                      : genasm_kernel<uint32_t, kSmallBlock>)
+                                      : (a.big_blocks ? genasm_kernel<uint64_t, kBigBlock>
+                                                      : genasm_kernel<uint64_t, kSmallBlock>);
     int bps = 0;
-    cudaError_t err = band ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, genasm_kernel<uint32_t>, 128, 0)
-                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, genasm_kernel<uint64_t>, 128, 0);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 128, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     size_t warps = (size_t)num_sms * bps * 4;
@@ -409,8 +412,7 @@ cudaError_t launch_genasm(int W, int O, const PairsView& P, const LimitView& L, 
     if (warps == 0) return cudaSuccess;
     a.nwarps = (uint32_t)warps;
     const unsigned blocks = (unsigned)((warps + 3) / 4);
-    if (band) genasm_kernel<uint32_t><<<blocks, 128, 0, st>>>(a);
-    else genasm_kernel<uint64_t><<<blocks, 128, 0, st>>>(a);
+    kernel<<<blocks, 128, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
 }
