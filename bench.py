@@ -335,9 +335,10 @@ def run_ours(args, w, algo):
 
         def step(src=None):
             aim.aim_batch_run(plan)
-        # kernels per replay: 2 pack, bucket count/scan/scatter, alignment; a compact first pass adds the second
-        # pass's count/scan/scatter and alignment
-        launches_per_step = 6 + (4 if n_compact else 0)
+        # kernels per replay: 2 pack and 3 bucketing launches, then one alignment launch per distinct lanes-per-pair
+        # value; a compact first pass adds the second pass's count/scan/scatter and its alignment launches
+        first_eff = [f or g for f, g in zip(first_pass, full_pass)]
+        launches_per_step = 5 + (len(set(first_eff)) + 3 + len(set(full_pass)) if n_compact else len(set(full_pass)))
     else:
         def step(src=None):
             src = src or d
