@@ -572,8 +572,8 @@ def serving(args, local):
         pairs = sum(k for _, _, k in tickets)
         return np.array(lats), pairs, wall
 
-    # peak: a backlog of requests submitted at once
-    _, sizes = gen.arrivals(505, 160, 1.0)
+    # peak: a backlog of requests submitted at once (about a second of work, so start and drain matter little)
+    _, sizes = gen.arrivals(505, 480, 1.0)
     run(np.zeros(16), sizes[:16])                               # warm-up
     lat, pairs, wall = run(np.zeros(len(sizes)), sizes)
     peak = pairs / wall
@@ -583,8 +583,10 @@ def serving(args, local):
         rate = frac * peak / mean_req                          # requests per second
         count = max(20, int(rate * args.serve_seconds))
         arr, sz = gen.arrivals(600 + int(frac * 100), count, rate)
+        arr = arr * (float(sz.mean()) / mean_req)              # offered pairs/s = frac * peak for this sample's sizes
         lat, pairs, wall = run(arr, sz)
-        levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": frac * peak, "requests": count,
+        levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": float(sz.sum()) / float(arr[-1]) if count > 1 else
+                                         frac * peak, "requests": count,
                                          "sustained_alignments_per_s": pairs / wall,
                                          "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
                                          "p99_latency_ms": float(np.percentile(lat, 99) * 1e3)}
