@@ -489,15 +489,16 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
     }
 }
 
-#ifndef AIM_WFA_MIN_BLOCKS
-#define AIM_WFA_MIN_BLOCKS 4
-#endif
+// blocks of 256 per SM the register budget must allow: 4 (64 registers), except 3 (85 registers) for the exact
+// kernel with 32 lanes per pair, which measured 2.5 % faster that way on long pairs (the others were slower)
+template <int G, bool ADAPT>
+constexpr int wfa_min_blocks() { return (G == 32 && !ADAPT) ? 3 : 4; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
 // kernel with every variant spilled about 1 KB per thread and ran 14 % slower).
 template <int G, bool ADAPT>
-__global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a) {
+__global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT>())) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
@@ -516,17 +517,16 @@ __global__ void __launch_bounds__(256, AIM_WFA_MIN_BLOCKS) wfa_kernel(WfaArgs a)
 }
 
 template <bool ADAPT>
-cudaError_t launch_one(int G, unsigned blocks, cudaStream_t st, const WfaArgs& a) {
+void (*kernel_for(int G))(WfaArgs) {
     switch (G) {
-        case 1: wfa_kernel<1, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        case 2: wfa_kernel<2, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        case 4: wfa_kernel<4, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        case 8: wfa_kernel<8, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        case 16: wfa_kernel<16, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        case 32: wfa_kernel<32, ADAPT><<<blocks, 256, 0, st>>>(a); break;
-        default: wfa_kernel<256, ADAPT><<<blocks, 256, 0, st>>>(a); break;
+        case 1: return wfa_kernel<1, ADAPT>;
+        case 2: return wfa_kernel<2, ADAPT>;
+        case 4: return wfa_kernel<4, ADAPT>;
+        case 8: return wfa_kernel<8, ADAPT>;
+        case 16: return wfa_kernel<16, ADAPT>;
+        case 32: return wfa_kernel<32, ADAPT>;
+        default: return wfa_kernel<256, ADAPT>;
     }
-    return cudaGetLastError();
 }
 
 int gcd_i(int a, int b) {
@@ -614,27 +614,10 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
     a.retry_only = plan.retry_only;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int16_t)(b < nbuckets ? groups[b] : 32);
-    int bps = 0;
     const bool adapt = plan.adapt_min_len >= 0;
-    cudaError_t err = adapt ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<32, true>, 256, 0)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, wfa_kernel<32, false>, 256, 0);
-    if (err != cudaSuccess) return err;
-    if (bps < 1) bps = 1;
-    // whole blocks of 8 warps (a 256-lane group uses all of them)
-    size_t warps = (size_t)num_sms * bps * 8;
-    const size_t fit = scratch_bytes / warp_bytes;
-    if (warps > fit) warps = fit;
-    if (!bounds) {
-        const int g0 = groups[0];
-        const size_t need = g0 > 32 ? (size_t)P.num_pairs * (g0 / 32) : (P.num_pairs + (32 / g0) - 1) / (32 / g0);
-        if (warps > need) warps = (need + 7) / 8 * 8 <= fit ? (need + 7) / 8 * 8 : need;
-    }
-    warps = warps / 8 * 8;
-    if (warps == 0) return cudaSuccess;
-    a.nwarps = (uint32_t)warps;
-    const unsigned blocks = (unsigned)((warps + 7) / 8);
-    *warps_used = (int)warps;
-    // one launch per distinct group size, in the order the buckets (heaviest first) first use it
+    int launched = 0;
+    // one launch per distinct group size, in the order the buckets (heaviest first) first use it; each sized
+    // by its own instance's occupancy (whole blocks of 8 warps: a 256-lane group uses all of them)
     int seen[kMaxBuckets];
     int nseen = 0;
     for (int b = 0; b < nbuckets; ++b) {
@@ -643,9 +626,27 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         for (int i = 0; i < nseen; ++i) dup |= seen[i] == G;
         if (dup) continue;
         seen[nseen++] = G;
-        err = adapt ? launch_one<true>(G, blocks, st, a) : launch_one<false>(G, blocks, st, a);
+        void (*kernel)(WfaArgs) = adapt ? kernel_for<true>(G) : kernel_for<false>(G);
+        int bps = 0;
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, 0);
         if (err != cudaSuccess) return err;
+        if (bps < 1) bps = 1;
+        size_t warps = (size_t)num_sms * bps * 8;
+        const size_t fit = scratch_bytes / warp_bytes;
+        if (warps > fit) warps = fit;
+        if (!bounds) {
+            const size_t need = G > 32 ? (size_t)P.num_pairs * (G / 32) : (P.num_pairs + (32 / G) - 1) / (32 / G);
+            if (warps > need) warps = (need + 7) / 8 * 8 <= fit ? (need + 7) / 8 * 8 : need;
+        }
+        warps = warps / 8 * 8;
+        if (warps == 0) { *warps_used = 0; return cudaSuccess; }   // not one block's scratch fits: caller reports it
+        a.nwarps = (uint32_t)warps;
+        kernel<<<(unsigned)(warps / 8), 256, 0, st>>>(a);
+        err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+        launched = std::max(launched, (int)warps);
     }
+    *warps_used = launched;
     return cudaSuccess;
 }
 
