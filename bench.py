@@ -5,8 +5,8 @@
 A step aligns one whole batch on inputs already in device memory.  The
 default workload (4M pairs, reads 100-1000 bp, 1-10 % edits, thresholds at
 10 % of length) runs the batched form: one CUDA-graph replay of 2-bit packing,
-device-side bucketing and one persistent WFA launch over the buckets with
-autotuned lanes per pair (aim_batch_run); the plain form (one
+device-side bucketing and persistent WFA launches (one per lanes-per-pair value)
+over the buckets with autotuned lanes per pair (aim_batch_run); the plain form (one
 aim_align_batch_ascii launch per read-length group) is timed beside it on the
 same pairs and must give identical results.  The other workloads run one
 aim_align_batch_ascii call per step.  `e2e` repeats the step with the inputs in pinned host memory and

@@ -226,11 +226,13 @@ AIM_API int aim_set_genasm_window(aim_ctx *ctx, int window, int overlap);
 
 /*
  * Batched form (wavefront algorithm): pairs of uneven length and error rate
- * in one persistent launch.  The batch is planned once and then replayed:
+ * in persistent launches over length-bucketed queues.  The batch is planned
+ * once and then replayed:
  *   - packing, length/threshold bucketing of the pairs (on the device: a
  *     histogram, a scan and a scatter into an order array, heaviest work class
- *     first) and one persistent alignment launch that drains the buckets in
- *     that order are recorded as one CUDA graph;
+ *     first, buckets sharing a lanes-per-pair value kept contiguous) and one
+ *     persistent alignment launch per lanes-per-pair value, each draining its
+ *     queue range in that order, are recorded as one CUDA graph;
  *   - with `autotune`, the lanes per pair of every non-empty bucket are chosen by
  *     timed trial launches on a device-filling sample of its pairs (each choice cached in
  *     the context per costs, band and bucket); otherwise from the bucket's

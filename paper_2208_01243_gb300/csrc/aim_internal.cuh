@@ -154,7 +154,8 @@ struct WfaArgs {
     int16_t group[kMaxBuckets]; // lanes per pair of each bucket (1..32, or 256: a whole block)
 };
 
-// one launch over buckets (longest-first order given by the caller)
+// bucketed queues (longest-first order given by the caller): one launch per distinct group size among the
+// buckets, each draining the buckets of its size; warps_used: the largest grid (0: nothing fitted)
 cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const LimitView& L, const OutView& O,
                                const uint32_t* order, const uint32_t* bounds, const int* groups, int nbuckets,
                                size_t warp_bytes, uint8_t* scratch, size_t scratch_bytes, uint32_t* counters,

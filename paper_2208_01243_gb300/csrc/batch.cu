@@ -1,7 +1,8 @@
 // Batched form of the wavefront aligner: pairs of uneven length and error
-// rate go into one persistent launch through length-bucketed work queues,
-// with the lanes per pair of every bucket chosen by an autotuner and the
-// whole run (packing, bucketing, alignment) replayed as a CUDA graph.
+// rate go through length-bucketed work queues into persistent launches (one
+// per lanes-per-pair value), with the lanes per pair of every bucket chosen by
+// an autotuner and the whole run (packing, bucketing, alignment) replayed as a
+// CUDA graph.
 //
 // Buckets.  Each pair's work is bounded by its threshold: with S = limit/g
 // scaled score steps, no wavefront is wider than W = min(2 S/E + 3, n+m+1,

@@ -43,10 +43,12 @@
 // D~[c,k] reaches the current offset; its length comes from a backward
 // comparison of 32-base windows (XOR, count trailing zero base pairs).
 //
-// Work distribution: the launch walks a list of buckets (a range of a pair
-// order array plus a group size each); warps take 32/G consecutive positions
-// of a bucket from its device counter, and move to the next bucket when it is
-// exhausted, so a longest-first bucket order leaves short pairs for the tail.
+// Work distribution: a launch is compiled for one group size G and walks the
+// buckets of that size (each a range of a pair order array); warps take 32/G
+// consecutive positions of a bucket from its device counter and move to the
+// next bucket when it is exhausted, so a longest-first bucket order leaves
+// short pairs for the tail.  Callers with buckets of several sizes get one
+// launch per size.
 #include <algorithm>
 #include <cstdint>
 #include <vector>
