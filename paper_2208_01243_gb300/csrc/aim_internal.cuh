@@ -109,13 +109,16 @@ cudaError_t launch_dp(const DpPlan& plan, const Costs& c, const PairsView& P, co
                       int num_sms, cudaStream_t st, int* warps_used);
 
 constexpr int kMaxBuckets = 32;
+// wavefront history: one entry per (score, diagonal) holds M~, I~, D~ and a spare slot as four int16, so an entry
+// is written with one 8-byte store
+constexpr int kEntryElems = 4;
 
 struct WfaPlan {
     int g;               // gcd of the costs; scores run in units of g
     int x, oe, e;        // scaled mismatch, open+extend, extend
     int64_t smax;        // largest scaled score any pair may reach
     int band;            // < 0: none
-    size_t hist_elems;   // int16 entries of wavefront history per pair (worst case)
+    size_t hist_elems;   // int16 elements of wavefront history per pair (worst case; kEntryElems per entry)
     int runs_cap;        // CIGAR runs staged per pair
     size_t meta_bytes;   // per-score (lo, hi, base, width) records, int4 each
     size_t runs_bytes;   // run staging

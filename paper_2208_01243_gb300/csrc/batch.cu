@@ -145,11 +145,11 @@ size_t bucket_group_bytes(const WfaPlan& plan, int b, uint32_t max_length) {
     size_t hist = plan.hist_elems;
     if (kc < kWorkClasses - 1) {
         const size_t cmax = ((size_t)1 << (3 * (kc + 1))) - 1;
-        hist = std::min(hist, 3 * cmax + 3);
+        hist = std::min(hist, kEntryElems * (cmax + 1));
     }
     if (wc < kWidthClasses - 1) {
         const size_t wmax = (size_t)64 << wc;
-        hist = std::min(hist, 3 * ((size_t)plan.smax + 1) * wmax + 3);
+        hist = std::min(hist, kEntryElems * (((size_t)plan.smax + 1) * wmax + 1));
     }
     (void)max_length;
     return align_up(plan.meta_bytes + plan.runs_bytes + hist * sizeof(int16_t), 16);

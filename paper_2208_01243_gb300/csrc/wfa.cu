@@ -59,8 +59,8 @@ namespace aim {
 namespace {
 
 struct Wf {
-    int lo, cnt, base, w;   // diagonals lo .. lo+cnt-1 (cnt == 0: empty); diagonal k of component c at
-                            // base + c*w + k (base already offset by -lo)
+    int lo, cnt, base, w;   // diagonals lo .. lo+cnt-1 (cnt == 0: empty); component c of diagonal k at element
+                            // (base + k) * kEntryElems + c (base: first entry, already offset by -lo)
 };
 
 __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
@@ -76,7 +76,7 @@ __device__ __forceinline__ int wf_hi(const Wf& f) { return f.lo + f.cnt - 1; }
 // component c (0 M, 1 I, 2 D) of wavefront f at diagonal k, or a negative value
 __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, int k) {
     if ((unsigned)(k - f.lo) >= (unsigned)f.cnt) return kNeg16;   // one compare covers both ends and empty
-    return hist[f.base + c * f.w + k];
+    return hist[(f.base + k) * kEntryElems + c];
 }
 
 // furthest offset reached from (h - k, h) along matches on diagonal k
@@ -251,13 +251,13 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, w0);
         st.windows += w0;
         ++st.cells;
-        hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16;
+        hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
         found0 = (kend == 0 && m0 >= m);
     }
     found0 = grp.bcast(found0);
     if (status == kRun) {
-        top = 3;
+        top = 1;   // entries used
         if (found0) status = kDone;
     }
     grp.sync();
@@ -277,7 +277,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
             w = lo <= hi ? hi - lo + 1 : 0;
-            if (w && (size_t)top + 3 * (size_t)w > hist_cap) { status = kCap; run = false; w = 0; }
+            if (w && ((size_t)top + (size_t)w) * kEntryElems > hist_cap) { status = kCap; run = false; w = 0; }
         }
         const int iters = grp.iterations(w);
         bool hit = false;
@@ -298,9 +298,8 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
                 const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, n_windows) : kNeg16;
                 ++n_cells;
-                hist[base + k] = (int16_t)mv;
-                hist[base + w + k] = (int16_t)ins;
-                hist[base + 2 * w + k] = (int16_t)del;
+                *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
+                    (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
                 hit |= (k == kend && mv >= m);
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
             }
@@ -317,7 +316,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
             for (int it = 0; it < iters; ++it) {
                 const int k = lo + gl + it * G;
                 if (prune && k >= vlo && k <= vhi) {
-                    const int h = hist[base + k];
+                    const int h = hist[(size_t)(base + k) * kEntryElems];
                     if (h >= 0) dmin = min(dmin, max(n - (h - k), m - h));
                 }
             }
@@ -326,7 +325,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
             for (int it = 0; it < iters; ++it) {
                 const int k = lo + gl + it * G;
                 if (prune && k >= vlo && k <= vhi) {
-                    const int h = hist[base + k];
+                    const int h = hist[(size_t)(base + k) * kEntryElems];
                     if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
                         klo = min(klo, k);
                         khi = max(khi, k);
@@ -341,7 +340,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
                 reinterpret_cast<int4*>(meta)[s] = rec;
             }
-            top += 3 * w;
+            top += w;
             if (group_hit) { status = kDone; final_s = s; }
         }
         grp.sync();
@@ -544,7 +543,7 @@ size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax) {
     const int64_t khi = p.band >= 0 ? std::min<int64_t>(max_len, p.band) : max_len;
     std::vector<int64_t> lo(smax + 1), hi(smax + 1);
     lo[0] = 0; hi[0] = 0;
-    size_t elems = 3;
+    size_t elems = kEntryElems;
     for (int64_t s = 1; s <= smax; ++s) {
         int64_t l = INT64_MAX, h = INT64_MIN;
         auto take = [&](int64_t src, int64_t grow) {
@@ -554,7 +553,7 @@ size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax) {
         take(s - p.x, 0); take(s - p.oe, 1); take(s - p.e, 1);
         l = std::max(l, klo); h = std::min(h, khi);
         lo[s] = l; hi[s] = h;
-        if (l <= h) elems += 3 * (size_t)(h - l + 1);
+        if (l <= h) elems += kEntryElems * (size_t)(h - l + 1);
     }
     return elems;
 }
@@ -586,7 +585,7 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
 
 WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width) {
     WfaPlan p = full;
-    const size_t compact = 3 * (size_t)(full.smax + 1) * (size_t)std::max<int64_t>(width, 1) + 3;
+    const size_t compact = kEntryElems * ((size_t)(full.smax + 1) * (size_t)std::max<int64_t>(width, 1) + 1);
     if (compact < p.hist_elems) p.hist_elems = compact;
     p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
     return p;
