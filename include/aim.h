@@ -380,7 +380,7 @@ AIM_API int aim_timing_read(aim_ctx *ctx, int kind, double *total_ms /* host */,
  * before any stream capture.
  *
  * Limits: if one pair's scratch (from max_length, the threshold and the band;
- * about 4.5 KB for 150 bp reads at 6 edits, about 1 MB for 1 kbp at 100 edits)
+ * about 5.5 KB for 150 bp reads at 6 edits, about 1.3 MB for 1 kbp at 100 edits)
  * exceeds the 32 MiB array, the call returns AIM_ERR_NOMEM and launches
  * nothing.  Smaller scratch needs let more warps run at once.  Otherwise
  * arguments, flags and results are those of aim_align_batch, bit for bit.
