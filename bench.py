@@ -10,7 +10,9 @@ over the buckets with autotuned lanes per pair (aim_batch_run); the plain form (
 aim_align_batch_ascii launch per read-length group) is timed beside it on the
 same pairs and must give identical results.  The other workloads run one
 aim_align_batch_ascii call per step.  `e2e` repeats the step with the inputs in pinned host memory and
-the host<->device copies inside the timed region.  Multi-GPU (torchrun): every
+the host<->device copies inside the timed region, as a double-buffered pipeline (step i+1's inputs copy in
+and step i's results copy out while step i aligns); `e2e.serial` times the same steps one after another.
+Multi-GPU (torchrun): every
 rank aligns its own slice of the pair stream (weak scaling, no collective on
 the data path); timing is bracketed by barriers and the slowest rank counts.
 `--impl reference` times the CPU oracle on a bounded sample of the workload.
@@ -425,34 +427,102 @@ def run_ours(args, w, algo):
                  "batched_pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c}}
         del gd
 
-    # ---- end to end through the same call: pinned host inputs in, results out, copies timed
+    # ---- end to end through the same call: pinned host inputs in, results out, copies timed.  The steps run as
+    # a double-buffered pipeline over two device buffer sets: step i+1's inputs copy in on one copy stream while
+    # step i aligns on the compute stream, and step i's results copy out on a second copy stream meanwhile.
+    # Every step still copies its own inputs in and its own results out inside the timed region.
     hp = {k: torch.from_numpy(np.ascontiguousarray(v).view(
         {np.dtype(np.uint64): np.int64, np.dtype(np.uint32): np.int32}.get(np.asarray(v).dtype, np.asarray(v).dtype)))
         .pin_memory() for k, v in host.items()}
-    ho = {k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()}
     h2d = sum(v.numel() * v.element_size() for v in hp.values())
-    d2h = sum(v.numel() * v.element_size() for v in ho.values())
-    # the batched plan is bound to the device buffers d: the e2e step refills them from pinned host memory
-    dd = d if batched else {k: torch.empty_like(v, device=dev) for k, v in hp.items()}
+    d2h = sum(v.numel() * v.element_size() for v in out.values())
+    # set 0: the buffers the device-resident run used (a batched plan is bound to them); set 1: a second copy
+    din = [d if batched else {k: torch.empty_like(v, device=dev) for k, v in hp.items()},
+           {k: torch.empty_like(v, device=dev) for k, v in hp.items()}]
+    dout = [out, {k: torch.empty_like(v) for k, v in out.items()}]
+    hout = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()} for _ in range(2)]
+    for k in hp:   # planning packs and buckets the bound inputs, so the second set holds them first
+        din[1][k].copy_(hp[k])
+    torch.cuda.synchronize()
+    plan1 = None
+    if batched:   # the second plan takes the lanes per bucket the first one tuned (cached in the context)
+        plan1 = aim.aim_batch_plan(al.ctx, din[1]["reads"], din[1]["targets"], din[1]["ro"], din[1]["to"],
+                                   din[1]["rl"], din[1]["tl"], max_len, pen, max_edits, din[1].get("pp"),
+                                   dout[1]["scores"], dout[1]["cigars"], coff_d, dout[1]["lens"], dout[1]["flags"],
+                                   scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=False)
+    plans = [plan, plan1]
+    cs = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
 
-    def e2e_step():
+    def align_set(b):
+        if batched:
+            aim.aim_batch_run(plans[b], cs)
+        else:
+            src, o = din[b], dout[b]
+            aim.aim_align_batch_ascii(al.ctx, src["reads"], src["targets"], src["ro"], src["to"], src["rl"],
+                                      src["tl"], max_len, algo, pen, max_edits, src.get("pp"), o["scores"],
+                                      o["cigars"], coff_d, o["lens"], o["flags"], stream=cs)
+
+    def e2e_run(n_steps):
+        """n_steps pipelined steps; returns the elapsed ms from before the first copy in to after the last copy
+        out."""
+        ev = lambda: torch.cuda.Event(enable_timing=False)
+        aligned = [None, None]    # per set: its last step's alignment finished (inputs free, results ready)
+        copied = [None, None]     # per set: its last step's results are in host memory (outputs free)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(cs)
+        s_in.wait_event(t0)
+        for i in range(n_steps):
+            b = i % 2
+            if aligned[b] is not None:
+                s_in.wait_event(aligned[b])
+            with torch.cuda.stream(s_in):
+                for k in hp:
+                    din[b][k].copy_(hp[k], non_blocking=True)
+            loaded = ev(); loaded.record(s_in)
+            cs.wait_event(loaded)
+            if copied[b] is not None:
+                cs.wait_event(copied[b])
+            align_set(b)
+            aligned[b] = ev(); aligned[b].record(cs)
+            s_out.wait_event(aligned[b])
+            with torch.cuda.stream(s_out):
+                for k in out:
+                    hout[b][k].copy_(dout[b][k], non_blocking=True)
+            copied[b] = ev(); copied[b].record(s_out)
+        for c in copied:
+            if c is not None:
+                cs.wait_event(c)
+        t1.record(cs)
+        torch.cuda.synchronize()
+        return t0.elapsed_time(t1)
+
+    e2e_run(max(2, args.warmup))
+    barrier(); torch.cuda.synchronize()
+    e2e_ms = _dist_max(e2e_run(args.steps) / args.steps, dev, world)
+    for b in range(min(2, args.steps)):
+        assert np.array_equal(hout[b]["scores"].numpy(), res_scores), "e2e results differ from the device-resident run"
+        assert np.array_equal(hout[b]["flags"].numpy(), res_flags), "e2e flags differ from the device-resident run"
+
+    # the same steps one after another (copy in, align, copy out), for comparison
+    def serial_step():
         for k in hp:
-            dd[k].copy_(hp[k], non_blocking=True)
-        step(dd)
+            din[0][k].copy_(hp[k], non_blocking=True)
+        align_set(0)
         for k in out:
-            ho[k].copy_(out[k], non_blocking=True)
-
-    for _ in range(max(1, args.warmup)):
-        e2e_step()
+            hout[0][k].copy_(dout[0][k], non_blocking=True)
+    serial_step()
     torch.cuda.synchronize(); barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    e0.record(cs)
     for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
+        serial_step()
+    e1.record(cs)
     torch.cuda.synchronize(); barrier()
-    e2e_ms = _dist_max(e0.elapsed_time(e1) / args.steps, dev, world)
-    assert np.array_equal(ho["scores"].numpy(), res_scores), "e2e results differ from the device-resident run"
+    serial_ms = _dist_max(e0.elapsed_time(e1) / args.steps, dev, world)
+    if plan1 is not None:
+        aim.aim_batch_destroy(plan1)
+    del din, dout
 
     if rank != 0:
         if plan is not None:
@@ -506,7 +576,11 @@ def run_ours(args, w, algo):
             "rejected_frac": float((res_flags & 1).mean()),
             "roofline": roof,
             "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
-                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                    "form": "double-buffered: step i+1's inputs copy in and step i's results copy out while step i "
+                            "aligns (two copy streams, two device buffer sets)",
+                    "serial": {"value": world * n_pairs / (serial_ms / 1e3), "ms_per_step": serial_ms,
+                               "form": "copy in, align, copy out, one step after another"}},
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk}
     if plain is not None:

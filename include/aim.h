@@ -245,6 +245,8 @@ AIM_API int aim_set_genasm_window(aim_ctx *ctx, int window, int overlap);
  * aim_batch_plan synchronises the device, allocates the plan's own device
  * memory (packed copies, bucket arrays, order, scratch) and launches trial
  * runs; aim_batch_run is asynchronous on `stream` (one graph launch).
+ * Planning packs and buckets the bound inputs, so they must already hold
+ * valid pairs (offsets and lengths inside their arrays) when it is called.
  * Results are bit-identical to aim_align_batch_ascii with AIM_ALGO_WFA_AFFINE.
  * One plan must not run concurrently with itself.
  */

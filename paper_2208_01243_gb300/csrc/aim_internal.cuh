@@ -148,6 +148,7 @@ struct WfaArgs {
     size_t meta_bytes, runs_bytes;
     uint32_t runs_cap;
     uint32_t nwarps;
+    uint32_t seq_slot_words;   // words per sequence copy in shared memory (0: the extend reads global memory)
     const uint32_t* order;     // pair index at each queue position, or null (identity)
     const uint32_t* bounds;    // bucket b covers queue positions [bounds[b], bounds[b+1]); null: one bucket of all
     uint32_t* counters;        // one claim counter per bucket, zero at launch

@@ -19,6 +19,9 @@
 // Lane j of a group handles diagonals lo+j, lo+j+G, ...  The extend compares
 // 32 bases at a time: a two-word funnel shift aligns each sequence to the
 // current base, XOR marks mismatching bases, and clz/2 counts leading matches.
+// Launches of groups up to 16 lanes first copy each pair's packed read and
+// target into shared memory (when a block's copies fit in 24 KB), so their
+// extends read at shared-memory latency.
 // Each wavefront is trimmed to the diagonals that hold a valid entry, so the
 // next range grows only from reachable diagonals.
 //
@@ -79,13 +82,25 @@ __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, i
     return hist[(f.base + k) * kEntryElems + c];
 }
 
-// furthest offset reached from (h - k, h) along matches on diagonal k
+// 32 bases starting at base pos of a sequence of nwords words, for pos inside the sequence (so word pos / 32
+// exists); the word after it reads as 0 past the end.  w may point to global or shared memory.  (lo >> 1) >> (63 - sh) is lo >> (64 - sh) for sh > 0 and
+// 0 for sh == 0, with no branch.
+template <bool GENERIC>
+__device__ __forceinline__ uint64_t window_in(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
+    const uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
+    const uint64_t hi = GENERIC ? w[wi] : __ldg(w + wi);
+    const uint64_t lo = wi + 1 < nwords ? (GENERIC ? w[wi + 1] : __ldg(w + wi + 1)) : 0ull;
+    return (hi << sh) | ((lo >> 1) >> (63 - sh));
+}
+
+// furthest offset reached from (h - k, h) along matches on diagonal k (GENERIC: P, T may be shared copies)
+template <bool GENERIC>
 __device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, const uint64_t* Tw, uint32_t nwT,
                                       int m, int k, int h, uint32_t& windows) {
     int v = h - k;
     while (v < n && h < m) {
         ++windows;
-        const uint64_t d = window32(Pw, nwP, (uint32_t)v) ^ window32(Tw, nwT, (uint32_t)h);
+        const uint64_t d = window_in<GENERIC>(Pw, nwP, (uint32_t)v) ^ window_in<GENERIC>(Tw, nwT, (uint32_t)h);
         const int rem = min(n - v, m - h);
         int adv = d ? (__clzll((long long)d) >> 1) : 32;
         if (adv > rem) adv = rem;
@@ -197,9 +212,13 @@ struct Counters {
 // order positions q0 + g (those < qend).  All lanes must call this together.
 // ADAPT: WFA-adaptive pruning and the source-following traceback (a kernel of its own, so the exact
 // algorithm carries none of its registers).
+// group sizes whose launches copy each pair's sequences to shared memory for the extend
+__host__ __device__ constexpr bool wfa_staged(int G) { return G <= 16; }
+
 template <int G, bool ADAPT>
 __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
                              Counters& st) {
+    constexpr bool kStaged = wfa_staged(G);
     const Group<G> grp(lane);
     const int g = grp.index(lane), gl = grp.gl;
     const size_t group_bytes =
@@ -215,7 +234,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     int status = kIdle;
     uint32_t pi = 0;
     int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0;
-    const uint64_t *Pw = nullptr, *Tw = nullptr;
+    const uint64_t *Pw = nullptr, *Tw = nullptr;   // what the extend reads: global memory or the group's copy
     uint32_t nwP = 0, nwT = 0;
     if (q < qend && a.retry_only && a.O.flags[a.order ? a.order[q] : q] != AIM_F_STEP_CAP) {
         // second pass: this pair already has its result
@@ -243,12 +262,28 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         if (gl == 0) st.pairs += 1;
     }
 
+    // the group's copy of its pair in shared memory, one spare word after each sequence (launches whose
+    // copies fit; the extend then reads them at shared-memory latency)
+    if (kStaged && a.seq_slot_words) {
+        extern __shared__ uint64_t s_seq[];
+        const uint32_t slot = G > 32 ? 0u : (threadIdx.x >> 5) * (uint32_t)(32 / G) + (uint32_t)g;
+        uint64_t* sP = s_seq + (size_t)slot * 2 * a.seq_slot_words;
+        uint64_t* sT = sP + a.seq_slot_words;
+        if (status == kRun) {
+            for (uint32_t j = (uint32_t)gl; j < nwP; j += (uint32_t)G) sP[j] = __ldg(Pw + j);
+            for (uint32_t j = (uint32_t)gl; j < nwT; j += (uint32_t)G) sT[j] = __ldg(Tw + j);
+            if (gl == 0) { sP[nwP] = 0; sT[nwT] = 0; }
+            Pw = sP; Tw = sT;
+        }
+        grp.sync();
+    }
+
     // score 0: diagonal 0 only
     int top = 0, final_s = 0;
     int found0 = 0;
     if (status == kRun && gl == 0) {
         uint32_t w0 = 0;
-        const int m0 = extend(Pw, nwP, n, Tw, nwT, m, 0, 0, w0);
+        const int m0 = extend<kStaged>(Pw, nwP, n, Tw, nwT, m, 0, 0, w0);
         st.windows += w0;
         ++st.cells;
         hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
@@ -296,7 +331,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 mis = mis >= 0 ? mis + 1 : kNeg16;
                 if (mis > m || mis - k > n) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
-                const int mv = f0 >= 0 ? extend(Pw, nwP, n, Tw, nwT, m, k, f0, n_windows) : kNeg16;
+                const int mv = f0 >= 0 ? extend<kStaged>(Pw, nwP, n, Tw, nwT, m, k, f0, n_windows) : kNeg16;
                 ++n_cells;
                 *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
                     (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
@@ -397,6 +432,8 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     if (!ADAPT && status == kDone && gl == 0) {
         const int* __restrict__ cmeta = meta;
         const int16_t* __restrict__ chist = hist;
+        const uint64_t* Pg = read_words(a.P, pi);     // the pair in global memory (Pw, Tw may be shared copies)
+        const uint64_t* Tg = target_words(a.P, pi);
         RunWriter wr;
         wr.init(staged, a.runs_cap);
         int v = n, h = m, cM = final_s, cI = final_s, cD = final_s;
@@ -405,7 +442,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
             const bool diag = v > 0 && h > 0;
             const Wf fX = load_wf(cmeta, cM - X), fI = load_wf(cmeta, cI), fD = load_wf(cmeta, cD);
             const Wf fM = load_wf(cmeta, cM);
-            const uint32_t pb = diag ? base_at(Pw, v - 1) : 0u, tb = diag ? base_at(Tw, h - 1) : 1u;
+            const uint32_t pb = diag ? base_at(Pg, v - 1) : 0u, tb = diag ? base_at(Tg, h - 1) : 1u;
             const int vX = wf_get(chist, fX, 0, k), vI = wf_get(chist, fI, 1, k), vD = wf_get(chist, fD, 2, k);
             const int vM = wf_get(chist, fM, 0, k);
             const int stop = max(wf_get(chist, fM, 1, k), wf_get(chist, fM, 2, k));
@@ -424,7 +461,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 wr.put(kOpDel, 1);
             } else if (match && vM >= h - 1) {
                 const int c = cM;
-                int run = match_run_back(Pw, nwP, v, Tw, nwT, h);
+                int run = match_run_back(Pg, nwP, v, Tg, nwT, h);
                 if (run > h - stop) run = h - stop;
                 if (run < 1) { ok = false; break; }
                 v -= run; h -= run;
@@ -530,6 +567,9 @@ void (*kernel_for(int G))(WfaArgs) {
     }
 }
 
+// shared memory per block for the pairs' sequence copies; above it the extend reads global memory
+constexpr size_t kStageBytes = 24 << 10;
+
 int gcd_i(int a, int b) {
     while (b) { const int t = a % b; a = b; b = t; }
     return a < 0 ? -a : a;
@@ -628,8 +668,14 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         if (dup) continue;
         seen[nseen++] = G;
         void (*kernel)(WfaArgs) = adapt ? kernel_for<true>(G) : kernel_for<false>(G);
+        // sequence copies in shared memory when a block's fit in kStageBytes
+        const size_t slot_words = ((size_t)P.max_length + 31) / 32 + 1;
+        const size_t groups_per_block = G > 32 ? 1 : (size_t)8 * (32 / G);
+        size_t smem = groups_per_block * 2 * slot_words * sizeof(uint64_t);
+        if (!wfa_staged(G) || smem > kStageBytes) smem = 0;
+        a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
         int bps = 0;
-        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, 0);
+        cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, smem);
         if (err != cudaSuccess) return err;
         if (bps < 1) bps = 1;
         size_t warps = (size_t)num_sms * bps * 8;
@@ -642,7 +688,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         warps = warps / 8 * 8;
         if (warps == 0) { *warps_used = 0; return cudaSuccess; }   // not one block's scratch fits: caller reports it
         a.nwarps = (uint32_t)warps;
-        kernel<<<(unsigned)(warps / 8), 256, 0, st>>>(a);
+        kernel<<<(unsigned)(warps / 8), 256, smem, st>>>(a);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
         launched = std::max(launched, (int)warps);
