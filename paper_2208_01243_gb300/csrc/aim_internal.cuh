@@ -25,12 +25,12 @@ __device__ __forceinline__ uint32_t base_at(const uint64_t* __restrict__ w, uint
 
 // 32 bases starting at base `pos` of a sequence of `nwords` words, first base in the top bits.
 // Bases past the last word read as 0; callers cap comparisons by the remaining length.
+// (lo >> 1) >> (63 - sh) is lo >> (64 - sh) for sh > 0 and 0 for sh == 0: no branch for lanes to diverge on.
 __device__ __forceinline__ uint64_t window32(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
-    uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
-    uint64_t hi = wi < nwords ? __ldg(w + wi) : 0ull;
-    if (sh == 0) return hi;
-    uint64_t lo = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0ull;
-    return (hi << sh) | (lo >> (64 - sh));
+    const uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
+    const uint64_t hi = wi < nwords ? __ldg(w + wi) : 0ull;
+    const uint64_t lo = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0ull;
+    return (hi << sh) | ((lo >> 1) >> (63 - sh));
 }
 
 // ---- per-call description handed to the kernels ----

@@ -114,7 +114,7 @@ __device__ __forceinline__ int match_run(const uint64_t* rw, uint32_t nrw, uint3
     int run = 0;
     while (run < cap) {
         const uint64_t x = window32(rw, nrw, p + run) ^ window32(tw, ntw, q + run);
-        const int same = x ? (__clzll(x) >> 1) : 32;
+        const int same = __clzll((long long)x) >> 1;   // __clzll(0) = 64: the whole window matches
         run += same;
         if (same < 32) break;
     }

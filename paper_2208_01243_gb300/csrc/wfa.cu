@@ -98,13 +98,12 @@ template <bool GENERIC>
 __device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, const uint64_t* Tw, uint32_t nwT,
                                       int m, int k, int h, uint32_t& windows) {
     int v = h - k;
-    while (v < n && h < m) {
+    int rem = min(n - v, m - h);   // bases left on both sequences
+    while (rem > 0) {
         ++windows;
         const uint64_t d = window_in<GENERIC>(Pw, nwP, (uint32_t)v) ^ window_in<GENERIC>(Tw, nwT, (uint32_t)h);
-        const int rem = min(n - v, m - h);
-        int adv = d ? (__clzll((long long)d) >> 1) : 32;
-        if (adv > rem) adv = rem;
-        v += adv; h += adv;
+        const int adv = min(__clzll((long long)d) >> 1, rem);   // __clzll(0) = 64: the whole window matches
+        v += adv; h += adv; rem -= adv;
         if (adv < 32) break;
     }
     return h;
