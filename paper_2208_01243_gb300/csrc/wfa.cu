@@ -82,26 +82,51 @@ __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, i
     return hist[(f.base + k) * kEntryElems + c];
 }
 
-// 32 bases starting at base pos of a sequence of nwords words, for pos inside the sequence (so word pos / 32
-// exists); the word after it reads as 0 past the end.  w may point to global or shared memory.  (lo >> 1) >> (63 - sh) is lo >> (64 - sh) for sh > 0 and
-// 0 for sh == 0, with no branch.
-template <bool GENERIC>
+// 32 bases starting at base pos of a sequence of nwords words in global memory, for pos inside the sequence
+// (so word pos / 32 exists); the word after it reads as 0 past the end.  (lo >> 1) >> (63 - sh) is
+// lo >> (64 - sh) for sh > 0 and 0 for sh == 0, with no branch.
 __device__ __forceinline__ uint64_t window_in(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
     const uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
-    const uint64_t hi = GENERIC ? w[wi] : __ldg(w + wi);
-    const uint64_t lo = wi + 1 < nwords ? (GENERIC ? w[wi + 1] : __ldg(w + wi + 1)) : 0ull;
+    const uint64_t hi = __ldg(w + wi);
+    const uint64_t lo = wi + 1 < nwords ? __ldg(w + wi + 1) : 0ull;
     return (hi << sh) | ((lo >> 1) >> (63 - sh));
 }
 
-// furthest offset reached from (h - k, h) along matches on diagonal k (GENERIC: P, T may be shared copies)
-template <bool GENERIC>
-__device__ __forceinline__ int extend(const uint64_t* Pw, uint32_t nwP, int n, const uint64_t* Tw, uint32_t nwT,
-                                      int m, int k, int h, uint32_t& windows) {
+// copies of the pairs' packed sequences, one slot per group (launches with sequence staging)
+extern __shared__ uint64_t s_seq[];
+
+// the same window from a copy at word offset `off` of s_seq, which holds a spare word after the sequence, so
+// both loads stay inside it without a check
+__device__ __forceinline__ uint64_t window_shared(uint32_t off, uint32_t pos) {
+    const uint32_t wi = off + (pos >> 5), sh = 2 * (pos & 31);
+    return (s_seq[wi] << sh) | ((s_seq[wi + 1] >> 1) >> (63 - sh));
+}
+
+// the extend's view of one pair: global memory, or the group's copies in shared memory
+template <bool STAGE>
+struct PairSeqs;
+template <>
+struct PairSeqs<false> {
+    const uint64_t *P, *T;
+    uint32_t nwP, nwT;
+    __device__ uint64_t read_window(uint32_t pos) const { return window_in(P, nwP, pos); }
+    __device__ uint64_t target_window(uint32_t pos) const { return window_in(T, nwT, pos); }
+};
+template <>
+struct PairSeqs<true> {
+    uint32_t offP, offT;
+    __device__ uint64_t read_window(uint32_t pos) const { return window_shared(offP, pos); }
+    __device__ uint64_t target_window(uint32_t pos) const { return window_shared(offT, pos); }
+};
+
+// furthest offset reached from (h - k, h) along matches on diagonal k
+template <bool STAGE>
+__device__ __forceinline__ int extend(const PairSeqs<STAGE>& q, int n, int m, int k, int h, uint32_t& windows) {
     int v = h - k;
     int rem = min(n - v, m - h);   // bases left on both sequences
     while (rem > 0) {
         ++windows;
-        const uint64_t d = window_in<GENERIC>(Pw, nwP, (uint32_t)v) ^ window_in<GENERIC>(Tw, nwT, (uint32_t)h);
+        const uint64_t d = q.read_window((uint32_t)v) ^ q.target_window((uint32_t)h);
         const int adv = min(__clzll((long long)d) >> 1, rem);   // __clzll(0) = 64: the whole window matches
         v += adv; h += adv; rem -= adv;
         if (adv < 32) break;
@@ -157,12 +182,12 @@ struct Group<G, false> {
         if constexpr (G == 32) {   // the whole warp is one group: one warp-wide reduction each
             lo = __reduce_min_sync(kFull, lo);
             hi = __reduce_max_sync(kFull, hi);
-            return;
-        }
+        } else {
 #pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            lo = min(lo, __shfl_xor_sync(kFull, lo, o));
-            hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+            for (int o = G / 2; o > 0; o >>= 1) {
+                lo = min(lo, __shfl_xor_sync(kFull, lo, o));
+                hi = max(hi, __shfl_xor_sync(kFull, hi, o));
+            }
         }
     }
     __device__ bool group_any(bool x) const { return (__ballot_sync(kFull, x) & gmask) != 0; }
@@ -211,13 +236,12 @@ struct Counters {
 // order positions q0 + g (those < qend).  All lanes must call this together.
 // ADAPT: WFA-adaptive pruning and the source-following traceback (a kernel of its own, so the exact
 // algorithm carries none of its registers).
-// group sizes whose launches copy each pair's sequences to shared memory for the extend
-__host__ __device__ constexpr bool wfa_staged(int G) { return G <= 16; }
-
-template <int G, bool ADAPT>
+// STAGE: each group first copies its pair's packed read and target into its slot of s_seq (the launch gives
+// every group a slot of 2 * seq_slot_words words) and the extend reads the copies.
+template <int G, bool ADAPT, bool STAGE>
 __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
                              Counters& st) {
-    constexpr bool kStaged = wfa_staged(G);
+    static_assert(!STAGE || G <= 32, "sequence staging is per group of a warp");
     const Group<G> grp(lane);
     const int g = grp.index(lane), gl = grp.gl;
     const size_t group_bytes =
@@ -233,7 +257,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     int status = kIdle;
     uint32_t pi = 0;
     int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0;
-    const uint64_t *Pw = nullptr, *Tw = nullptr;   // what the extend reads: global memory or the group's copy
+    const uint64_t *Pw = nullptr, *Tw = nullptr;
     uint32_t nwP = 0, nwT = 0;
     if (q < qend && a.retry_only && a.O.flags[a.order ? a.order[q] : q] != AIM_F_STEP_CAP) {
         // second pass: this pair already has its result
@@ -261,20 +285,21 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         if (gl == 0) st.pairs += 1;
     }
 
-    // the group's copy of its pair in shared memory, one spare word after each sequence (launches whose
-    // copies fit; the extend then reads them at shared-memory latency)
-    if (kStaged && a.seq_slot_words) {
-        extern __shared__ uint64_t s_seq[];
-        const uint32_t slot = G > 32 ? 0u : (threadIdx.x >> 5) * (uint32_t)(32 / G) + (uint32_t)g;
-        uint64_t* sP = s_seq + (size_t)slot * 2 * a.seq_slot_words;
-        uint64_t* sT = sP + a.seq_slot_words;
+    // the extend's view of the pair: with STAGE, the group's copy in shared memory (a spare zero word after
+    // each sequence), read at shared-memory latency
+    PairSeqs<STAGE> seqs;
+    if constexpr (STAGE) {
+        const uint32_t slot = (threadIdx.x >> 5) * (uint32_t)(32 / G) + (uint32_t)g;
+        seqs.offP = slot * 2 * a.seq_slot_words;
+        seqs.offT = seqs.offP + a.seq_slot_words;
         if (status == kRun) {
-            for (uint32_t j = (uint32_t)gl; j < nwP; j += (uint32_t)G) sP[j] = __ldg(Pw + j);
-            for (uint32_t j = (uint32_t)gl; j < nwT; j += (uint32_t)G) sT[j] = __ldg(Tw + j);
-            if (gl == 0) { sP[nwP] = 0; sT[nwT] = 0; }
-            Pw = sP; Tw = sT;
+            for (uint32_t j = (uint32_t)gl; j < nwP; j += (uint32_t)G) s_seq[seqs.offP + j] = __ldg(Pw + j);
+            for (uint32_t j = (uint32_t)gl; j < nwT; j += (uint32_t)G) s_seq[seqs.offT + j] = __ldg(Tw + j);
+            if (gl == 0) { s_seq[seqs.offP + nwP] = 0; s_seq[seqs.offT + nwT] = 0; }
         }
         grp.sync();
+    } else {
+        seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
     }
 
     // score 0: diagonal 0 only
@@ -282,7 +307,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     int found0 = 0;
     if (status == kRun && gl == 0) {
         uint32_t w0 = 0;
-        const int m0 = extend<kStaged>(Pw, nwP, n, Tw, nwT, m, 0, 0, w0);
+        const int m0 = extend<STAGE>(seqs, n, m, 0, 0, w0);
         st.windows += w0;
         ++st.cells;
         hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
@@ -318,6 +343,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
         uint32_t n_cells = 0, n_windows = 0;
+        int dmin = 1 << 30, dmax = -(1 << 30);   // WFA-adaptive: distances of the new entries to the end cell
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
             if (run && k <= hi) {
@@ -330,12 +356,17 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 mis = mis >= 0 ? mis + 1 : kNeg16;
                 if (mis > m || mis - k > n) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
-                const int mv = f0 >= 0 ? extend<kStaged>(Pw, nwP, n, Tw, nwT, m, k, f0, n_windows) : kNeg16;
+                const int mv = f0 >= 0 ? extend<STAGE>(seqs, n, m, k, f0, n_windows) : kNeg16;
                 ++n_cells;
                 *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
                     (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
                 hit |= (k == kend && mv >= m);
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
+                if (ADAPT && mv >= 0) {
+                    const int dist = max(n - (mv - k), m - mv);
+                    dmin = min(dmin, dist);
+                    dmax = max(dmax, dist);
+                }
             }
         }
         st.cells += n_cells;
@@ -344,30 +375,27 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         const bool group_hit = grp.group_any(hit);
         if constexpr (ADAPT) {
             // WFA-adaptive: once the wavefront spans at least adapt_min_len diagonals, drop outer diagonals
-            // whose distance to the end cell, max(n - v, m - h), exceeds the smallest by more than adapt_max_dist
-            const bool prune = run && !group_hit && vlo <= vhi && vhi - vlo + 1 >= a.adapt_min_len;
-            int dmin = 1 << 30, dummy = -(1 << 30);
-            for (int it = 0; it < iters; ++it) {
-                const int k = lo + gl + it * G;
-                if (prune && k >= vlo && k <= vhi) {
-                    const int h = hist[(size_t)(base + k) * kEntryElems];
-                    if (h >= 0) dmin = min(dmin, max(n - (h - k), m - h));
-                }
-            }
-            grp.min_max(dmin, dummy);
-            int klo = 1 << 30, khi = -(1 << 30);
-            for (int it = 0; it < iters; ++it) {
-                const int k = lo + gl + it * G;
-                if (prune && k >= vlo && k <= vhi) {
-                    const int h = hist[(size_t)(base + k) * kEntryElems];
-                    if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
-                        klo = min(klo, k);
-                        khi = max(khi, k);
+            // whose distance to the end cell, max(n - v, m - h), exceeds the smallest by more than
+            // adapt_max_dist.  The loop above gave each lane the smallest and largest distance of its
+            // entries; the pass over the wavefront runs only where some entry is that far out.
+            grp.min_max(dmin, dmax);
+            const bool prune = run && !group_hit && vlo <= vhi && vhi - vlo + 1 >= a.adapt_min_len &&
+                               dmax - dmin > a.adapt_max_dist;
+            if (grp.any_running(prune)) {
+                int klo = 1 << 30, khi = -(1 << 30);
+                for (int it = 0; it < iters; ++it) {
+                    const int k = lo + gl + it * G;
+                    if (prune && k >= vlo && k <= vhi) {
+                        const int h = hist[(size_t)(base + k) * kEntryElems];
+                        if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
+                            klo = min(klo, k);
+                            khi = max(khi, k);
+                        }
                     }
                 }
+                grp.min_max(klo, khi);
+                if (prune) { vlo = klo; vhi = khi; }
             }
-            grp.min_max(klo, khi);
-            if (prune) { vlo = klo; vhi = khi; }
         }
         if (run) {
             if (gl == 0) {
@@ -431,8 +459,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     if (!ADAPT && status == kDone && gl == 0) {
         const int* __restrict__ cmeta = meta;
         const int16_t* __restrict__ chist = hist;
-        const uint64_t* Pg = read_words(a.P, pi);     // the pair in global memory (Pw, Tw may be shared copies)
+        const uint64_t* Pg = read_words(a.P, pi);     // the pair in global memory
         const uint64_t* Tg = target_words(a.P, pi);
+        const uint32_t gwP = (uint32_t)(n + 31) >> 5, gwT = (uint32_t)(m + 31) >> 5;
         RunWriter wr;
         wr.init(staged, a.runs_cap);
         int v = n, h = m, cM = final_s, cI = final_s, cD = final_s;
@@ -460,7 +489,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
                 wr.put(kOpDel, 1);
             } else if (match && vM >= h - 1) {
                 const int c = cM;
-                int run = match_run_back(Pg, nwP, v, Tg, nwT, h);
+                int run = match_run_back(Pg, gwP, v, Tg, gwT, h);
                 if (run > h - stop) run = h - stop;
                 if (run < 1) { ok = false; break; }
                 v -= run; h -= run;
@@ -498,7 +527,7 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
     __syncwarp();
 }
 
-template <int G, bool ADAPT>
+template <int G, bool ADAPT, bool STAGE>
 __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
@@ -512,7 +541,7 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
             const uint32_t pos = s_pos;
             __syncthreads();
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G, ADAPT>(a, block_slot, begin + pos, end, lane, st);
+            align_groups<G, ADAPT, false>(a, block_slot, begin + pos, end, lane, st);
         }
     } else {
         constexpr int P = 32 / G;
@@ -521,7 +550,7 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
             if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
             pos = __shfl_sync(kFull, pos, 0);
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G, ADAPT>(a, warp_slot, begin + pos, end, lane, st);
+            align_groups<G, ADAPT, STAGE>(a, warp_slot, begin + pos, end, lane, st);
         }
     }
 }
@@ -534,7 +563,8 @@ constexpr int wfa_min_blocks() { return (G == 32 && !ADAPT) ? 3 : 4; }
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
 // kernel with every variant spilled about 1 KB per thread and ran 14 % slower).
-template <int G, bool ADAPT>
+// STAGE (groups up to 16 lanes): the launch gives each group a shared-memory slot for its pair's sequences.
+template <int G, bool ADAPT, bool STAGE>
 __global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT>())) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -543,30 +573,33 @@ __global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT>())) wfa_kernel(
     Counters st{0, 0, 0};
     if (a.nbuckets == 1) {
         // one queue range (plain calls, and the batched form's groups): measured 7 % faster than the loop below
-        run_bucket<G, ADAPT>(a, 0, warp_slot, lane, st);
+        run_bucket<G, ADAPT, STAGE>(a, 0, warp_slot, lane, st);
     } else {
         for (int b = 0; b < a.nbuckets; ++b)
-            if ((a.group[b] > 32 ? 256 : a.group[b]) == G) run_bucket<G, ADAPT>(a, b, warp_slot, lane, st);
+            if ((a.group[b] > 32 ? 256 : a.group[b]) == G) run_bucket<G, ADAPT, STAGE>(a, b, warp_slot, lane, st);
     }
     warp_stat_add(a.O.stats, 0, st.cells, lane);
     warp_stat_add(a.O.stats, 1, st.windows, lane);
     warp_stat_add(a.O.stats, 3, st.pairs, lane);
 }
 
-template <bool ADAPT>
+template <bool ADAPT, bool STAGE>
 void (*kernel_for(int G))(WfaArgs) {
     switch (G) {
-        case 1: return wfa_kernel<1, ADAPT>;
-        case 2: return wfa_kernel<2, ADAPT>;
-        case 4: return wfa_kernel<4, ADAPT>;
-        case 8: return wfa_kernel<8, ADAPT>;
-        case 16: return wfa_kernel<16, ADAPT>;
-        case 32: return wfa_kernel<32, ADAPT>;
-        default: return wfa_kernel<256, ADAPT>;
+        case 1: return wfa_kernel<1, ADAPT, STAGE>;
+        case 2: return wfa_kernel<2, ADAPT, STAGE>;
+        case 4: return wfa_kernel<4, ADAPT, STAGE>;
+        case 8: return wfa_kernel<8, ADAPT, STAGE>;
+        case 16: return wfa_kernel<16, ADAPT, STAGE>;
+        case 32: return wfa_kernel<32, ADAPT, false>;
+        default: return wfa_kernel<256, ADAPT, false>;
     }
 }
 
-// shared memory per block for the pairs' sequence copies; above it the extend reads global memory
+// Groups of up to 16 lanes (many pairs per SM) stage their pairs' sequences in shared memory when a block's
+// copies fit in kStageBytes; groups of 32 lanes and whole blocks (one long pair per warp or block) gained
+// nothing from it and read global memory.
+constexpr int kStageMaxGroup = 16;
 constexpr size_t kStageBytes = 24 << 10;
 
 int gcd_i(int a, int b) {
@@ -666,13 +699,13 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         for (int i = 0; i < nseen; ++i) dup |= seen[i] == G;
         if (dup) continue;
         seen[nseen++] = G;
-        void (*kernel)(WfaArgs) = adapt ? kernel_for<true>(G) : kernel_for<false>(G);
-        // sequence copies in shared memory when a block's fit in kStageBytes
+        // sequence copies in shared memory when the group size takes them and a block's fit in kStageBytes
         const size_t slot_words = ((size_t)P.max_length + 31) / 32 + 1;
-        const size_t groups_per_block = G > 32 ? 1 : (size_t)8 * (32 / G);
-        size_t smem = groups_per_block * 2 * slot_words * sizeof(uint64_t);
-        if (!wfa_staged(G) || smem > kStageBytes) smem = 0;
+        size_t smem = (size_t)8 * (32 / std::min(G, 32)) * 2 * slot_words * sizeof(uint64_t);
+        if (G > kStageMaxGroup || smem > kStageBytes) smem = 0;
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
+        void (*kernel)(WfaArgs) = adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
+                                        : (smem ? kernel_for<false, true>(G) : kernel_for<false, false>(G));
         int bps = 0;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, smem);
         if (err != cudaSuccess) return err;
