@@ -145,6 +145,8 @@ struct WfaArgs {
     OutView O;
     uint8_t* scratch;
     size_t warp_bytes;         // scratch per warp; a warp of G-lane groups gives each group warp_bytes / (32/G)
+    size_t pair_bytes;         // scratch one pair of a G-lane group may need (G <= 32; the rest of the group's
+                               // share holds finished pairs awaiting their traceback)
     size_t meta_bytes, runs_bytes;
     uint32_t runs_cap;
     uint32_t nwarps;

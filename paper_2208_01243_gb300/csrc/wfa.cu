@@ -232,25 +232,27 @@ struct Counters {
     unsigned long long cells, windows, pairs;
 };
 
-// One step of the warp's work: groups g = 0 .. 32/G - 1 align the pairs at
-// order positions q0 + g (those < qend).  All lanes must call this together.
-// ADAPT: WFA-adaptive pruning and the source-following traceback (a kernel of its own, so the exact
-// algorithm carries none of its registers).
+// Result of a pair's forward pass: its status, the score it ended at, the history entries it used.
+struct Forward {
+    int status, final_s, top;
+    uint32_t pi;
+};
+
+// Forward pass of one step of the warp's work: groups g = 0 .. 32/G - 1 take the pairs at order positions
+// q0 + g (those < qend), each in its own region of region_bytes (meta records, run staging, history).  All
+// lanes must call this together.  The traceback runs later, from the region as this leaves it.
+// ADAPT: WFA-adaptive pruning (a kernel of its own, so the exact algorithm carries none of its registers).
 // STAGE: each group first copies its pair's packed read and target into its slot of s_seq (the launch gives
 // every group a slot of 2 * seq_slot_words words) and the extend reads the copies.
 template <int G, bool ADAPT, bool STAGE>
-__device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, uint32_t qend, uint32_t lane,
-                             Counters& st) {
+__device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* region, size_t region_bytes, uint32_t q0,
+                                                uint32_t qend, uint32_t lane, Counters& st) {
     static_assert(!STAGE || G <= 32, "sequence staging is per group of a warp");
     const Group<G> grp(lane);
     const int g = grp.index(lane), gl = grp.gl;
-    const size_t group_bytes =
-        G > 32 ? a.warp_bytes * (size_t)(G / 32) : (a.warp_bytes / (size_t)(32 / (G > 32 ? 32 : G))) & ~(size_t)15;
-    uint8_t* slot = warp_slot + (size_t)g * group_bytes;
-    int* meta = reinterpret_cast<int*>(slot);
-    uint32_t* staged = reinterpret_cast<uint32_t*>(slot + a.meta_bytes);
-    int16_t* hist = reinterpret_cast<int16_t*>(slot + a.meta_bytes + a.runs_bytes);
-    const size_t hist_cap = (group_bytes - a.meta_bytes - a.runs_bytes) / sizeof(int16_t);
+    int* meta = reinterpret_cast<int*>(region);
+    int16_t* hist = reinterpret_cast<int16_t*>(region + a.meta_bytes + a.runs_bytes);
+    const size_t hist_cap = (region_bytes - a.meta_bytes - a.runs_bytes) / sizeof(int16_t);
     const int X = a.X, OE = a.OE, E = a.E;
 
     const uint32_t q = q0 + (uint32_t)g;
@@ -408,10 +410,22 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         grp.sync();
     }
 
-    // traceback on each group's first lane
+    return Forward{status, final_s, top, pi};
+}
+
+// Traceback of one finished pair by one lane, from its region as the forward pass left it.  Returns the
+// number of runs, staged end-first after the meta records; ok turns false if a step finds no source (not
+// expected) or the runs overflow the staging area.
+template <bool ADAPT>
+__device__ uint32_t traceback(const WfaArgs& a, uint8_t* region, uint32_t pi, int final_s, bool& ok) {
+    const int* meta = reinterpret_cast<const int*>(region);
+    uint32_t* staged = reinterpret_cast<uint32_t*>(region + a.meta_bytes);
+    const int16_t* hist = reinterpret_cast<const int16_t*>(region + a.meta_bytes + a.runs_bytes);
+    const int n = (int)a.P.read_len[pi], m = (int)a.P.target_len[pi];
+    const int X = a.X, OE = a.OE, E = a.E;
     uint32_t nruns = 0;
-    bool ok = true;
-    if (ADAPT && status == kDone && gl == 0) {
+    if constexpr (ADAPT) {
+        const int kend = m - n;
         // WFA-adaptive: follow the sources.  State M at offset h of (c, k): the matches run back to f0, whose
         // source is the mismatch candidate, then I, then D; state I (value h): an extension I[c-E, k+1] == h
         // before an opening M[c-OE, k+1] == h; state D likewise with D[c-E, k-1] + 1 and M[c-OE, k-1] + 1.
@@ -453,10 +467,9 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         wr.finish();
         nruns = wr.n;
         ok = ok && wr.n <= wr.cap;
-    }
-    // canonical traceback; every step issues the loads of all four tight tests at once (two memory round
-    // trips per step instead of a chain of dependent ones)
-    if (!ADAPT && status == kDone && gl == 0) {
+    } else {
+        // canonical traceback; every step issues the loads of all four tight tests at once (two memory round
+        // trips per step instead of a chain of dependent ones)
         const int* __restrict__ cmeta = meta;
         const int16_t* __restrict__ chist = hist;
         const uint64_t* Pg = read_words(a.P, pi);     // the pair in global memory
@@ -504,61 +517,143 @@ __device__ void align_groups(const WfaArgs& a, uint8_t* warp_slot, uint32_t q0, 
         nruns = wr.n;
         ok = ok && wr.n <= wr.cap;
     }
-    grp.sync();
-    nruns = (uint32_t)grp.bcast((int)nruns);
-    ok = grp.bcast(ok ? 1 : 0) != 0;
-    if (status == kDone) {
-        const int32_t score = final_s * a.g;
-        uint8_t flags = ok ? 0 : AIM_F_STEP_CAP;
-        if (ok && a.O.cigars && a.O.cigar_off) {
-            const uint64_t off = a.O.cigar_off[pi];
-            const uint64_t cap = a.O.cigar_off[pi + 1] - off;
-            if (nruns <= cap) {
-                for (uint32_t j = (uint32_t)gl; j < nruns; j += G) a.O.cigars[off + j] = staged[nruns - 1 - j];
-            } else {
-                flags |= AIM_F_CIGAR_OVERFLOW;
-            }
+    return nruns;
+}
+
+// Result of a finished pair: score, flags, run count, and its runs (staged end-first) copied start-first by
+// lanes gl, gl + G, ... of its group; every lane of the group calls this with the same values.
+__device__ __forceinline__ void emit_done(const WfaArgs& a, uint32_t pi, int final_s, uint32_t nruns, bool ok,
+                                          const uint32_t* staged, int gl, int G) {
+    const int32_t score = final_s * a.g;
+    uint8_t flags = ok ? 0 : AIM_F_STEP_CAP;
+    if (ok && a.O.cigars && a.O.cigar_off) {
+        const uint64_t off = a.O.cigar_off[pi];
+        const uint64_t cap = a.O.cigar_off[pi + 1] - off;
+        if (nruns <= cap) {
+            for (uint32_t j = (uint32_t)gl; j < nruns; j += (uint32_t)G) a.O.cigars[off + j] = staged[nruns - 1 - j];
+        } else {
+            flags |= AIM_F_CIGAR_OVERFLOW;
         }
-        if (gl == 0) write_header(a.O, pi, ok ? score : -1, flags, nruns);
-    } else if (status != kIdle && gl == 0) {
-        const uint8_t f = status == kBad ? AIM_F_BAD_PAIR : status == kRejected ? AIM_F_REJECTED : AIM_F_STEP_CAP;
-        write_header(a.O, pi, -1, f, 0);
+    }
+    if (gl == 0) write_header(a.O, pi, ok ? score : -1, flags, nruns);
+}
+
+// One lane: result of a pair that ended without an alignment.
+__device__ __forceinline__ void emit_failed(const WfaArgs& a, uint32_t pi, int status) {
+    const uint8_t f = status == kBad ? AIM_F_BAD_PAIR : status == kRejected ? AIM_F_REJECTED : AIM_F_STEP_CAP;
+    write_header(a.O, pi, -1, f, 0);
+}
+
+// finished pairs awaiting their traceback: G records per group, 32 per warp (pair, final score, region
+// offset in 16-byte units)
+__shared__ int4 s_pend[256];
+
+// Whole warp: lane gl of each group traces back the group's pending pair gl (so up to 32 tracebacks run side
+// by side instead of one per group), then the group writes each pair's result.
+template <int G, bool ADAPT>
+__device__ __forceinline__ void finish_pending(const WfaArgs& a, const Group<G>& grp, uint8_t* arena,
+                                               const int4* pend, int npend) {
+    __syncwarp();
+    const int gl = grp.gl;
+    uint32_t pi = 0, nruns = 0, off = 0;
+    int final_s = 0;
+    bool ok = true;
+    if (gl < npend) {
+        const int4 r = pend[gl];
+        pi = (uint32_t)r.x; final_s = r.y; off = (uint32_t)r.z;
+        nruns = traceback<ADAPT>(a, arena + ((size_t)off << 4), pi, final_s, ok);
+    }
+    __syncwarp();
+    for (int j = 0; j < G; ++j) {
+        const int src = grp.leader + j;
+        const uint32_t pj = __shfl_sync(kFull, pi, src), nj = __shfl_sync(kFull, nruns, src);
+        const uint32_t oj = __shfl_sync(kFull, off, src);
+        const int fj = __shfl_sync(kFull, final_s, src);
+        const bool okj = __shfl_sync(kFull, ok ? 1 : 0, src) != 0;
+        if (j < npend)
+            emit_done(a, pj, fj, nj, okj, reinterpret_cast<const uint32_t*>(arena + ((size_t)oj << 4) + a.meta_bytes),
+                      gl, G);
     }
     __syncwarp();
 }
 
+// Drains bucket b.  Groups of up to 32 lanes defer tracebacks: a group keeps finishing pairs in fresh parts
+// of its arena (its share of the warp's scratch) and traces them back G at a time, once it holds G of them,
+// once its arena has less room left than one pair may need (pair_bytes), or when the bucket is drained.
+// A pair's forward pass therefore always has at least pair_bytes, as without deferral.
 template <int G, bool ADAPT, bool STAGE>
 __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     if constexpr (G > 32) {
-        // the whole block takes one pair at a time; its warps' scratch regions form the pair's slot
+        // the whole block takes one pair at a time; its warps' scratch regions form the pair's region, and
+        // thread 0 traces it back
         __shared__ uint32_t s_pos;
-        uint8_t* block_slot = a.scratch + (size_t)blockIdx.x * (blockDim.x / 32) * a.warp_bytes;
+        const Group<G> grp(lane);
+        const size_t block_bytes = (blockDim.x / 32) * a.warp_bytes;
+        uint8_t* block_slot = a.scratch + (size_t)blockIdx.x * block_bytes;
         for (;;) {
             if (threadIdx.x == 0) s_pos = atomicAdd(a.counters + b, 1u);
             __syncthreads();
             const uint32_t pos = s_pos;
             __syncthreads();
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G, ADAPT, false>(a, block_slot, begin + pos, end, lane, st);
+            const Forward f = forward_pair<G, ADAPT, false>(a, block_slot, block_bytes, begin + pos, end, lane, st);
+            uint32_t nruns = 0;
+            bool ok = true;
+            if (f.status == kDone && threadIdx.x == 0) nruns = traceback<ADAPT>(a, block_slot, f.pi, f.final_s, ok);
+            nruns = (uint32_t)grp.bcast((int)nruns);
+            ok = grp.bcast(ok ? 1 : 0) != 0;
+            if (f.status == kDone)
+                emit_done(a, f.pi, f.final_s, nruns, ok, reinterpret_cast<const uint32_t*>(block_slot + a.meta_bytes),
+                          (int)threadIdx.x, G);
+            else if (f.status != kIdle && threadIdx.x == 0)
+                emit_failed(a, f.pi, f.status);
+            __syncthreads();
         }
     } else {
         constexpr int P = 32 / G;
+        const Group<G> grp(lane);
+        const int gl = grp.gl;
+        // the group's arena and its pending records (recomputed where needed, to keep registers for the
+        // forward pass); used16: bytes of the arena taken by pending pairs, in 16-byte units
+        const uint32_t arena16 = (uint32_t)((a.warp_bytes / P) >> 4);
+        const uint32_t pair16 = (uint32_t)((a.pair_bytes + 15) >> 4);
+        uint32_t used16 = 0;
+        int npend = 0;
         for (;;) {
             uint32_t pos = 0;
             if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
             pos = __shfl_sync(kFull, pos, 0);
             if (pos >= end - begin || end <= begin) break;
-            align_groups<G, ADAPT, STAGE>(a, warp_slot, begin + pos, end, lane, st);
+            if (__any_sync(kFull, npend == G || arena16 - used16 < pair16)) {
+                finish_pending<G, ADAPT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
+                                         s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
+                used16 = 0;
+                npend = 0;
+            }
+            uint8_t* region = warp_slot + (((size_t)grp.index(lane) * arena16 + used16) << 4);
+            const Forward f =
+                forward_pair<G, ADAPT, STAGE>(a, region, (size_t)(arena16 - used16) << 4, begin + pos, end, lane, st);
+            if (f.status == kDone) {
+                if (gl == 0)
+                    s_pend[(threadIdx.x & ~31u) + grp.index(lane) * G + npend] = make_int4((int)f.pi, f.final_s, (int)used16, 0);
+                ++npend;
+                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryElems * sizeof(int16_t) + 15) >> 4);
+            } else if (f.status != kIdle && gl == 0) {
+                emit_failed(a, f.pi, f.status);
+            }
         }
+        finish_pending<G, ADAPT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
+                                 s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
     }
 }
 
-// blocks of 256 per SM the register budget must allow: 4 (64 registers), except 3 (85 registers) for the exact
-// kernel with 32 lanes per pair, which measured 2.5 % faster that way on long pairs (the others were slower)
+// blocks of 256 per SM the register budget must allow: 4 (64 registers), except 3 (85 registers) for the
+// kernels with 32 lanes per pair: the exact one measured 2.5 % faster that way on long pairs (the others were
+// slower), and the adaptive one holds its deferred tracebacks without spilling
 template <int G, bool ADAPT>
-constexpr int wfa_min_blocks() { return (G == 32 && !ADAPT) ? 3 : 4; }
+constexpr int wfa_min_blocks() { return G == 32 ? 3 : 4; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
@@ -720,6 +815,11 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         warps = warps / 8 * 8;
         if (warps == 0) { *warps_used = 0; return cudaSuccess; }   // not one block's scratch fits: caller reports it
         a.nwarps = (uint32_t)warps;
+        // groups of up to 32 lanes spread the whole scratch over the launch's warps: what a pair may need
+        // stays pair_bytes, and the rest holds finished pairs until their tracebacks run side by side
+        a.warp_bytes = warp_bytes;
+        a.pair_bytes = (warp_bytes / (size_t)(32 / std::min(G, 32))) & ~(size_t)15;
+        if (G <= 32) a.warp_bytes = std::max(warp_bytes, (scratch_bytes / warps) & ~(size_t)15);
         kernel<<<(unsigned)(warps / 8), 256, smem, st>>>(a);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
