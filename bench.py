@@ -71,7 +71,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--pairs", type=int, default=0, help="override the workload's pair count (0: as defined)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workspace-gb", type=float, default=8.0, help="aligner context workspace (GiB)")
+    ap.add_argument("--workspace-gb", type=float, default=32.0,
+                    help="aligner context workspace and batched-plan scratch (GiB)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per pair for the plain WFA calls (0: library choice)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
@@ -592,14 +593,17 @@ def run_ours(args, w, algo):
         line["baseline_note"] = (f"Table 3 (WFA-adaptive, {t3[0][0]} bp, {t3[0][1]} % edits): UPMEM {ref:.4g} "
                                  "alignments/s on 2560 DPUs with host transfer included (compare e2e); real reads "
                                  "there, seeded synthetic pairs of the same shape here")
+    # the serving run has its own context and budgets: free this run's plan and workspace first
+    if plan is not None:
+        aim.aim_batch_destroy(plan)
+    al.close()
+    del d, out
+    torch.cuda.empty_cache()
     if batched and not args.no_serve and world == 1:
         line["serving"] = serving(args, local)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, algo)
     print(json.dumps(line))
-    if plan is not None:
-        aim.aim_batch_destroy(plan)
-    al.close()
     return 0
 
 

@@ -652,15 +652,15 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
 // blocks of 256 per SM the register budget must allow: 4 (64 registers), except 3 (85 registers) for the
 // kernels with 32 lanes per pair: the exact one measured 2.5 % faster that way on long pairs (the others were
 // slower), and the adaptive one holds its deferred tracebacks without spilling
-template <int G, bool ADAPT>
-constexpr int wfa_min_blocks() { return G == 32 ? 3 : 4; }
+template <int G, bool ADAPT, bool STAGE>
+constexpr int wfa_min_blocks() { return (G == 32 || STAGE) ? 3 : 4; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
 // kernel with every variant spilled about 1 KB per thread and ran 14 % slower).
 // STAGE (groups up to 16 lanes): the launch gives each group a shared-memory slot for its pair's sequences.
 template <int G, bool ADAPT, bool STAGE>
-__global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT>())) wfa_kernel(WfaArgs a) {
+__global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT, STAGE>())) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
