@@ -234,7 +234,7 @@ def cpu_baseline(w, algo):
     cores = os.cpu_count() or 1
     sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000, "wfa_adaptive": 200_000, "genasm": 400_000}[algo]
     if w is gen.WFA_UNEVEN:
-        sample = 10_000
+        sample = 40_000   # full-matrix DP over 100-1000 bp pairs: about 25 s of CPU work on 16 cores
     if algo in ("wfa_adaptive", "genasm"):
         sample = max(500, min(sample, 40_000_000 // max(w.len_max, 1)))
     p = gen.generate(w, sample)
