@@ -661,7 +661,8 @@ def serving(args, local):
         rate = frac * peak / mean_req                          # requests per second
         count = max(20, int(rate * args.serve_seconds))
         arr, sz = gen.arrivals(600 + int(frac * 100), count, rate)
-        arr = arr * (float(sz.mean()) / mean_req)              # offered pairs/s = frac * peak for this sample's sizes
+        if count > 1:   # Poisson gaps and sizes as drawn, the time axis scaled so the offered rate is exactly frac * peak
+            arr = arr * (float(sz.sum()) / (frac * peak) / float(arr[-1]))
         lat, pairs, wall = run(arr, sz)
         levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": float(sz.sum()) / float(arr[-1]) if count > 1 else
                                          frac * peak, "requests": count,
