@@ -45,6 +45,9 @@
 // A run of M's continues while the bases match and neither I~[c,k] nor
 // D~[c,k] reaches the current offset; its length comes from a backward
 // comparison of 32-base windows (XOR, count trailing zero base pairs).
+// A traceback is one lane's serial walk, so groups of up to 32 lanes defer
+// it: a group finishes up to G pairs in fresh parts of its scratch arena and
+// then traces them back side by side, lane j taking the j-th.
 //
 // Work distribution: a launch is compiled for one group size G and walks the
 // buckets of that size (each a range of a pair order array); warps take 32/G
