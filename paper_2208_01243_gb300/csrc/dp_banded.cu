@@ -26,8 +26,11 @@
 // touches one of any two consecutive anti-diagonals, so once every cell of
 // two consecutive anti-diagonals exceeds the limit the pair is rejected.
 //
-// Trace bits are stored per warp as rows of anti-diagonals, entry (d, q/2),
-// so the 32 lanes of a step write one contiguous row.
+// Trace bits are stored per pair as rows of anti-diagonals, entry (d, q/2),
+// so the 32 lanes of a step write one contiguous row.  A warp keeps up to 32
+// pair slots: finished pairs wait in them, and once they are all taken (or
+// the queue is drained) lane j traces back slot j, so the serial tracebacks
+// run side by side.
 #include <type_traits>
 #include <utility>
 
@@ -43,8 +46,9 @@ struct DpArgs {
     OutView O;
     int band;
     uint8_t* scratch;
-    size_t slot_bytes;
+    size_t slot_bytes;       // one pair's trace rows and run staging
     size_t trace_bytes;      // offset of the run staging area inside a slot
+    uint32_t defer;          // slots per warp: finished pairs wait in them and are traced back side by side
     uint32_t runs_cap;
     uint32_t nwarps;
     uint32_t* counter;
@@ -53,6 +57,77 @@ struct DpArgs {
 __device__ __forceinline__ int32_t cap_inf(int32_t v) { return v > kInf ? kInf : v; }
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
 
+// finished pairs awaiting their traceback, one record per slot of a warp: pair, score, tight end states
+__shared__ int4 s_dp_pend[256];
+
+// Canonical traceback of one finished pair by one lane, from its trace rows; returns the number of runs,
+// staged end-first.  ok turns false if a step finds no tight state (not expected) or the runs overflow.
+template <bool UNIT, int R>
+__device__ uint32_t dp_traceback(const DpArgs& a, const uint8_t* slot, uint32_t* staged, uint32_t pi, uint32_t ends,
+                                 bool& ok) {
+    using TB = typename std::conditional<UNIT, uint8_t, uint16_t>::type;
+    constexpr int RW = 32 * R;
+    const TB* trace = reinterpret_cast<const TB*>(slot);
+    const int b = a.band;
+    const uint64_t* Pw = read_words(a.P, pi);
+    const uint64_t* Tw = target_words(a.P, pi);
+    RunWriter w;
+    w.init(staged, a.runs_cap);
+    bool tM = ends & 1u, tI = (ends >> 1) & 1u, tD = (ends >> 2) & 1u;
+    int v = (int)a.P.read_len[pi], h = (int)a.P.target_len[pi];
+    while (v > 0 || h > 0) {
+        const int k = h - v;
+        if (k < -b || k > b) { ok = false; break; }
+        const uint32_t bits = trace[(size_t)(v + h) * RW + ((k + b) >> 1)];
+        if (UNIT) { tM = bits & 1u; tI = (bits >> 1) & 1u; tD = (bits >> 2) & 1u; }
+        const bool match = v > 0 && h > 0 && base_at(Pw, v - 1) == base_at(Tw, h - 1);
+        uint32_t op;
+        if (tM && v > 0 && h > 0 && !match) op = kOpMismatch;
+        else if (tI) op = kOpIns;
+        else if (tD) op = kOpDel;
+        else if (tM && match) op = kOpMatch;
+        else { ok = false; break; }
+        if (!UNIT) {
+            const uint32_t sh = (op == kOpIns) ? 3 : (op == kOpDel) ? 6 : 0;
+            const uint32_t t = bits >> sh;
+            if (op == kOpIns) { tM = t & 1u; tD = (t >> 1) & 1u; tI = (t >> 2) & 1u; }
+            else { tM = t & 1u; tI = (t >> 1) & 1u; tD = (t >> 2) & 1u; }
+        }
+        if (op == kOpMismatch || op == kOpMatch) { --v; --h; }
+        else if (op == kOpIns) { --v; }
+        else { --h; }
+        w.put(op, 1);
+    }
+    w.finish();
+    ok = ok && w.n <= w.cap;
+    return w.n;
+}
+
+// Whole warp: lane j traces back the pair waiting in slot j (so up to 32 tracebacks run side by side), then
+// the warp writes each pair's result.
+template <bool UNIT, int R>
+__device__ __forceinline__ void dp_finish(const DpArgs& a, uint8_t* warp_slots, const int4* pend, uint32_t npend,
+                                          uint32_t lane) {
+    __syncwarp();   // trace rows and records written by every lane are visible
+    uint32_t nruns = 0;
+    bool ok = true;
+    if (lane < npend) {
+        const int4 r = pend[lane];
+        uint8_t* slot = warp_slots + (size_t)lane * a.slot_bytes;
+        nruns = dp_traceback<UNIT, R>(a, slot, reinterpret_cast<uint32_t*>(slot + a.trace_bytes), (uint32_t)r.x,
+                                      (uint32_t)r.z, ok);
+    }
+    __syncwarp();
+    for (uint32_t j = 0; j < npend; ++j) {
+        const int4 r = pend[j];
+        const uint32_t nj = __shfl_sync(kFull, nruns, j);
+        const bool okj = __shfl_sync(kFull, ok ? 1 : 0, j) != 0;
+        const uint32_t* staged = reinterpret_cast<const uint32_t*>(warp_slots + (size_t)j * a.slot_bytes + a.trace_bytes);
+        write_cigar(a.O, (uint32_t)r.x, r.y, staged, nj, okj, lane);
+    }
+    __syncwarp();
+}
+
 template <bool UNIT, int R>
 __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
     using TB = typename std::conditional<UNIT, uint8_t, uint16_t>::type;
@@ -60,9 +135,9 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
-    uint8_t* slot = a.scratch + (size_t)gwarp * a.slot_bytes;
-    TB* trace = reinterpret_cast<TB*>(slot);
-    uint32_t* staged = reinterpret_cast<uint32_t*>(slot + a.trace_bytes);
+    uint8_t* warp_slots = a.scratch + (size_t)gwarp * a.defer * a.slot_bytes;
+    int4* pend = s_dp_pend + (threadIdx.x & ~31u);
+    uint32_t npend = 0;   // finished pairs waiting in slots 0 .. npend-1 (warp-uniform)
     const int b = a.band;
     const int32_t x = UNIT ? 1 : a.c.x;
     const int32_t oe = UNIT ? 1 : a.c.o + a.c.e;
@@ -89,6 +164,7 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
             continue;
         }
         const int32_t limc = lim >= (int64_t)kInf ? kInf - 1 : (int32_t)lim;
+        TB* trace = reinterpret_cast<TB*>(warp_slots + (size_t)npend * a.slot_bytes);
         const uint64_t* Pw = read_words(a.P, pi);
         const uint64_t* Tw = target_words(a.P, pi);
 
@@ -255,47 +331,13 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
             if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
             continue;
         }
-        __syncwarp();   // trace rows written by every lane are visible to lane 0
-        uint32_t nruns = 0;
-        bool ok = true;
-        if (lane == 0) {
-            RunWriter w;
-            w.init(staged, a.runs_cap);
-            bool tM = eM == s, tI = eI == s, tD = eD == s;
-            int v = (int)n, h = (int)m;
-            while (v > 0 || h > 0) {
-                const int k = h - v;
-                if (k < -b || k > b) { ok = false; break; }
-                const uint32_t bits = trace[(size_t)(v + h) * RW + ((k + b) >> 1)];
-                if (UNIT) { tM = bits & 1u; tI = (bits >> 1) & 1u; tD = (bits >> 2) & 1u; }
-                const bool match = v > 0 && h > 0 && base_at(Pw, v - 1) == base_at(Tw, h - 1);
-                uint32_t op;
-                if (tM && v > 0 && h > 0 && !match) op = kOpMismatch;
-                else if (tI) op = kOpIns;
-                else if (tD) op = kOpDel;
-                else if (tM && match) op = kOpMatch;
-                else { ok = false; break; }
-                if (!UNIT) {
-                    const uint32_t sh = (op == kOpIns) ? 3 : (op == kOpDel) ? 6 : 0;
-                    const uint32_t t = bits >> sh;
-                    if (op == kOpIns) { tM = t & 1u; tD = (t >> 1) & 1u; tI = (t >> 2) & 1u; }
-                    else { tM = t & 1u; tI = (t >> 1) & 1u; tD = (t >> 2) & 1u; }
-                }
-                if (op == kOpMismatch || op == kOpMatch) { --v; --h; }
-                else if (op == kOpIns) { --v; }
-                else { --h; }
-                w.put(op, 1);
-            }
-            w.finish();
-            nruns = w.n;
-            ok = ok && w.n <= w.cap;
+        if (lane == 0) pend[npend] = make_int4((int)pi, s, (int)((eM == s) | (eI == s) << 1 | (eD == s) << 2), 0);
+        if (++npend == a.defer) {
+            dp_finish<UNIT, R>(a, warp_slots, pend, npend, lane);
+            npend = 0;
         }
-        __syncwarp();
-        nruns = __shfl_sync(kFull, nruns, 0);
-        ok = __shfl_sync(kFull, ok, 0);
-        write_cigar(a.O, pi, s, staged, nruns, ok, lane);
-        __syncwarp();
     }
+    dp_finish<UNIT, R>(a, warp_slots, pend, npend, lane);
     warp_stat_add(a.O.stats, 2, st_cells, lane);
     warp_stat_add(a.O.stats, 3, st_pairs, lane);
 }
@@ -313,6 +355,9 @@ cudaError_t launch_t(const DpArgs& args0, int num_sms, cudaStream_t st, int* war
     if (warps == 0) { *warps_used = 0; return cudaSuccess; }
     DpArgs a = args0;
     a.nwarps = (uint32_t)warps;
+    // slots per warp: the scratch spread over the launch's warps, up to one per lane
+    const size_t per_warp = scratch_bytes / warps / args0.slot_bytes;
+    a.defer = (uint32_t)(per_warp > 32 ? 32 : per_warp);
     const unsigned blocks = (unsigned)((warps + 7) / 8);
     dp_kernel<UNIT, R><<<blocks, 256, 0, st>>>(a);
     *warps_used = (int)warps;
