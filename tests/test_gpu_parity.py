@@ -59,6 +59,40 @@ def test_gotoh_wfa_250bp_band25_parity_small(aligner, oracle_lib, gen_lib, algo)
     assert_same(dev, orc, what=f"{algo} band 25")
 
 
+@pytest.mark.parametrize("lanes", [4, 32])
+def test_wfa_deferred_tracebacks_any_workspace(oracle_lib, gen_lib, lanes):
+    """Groups defer their tracebacks as far as their share of the scratch allows: one pair per flush when the
+    arena holds one pair's planned need, several when it holds more, up to G, and a last flush when the queue is
+    drained.  30k pairs keep every warp busy with several pairs.  Results never depend on it."""
+    import paper_2208_01243_gb300 as aim
+    w = gen.WFA_150BP
+    p = gen.generate(w, 30_011)
+    orc = oracle_results(p, AFF, limits(w, p))
+    for ws in (16 << 20, 96 << 20, 2 << 30):
+        al = aim.Aligner(0, ws)
+        try:
+            aim.aim_set_wfa_group(al.ctx, lanes)
+            dev = device_results(p, "wfa", AFF, w.max_edits, aligner=al)
+        finally:
+            al.close()
+        assert_same(dev, orc, what=f"wfa lanes={lanes} workspace={ws >> 20} MiB")
+
+
+@pytest.mark.parametrize("algo", ["gotoh", "edit"])
+def test_dp_deferred_tracebacks_any_workspace(oracle_lib, gen_lib, algo):
+    """The banded DP keeps up to 32 finished pairs per warp for side-by-side tracebacks, as many slots as the
+    scratch spread over the warps allows: 1 with 40 MiB, a few with 320 MiB (flushes whenever they fill), many
+    with 4 GiB.  Results never depend on it."""
+    w = gen.GOTOH_WFA_250BP
+    p = gen.generate(w, 20_003)
+    pen = AFF if algo == "gotoh" else oracle.UNIT
+    lim = np.array([oracle.limit_for(pen, 25, unit=algo == "edit")] * len(p), np.int64)
+    orc = oracle_results(p, pen, lim, band=25)
+    for ws in (40 << 20, 320 << 20, 4 << 30):
+        dev = device_results(p, algo, pen, 25, band=25, workspace=ws)
+        assert_same(dev, orc, what=f"{algo} band 25 workspace={ws >> 20} MiB")
+
+
 def test_wfa_uneven_parity_sample(aligner, oracle_lib, gen_lib):
     w = gen.WFA_UNEVEN
     p = gen.generate(w, 1_500)
