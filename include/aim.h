@@ -116,7 +116,10 @@ AIM_API int aim_last_cuda_error(void);
  * (wavefront history, DP trace bits, CIGAR staging) and, for the ASCII entry
  * point, the packed copies of the sequences.  A call that needs more scratch
  * than fits runs fewer pairs at once; it fails with AIM_ERR_NOMEM only when
- * not even one pair's scratch fits.  *out is NULL on failure.
+ * not even one pair's scratch fits.  Scratch beyond what the resident warps
+ * need holds finished pairs whose tracebacks then run side by side (one lane
+ * each), so a larger workspace can be faster; results never depend on it.
+ * *out is NULL on failure.
  */
 AIM_API int aim_create(aim_ctx **out, int device, size_t workspace_bytes);
 
