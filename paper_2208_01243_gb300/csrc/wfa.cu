@@ -589,31 +589,59 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     if constexpr (G > 32) {
-        // the whole block takes one pair at a time; its warps' scratch regions form the pair's region, and
-        // thread 0 traces it back
+        // the whole block takes one pair at a time in its arena (its warps' scratch regions); finished pairs
+        // wait there, up to one per warp, and the first lane of warp w traces back the w-th
+        constexpr int kWarps = G / 32;
         __shared__ uint32_t s_pos;
-        const Group<G> grp(lane);
-        const size_t block_bytes = (blockDim.x / 32) * a.warp_bytes;
+        __shared__ int4 s_bpend[kWarps];   // pair, final score, region offset in 16-byte units
+        __shared__ uint2 s_bres[kWarps];   // run count, traceback ok
+        const size_t block_bytes = (size_t)kWarps * a.warp_bytes;
         uint8_t* block_slot = a.scratch + (size_t)blockIdx.x * block_bytes;
+        const uint32_t arena16 = (uint32_t)(block_bytes >> 4);
+        const uint32_t pair16 = (uint32_t)((a.pair_bytes + 15) >> 4);
+        uint32_t used16 = 0;
+        int npend = 0;
+        auto finish = [&]() {
+            __syncthreads();
+            const int w = (int)(threadIdx.x >> 5);
+            if ((threadIdx.x & 31) == 0 && w < npend) {
+                const int4 r = s_bpend[w];
+                bool ok = true;
+                const uint32_t nr = traceback<ADAPT>(a, block_slot + ((size_t)r.z << 4), (uint32_t)r.x, r.y, ok);
+                s_bres[w] = make_uint2(nr, ok ? 1u : 0u);
+            }
+            __syncthreads();
+            for (int j = 0; j < npend; ++j) {
+                const int4 r = s_bpend[j];
+                const uint2 q = s_bres[j];
+                emit_done(a, (uint32_t)r.x, r.y, q.x, q.y != 0,
+                          reinterpret_cast<const uint32_t*>(block_slot + ((size_t)r.z << 4) + a.meta_bytes),
+                          (int)threadIdx.x, G);
+            }
+            __syncthreads();
+        };
         for (;;) {
             if (threadIdx.x == 0) s_pos = atomicAdd(a.counters + b, 1u);
             __syncthreads();
             const uint32_t pos = s_pos;
             __syncthreads();
             if (pos >= end - begin || end <= begin) break;
-            const Forward f = forward_pair<G, ADAPT, false>(a, block_slot, block_bytes, begin + pos, end, lane, st);
-            uint32_t nruns = 0;
-            bool ok = true;
-            if (f.status == kDone && threadIdx.x == 0) nruns = traceback<ADAPT>(a, block_slot, f.pi, f.final_s, ok);
-            nruns = (uint32_t)grp.bcast((int)nruns);
-            ok = grp.bcast(ok ? 1 : 0) != 0;
-            if (f.status == kDone)
-                emit_done(a, f.pi, f.final_s, nruns, ok, reinterpret_cast<const uint32_t*>(block_slot + a.meta_bytes),
-                          (int)threadIdx.x, G);
-            else if (f.status != kIdle && threadIdx.x == 0)
+            if (npend == kWarps || arena16 - used16 < pair16) {
+                finish();
+                used16 = 0;
+                npend = 0;
+            }
+            const Forward f = forward_pair<G, ADAPT, false>(a, block_slot + ((size_t)used16 << 4),
+                                                            (size_t)(arena16 - used16) << 4, begin + pos, end, lane, st);
+            if (f.status == kDone) {
+                if (threadIdx.x == 0) s_bpend[npend] = make_int4((int)f.pi, f.final_s, (int)used16, 0);
+                ++npend;
+                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryElems * sizeof(int16_t) + 15) >> 4);
+            } else if (f.status != kIdle && threadIdx.x == 0) {
                 emit_failed(a, f.pi, f.status);
-            __syncthreads();
+            }
         }
+        finish();
     } else {
         constexpr int P = 32 / G;
         const Group<G> grp(lane);
@@ -656,7 +684,7 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
 // kernels with 32 lanes per pair: the exact one measured 2.5 % faster that way on long pairs (the others were
 // slower), and the adaptive one holds its deferred tracebacks without spilling
 template <int G, bool ADAPT, bool STAGE>
-constexpr int wfa_min_blocks() { return (G == 32 || STAGE) ? 3 : 4; }
+constexpr int wfa_min_blocks() { return (G >= 32 || STAGE) ? 3 : 4; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
@@ -818,11 +846,10 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         warps = warps / 8 * 8;
         if (warps == 0) { *warps_used = 0; return cudaSuccess; }   // not one block's scratch fits: caller reports it
         a.nwarps = (uint32_t)warps;
-        // groups of up to 32 lanes spread the whole scratch over the launch's warps: what a pair may need
-        // stays pair_bytes, and the rest holds finished pairs until their tracebacks run side by side
-        a.warp_bytes = warp_bytes;
-        a.pair_bytes = (warp_bytes / (size_t)(32 / std::min(G, 32))) & ~(size_t)15;
-        if (G <= 32) a.warp_bytes = std::max(warp_bytes, (scratch_bytes / warps) & ~(size_t)15);
+        // the launch spreads the whole scratch over its warps: what a pair may need stays pair_bytes, and
+        // the rest holds finished pairs until their tracebacks run side by side
+        a.pair_bytes = G > 32 ? warp_bytes * (size_t)(G / 32) : (warp_bytes / (size_t)(32 / G)) & ~(size_t)15;
+        a.warp_bytes = std::max(warp_bytes, (scratch_bytes / warps) & ~(size_t)15);
         kernel<<<(unsigned)(warps / 8), 256, smem, st>>>(a);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
