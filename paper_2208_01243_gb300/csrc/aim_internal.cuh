@@ -151,6 +151,8 @@ struct WfaArgs {
     uint32_t runs_cap;
     uint32_t nwarps;
     uint32_t seq_slot_words;   // words per sequence copy in shared memory (0: the extend reads global memory)
+    uint32_t meta_ring;        // records per group in a shared-memory ring of recent scores (power of 2; 0: none)
+    uint32_t ring_off;         // byte offset of the rings in dynamic shared memory (after the sequence copies)
     const uint32_t* order;     // pair index at each queue position, or null (identity)
     const uint32_t* bounds;    // bucket b covers queue positions [bounds[b], bounds[b+1]); null: one bucket of all
     uint32_t* counters;        // one claim counter per bucket, zero at launch

@@ -69,6 +69,16 @@ struct Wf {
                             // (base + k) * kEntryElems + c (base: first entry, already offset by -lo)
 };
 
+// record of score s: element s & mask of rec (mask -1: the group's records in scratch; R-1: its ring of the
+// last R scores in shared memory)
+__device__ __forceinline__ Wf load_wf(const int4* rec, int s, int mask) {
+    Wf f;
+    if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
+    const int4 q = rec[s & mask];
+    f.lo = q.x; f.cnt = q.y >= q.x ? q.y - q.x + 1 : 0; f.base = q.z; f.w = q.w;
+    return f;
+}
+
 __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     Wf f;
     if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
@@ -307,6 +317,21 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
     }
 
+    // STAGE: the records the next scores read come from a ring of the last meta_ring scores in shared memory,
+    // when the launch gives one (the records in scratch stay for the traceback).  Groups of 32 lanes and whole
+    // blocks read their records from scratch: a ring measured slower there.
+    const int4* src = reinterpret_cast<const int4*>(meta);
+    int4* ring = nullptr;
+    int mask = -1;
+    if constexpr (STAGE) {
+        if (a.meta_ring) {
+            const uint32_t gib = (threadIdx.x >> 5) * (uint32_t)(32 / G) + (uint32_t)g;
+            ring = reinterpret_cast<int4*>(reinterpret_cast<char*>(s_seq) + a.ring_off) + (size_t)gib * a.meta_ring;
+            src = ring;
+            mask = (int)a.meta_ring - 1;
+        }
+    }
+
     // score 0: diagonal 0 only
     int top = 0, final_s = 0;
     int found0 = 0;
@@ -317,6 +342,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         ++st.cells;
         hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
+        if (STAGE && ring) ring[0] = make_int4(0, 0, 0, 1);
         found0 = (kend == 0 && m0 >= m);
     }
     found0 = grp.bcast(found0);
@@ -334,7 +360,11 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         int lo = 0, hi = -1, w = 0;
         Wf fx, fo, fe;
         if (run) {
-            fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+            if constexpr (STAGE) {
+                fx = load_wf(src, s - X, mask); fo = load_wf(src, s - OE, mask); fe = load_wf(src, s - E, mask);
+            } else {
+                fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+            }
             lo = 1 << 30; hi = -(1 << 30);
             if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
             if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
@@ -406,6 +436,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (gl == 0) {
                 const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
                 reinterpret_cast<int4*>(meta)[s] = rec;
+                if (STAGE && ring) ring[s & mask] = rec;
             }
             top += w;
             if (group_hit) { status = kDone; final_s = s; }
@@ -680,11 +711,11 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
     }
 }
 
-// blocks of 256 per SM the register budget must allow: 4 (64 registers), except 3 (85 registers) for the
-// kernels with 32 lanes per pair: the exact one measured 2.5 % faster that way on long pairs (the others were
-// slower), and the adaptive one holds its deferred tracebacks without spilling
+// blocks of 256 per SM the register budget must allow: 3 (80 registers).  At 4 (64 registers) the deferred
+// tracebacks made every instance but the plain 32-lane one spill; the exact 32-lane kernel also measured 2.5 %
+// faster at 3 on long pairs, and whole-block groups 4 % faster.
 template <int G, bool ADAPT, bool STAGE>
-constexpr int wfa_min_blocks() { return (G >= 32 || STAGE) ? 3 : 4; }
+constexpr int wfa_min_blocks() { return 3; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
@@ -832,6 +863,13 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
         void (*kernel)(WfaArgs) = adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
                                         : (smem ? kernel_for<false, true>(G) : kernel_for<false, false>(G));
+        // staged launches: a ring of the last R score records per group, R a power of 2 above the farthest
+        // source (max(X, OE)), after the sequence copies, when a block's rings fit beside them in 48 KB
+        uint32_t R = 1;
+        while (R < (uint32_t)std::max(plan.x, plan.oe) + 1) R <<= 1;
+        const size_t ring_bytes = (G > 32 ? 1 : (size_t)8 * (32 / G)) * R * sizeof(int4);
+        a.meta_ring = 0; a.ring_off = (uint32_t)smem;
+        if (smem && R <= 64 && smem + ring_bytes <= (48u << 10)) { a.meta_ring = R; smem += ring_bytes; }
         int bps = 0;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, smem);
         if (err != cudaSuccess) return err;
