@@ -45,9 +45,10 @@
 // A run of M's continues while the bases match and neither I~[c,k] nor
 // D~[c,k] reaches the current offset; its length comes from a backward
 // comparison of 32-base windows (XOR, count trailing zero base pairs).
-// A traceback is one lane's serial walk, so groups of up to 32 lanes defer
-// it: a group finishes up to G pairs in fresh parts of its scratch arena and
-// then traces them back side by side, lane j taking the j-th.
+// A traceback is one lane's serial walk, so groups defer it: a group of up
+// to 32 lanes finishes up to G pairs in fresh parts of its scratch arena and
+// then traces them back side by side, lane j taking the j-th; a whole block
+// keeps up to one pair per warp, traced back by the warp's first lane.
 //
 // Work distribution: a launch is compiled for one group size G and walks the
 // buckets of that size (each a range of a pair order array); warps take 32/G
@@ -105,7 +106,8 @@ __device__ __forceinline__ uint64_t window_in(const uint64_t* __restrict__ w, ui
     return (hi << sh) | ((lo >> 1) >> (63 - sh));
 }
 
-// copies of the pairs' packed sequences, one slot per group (launches with sequence staging)
+// dynamic shared memory of staged launches: copies of the pairs' packed sequences, one slot per group, then
+// each group's ring of recent score records (at byte offset ring_off)
 extern __shared__ uint64_t s_seq[];
 
 // the same window from a copy at word offset `off` of s_seq, which holds a spare word after the sequence, so
@@ -317,13 +319,14 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
     }
 
-    // STAGE: the records the next scores read come from a ring of the last meta_ring scores in shared memory,
-    // when the launch gives one (the records in scratch stay for the traceback).  Groups of 32 lanes and whole
-    // blocks read their records from scratch: a ring measured slower there.
+    // exact staged launches: the records the next scores read come from a ring of the last meta_ring scores in
+    // shared memory, when the launch gives one (the records in scratch stay for the traceback).  Groups of 32
+    // lanes, whole blocks and the adaptive kernels read their records from scratch: a ring measured slower there.
+    constexpr bool kRing = STAGE && !ADAPT;
     const int4* src = reinterpret_cast<const int4*>(meta);
     int4* ring = nullptr;
     int mask = -1;
-    if constexpr (STAGE) {
+    if constexpr (kRing) {
         if (a.meta_ring) {
             const uint32_t gib = (threadIdx.x >> 5) * (uint32_t)(32 / G) + (uint32_t)g;
             ring = reinterpret_cast<int4*>(reinterpret_cast<char*>(s_seq) + a.ring_off) + (size_t)gib * a.meta_ring;
@@ -342,7 +345,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         ++st.cells;
         hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
-        if (STAGE && ring) ring[0] = make_int4(0, 0, 0, 1);
+        if (kRing && ring) ring[0] = make_int4(0, 0, 0, 1);
         found0 = (kend == 0 && m0 >= m);
     }
     found0 = grp.bcast(found0);
@@ -360,7 +363,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         int lo = 0, hi = -1, w = 0;
         Wf fx, fo, fe;
         if (run) {
-            if constexpr (STAGE) {
+            if constexpr (kRing) {
                 fx = load_wf(src, s - X, mask); fo = load_wf(src, s - OE, mask); fe = load_wf(src, s - E, mask);
             } else {
                 fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
@@ -436,7 +439,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (gl == 0) {
                 const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
                 reinterpret_cast<int4*>(meta)[s] = rec;
-                if (STAGE && ring) ring[s & mask] = rec;
+                if (kRing && ring) ring[s & mask] = rec;
             }
             top += w;
             if (group_hit) { status = kDone; final_s = s; }
@@ -863,13 +866,13 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
         void (*kernel)(WfaArgs) = adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
                                         : (smem ? kernel_for<false, true>(G) : kernel_for<false, false>(G));
-        // staged launches: a ring of the last R score records per group, R a power of 2 above the farthest
-        // source (max(X, OE)), after the sequence copies, when a block's rings fit beside them in 48 KB
+        // exact staged launches: a ring of the last R score records per group, R a power of 2 above the
+        // farthest source (max(X, OE)), after the sequence copies, when a block's rings fit beside them in 48 KB
         uint32_t R = 1;
         while (R < (uint32_t)std::max(plan.x, plan.oe) + 1) R <<= 1;
         const size_t ring_bytes = (G > 32 ? 1 : (size_t)8 * (32 / G)) * R * sizeof(int4);
         a.meta_ring = 0; a.ring_off = (uint32_t)smem;
-        if (smem && R <= 64 && smem + ring_bytes <= (48u << 10)) { a.meta_ring = R; smem += ring_bytes; }
+        if (smem && !adapt && R <= 64 && smem + ring_bytes <= (48u << 10)) { a.meta_ring = R; smem += ring_bytes; }
         int bps = 0;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, smem);
         if (err != cudaSuccess) return err;
