@@ -614,10 +614,11 @@ __device__ __forceinline__ void finish_pending(const WfaArgs& a, const Group<G>&
     __syncwarp();
 }
 
-// Drains bucket b.  Groups of up to 32 lanes defer tracebacks: a group keeps finishing pairs in fresh parts
-// of its arena (its share of the warp's scratch) and traces them back G at a time, once it holds G of them,
-// once its arena has less room left than one pair may need (pair_bytes), or when the bucket is drained.
-// A pair's forward pass therefore always has at least pair_bytes, as without deferral.
+// Drains bucket b.  Groups defer tracebacks: a group keeps finishing pairs in fresh parts of its arena (its
+// share of the scratch) and traces them back side by side once it holds as many as it has tracing lanes (G
+// for a group of up to 32 lanes, one per warp for a whole block), once its arena has less room left than
+// one pair may need (pair_bytes), or when the bucket is drained.  A pair's forward pass therefore always has
+// at least pair_bytes, as without deferral.
 template <int G, bool ADAPT, bool STAGE>
 __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
