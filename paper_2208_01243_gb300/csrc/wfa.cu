@@ -191,8 +191,15 @@ struct Group<G, false> {
         gmask = G == 32 ? kFull : (((1u << G) - 1u) << leader);
     }
     __device__ int index(uint32_t lane) const { return (int)lane / G; }
-    __device__ bool any_running(bool x) const { return __any_sync(kFull, x); }
-    __device__ int iterations(int w) const { return (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G)); }
+    // with G == 32 the warp is one group, whose status and width every lane computes alike: no vote needed
+    __device__ bool any_running(bool x) const {
+        if constexpr (G == 32) return x;
+        else return __any_sync(kFull, x);
+    }
+    __device__ int iterations(int w) const {
+        if constexpr (G == 32) return (w + 31) / 32;
+        else return (int)__reduce_max_sync(kFull, (unsigned)((w + G - 1) / G));
+    }
     __device__ void min_max(int& lo, int& hi) const {
         if constexpr (G == 32) {   // the whole warp is one group: one warp-wide reduction each
             lo = __reduce_min_sync(kFull, lo);
@@ -385,14 +392,17 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
             if (run && k <= hi) {
+                // a candidate offset h is inside the matrix iff h <= min(m, n + k) (h <= m and v = h - k <= n);
+                // negative candidates stay negative (k >= -n keeps the bound >= 0)
+                const int hmax = min(m, n + k);
                 int ins = max(wf_get(hist, fo, 0, k + 1), wf_get(hist, fe, 1, k + 1));
-                if (ins >= 0 && ins - k > n) ins = kNeg16;
+                if (ins > hmax) ins = kNeg16;
                 int del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1));
                 del = del >= 0 ? del + 1 : kNeg16;
-                if (del > m) del = kNeg16;
+                if (del > hmax) del = kNeg16;
                 int mis = wf_get(hist, fx, 0, k);
                 mis = mis >= 0 ? mis + 1 : kNeg16;
-                if (mis > m || mis - k > n) mis = kNeg16;
+                if (mis > hmax) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
                 const int mv = f0 >= 0 ? extend<STAGE>(seqs, n, m, k, f0, n_windows) : kNeg16;
                 ++n_cells;
