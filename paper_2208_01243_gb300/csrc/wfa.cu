@@ -392,17 +392,15 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
             if (run && k <= hi) {
-                // a candidate offset h is inside the matrix iff h <= min(m, n + k) (h <= m and v = h - k <= n);
-                // negative candidates stay negative (k >= -n keeps the bound >= 0)
-                const int hmax = min(m, n + k);
+                // a candidate offset h is valid iff 0 <= h <= min(m, n + k) (h <= m and v = h - k <= n): one
+                // unsigned comparison, since an invalid source entry is kNeg16 and stays negative after + 1
+                const unsigned hmax = (unsigned)min(m, n + k);
                 int ins = max(wf_get(hist, fo, 0, k + 1), wf_get(hist, fe, 1, k + 1));
-                if (ins > hmax) ins = kNeg16;
-                int del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1));
-                del = del >= 0 ? del + 1 : kNeg16;
-                if (del > hmax) del = kNeg16;
-                int mis = wf_get(hist, fx, 0, k);
-                mis = mis >= 0 ? mis + 1 : kNeg16;
-                if (mis > hmax) mis = kNeg16;
+                if ((unsigned)ins > hmax) ins = kNeg16;
+                int del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1)) + 1;
+                if ((unsigned)del > hmax) del = kNeg16;
+                int mis = wf_get(hist, fx, 0, k) + 1;
+                if ((unsigned)mis > hmax) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
                 const int mv = f0 >= 0 ? extend<STAGE>(seqs, n, m, k, f0, n_windows) : kNeg16;
                 ++n_cells;
