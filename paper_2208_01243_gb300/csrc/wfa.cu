@@ -384,10 +384,10 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (w && ((size_t)top + (size_t)w) * kEntryElems > hist_cap) { status = kCap; run = false; w = 0; }
         }
         const int iters = grp.iterations(w);
-        bool hit = false;
+        int mv_end = kNeg16;   // M~ on the end diagonal kend, in the lane that computes it
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
-        uint32_t n_cells = 0, n_windows = 0;
+        uint32_t n_windows = 0;
         int dmin = 1 << 30, dmax = -(1 << 30);   // WFA-adaptive: distances of the new entries to the end cell
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
@@ -403,10 +403,9 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 if ((unsigned)mis > hmax) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
                 const int mv = f0 >= 0 ? extend<STAGE>(seqs, n, m, k, f0, n_windows) : kNeg16;
-                ++n_cells;
                 *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
                     (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
-                hit |= (k == kend && mv >= m);
+                if (k == kend) mv_end = mv;
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
                 if (ADAPT && mv >= 0) {
                     const int dist = max(n - (mv - k), m - mv);
@@ -415,10 +414,10 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 }
             }
         }
-        st.cells += n_cells;
+        if (gl == 0) st.cells += (unsigned)w;   // the wavefront's entries, computed by the group's lanes
         st.windows += n_windows;
         grp.min_max(vlo, vhi);   // group-wide trimmed range
-        const bool group_hit = grp.group_any(hit);
+        const bool group_hit = grp.group_any(mv_end >= m);
         if constexpr (ADAPT) {
             // WFA-adaptive: once the wavefront spans at least adapt_min_len diagonals, drop outer diagonals
             // whose distance to the end cell, max(n - v, m - h), exceeds the smallest by more than
