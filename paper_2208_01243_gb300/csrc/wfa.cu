@@ -134,11 +134,12 @@ struct PairSeqs<true> {
     __device__ uint64_t target_window(uint32_t pos) const { return window_shared(offT, pos); }
 };
 
-// furthest offset reached from (h - k, h) along matches on diagonal k
+// furthest offset reached from (h - k, h) along matches on diagonal k; a negative h (no valid start) comes back
+// unchanged without reading the sequences
 template <bool STAGE>
 __device__ __forceinline__ int extend(const PairSeqs<STAGE>& q, int n, int m, int k, int h, uint32_t& windows) {
     int v = h - k;
-    int rem = min(n - v, m - h);   // bases left on both sequences
+    int rem = h >= 0 ? min(n - v, m - h) : 0;   // bases left on both sequences (none for an invalid start)
     while (rem > 0) {
         ++windows;
         const uint64_t d = q.read_window((uint32_t)v) ^ q.target_window((uint32_t)h);
@@ -402,7 +403,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 int mis = wf_get(hist, fx, 0, k) + 1;
                 if ((unsigned)mis > hmax) mis = kNeg16;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
-                const int mv = f0 >= 0 ? extend<STAGE>(seqs, n, m, k, f0, n_windows) : kNeg16;
+                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);   // f0 stays kNeg16 if invalid
                 *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
                     (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
                 if (k == kend) mv_end = mv;
