@@ -405,7 +405,8 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
                 const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);   // f0 stays kNeg16 if invalid
                 *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
-                    (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint16_t)del << 32);
+                    (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
+                // (the spare slot, bits 48-63, takes del's sign bits: nothing reads it)
                 if (k == kend) mv_end = mv;
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
                 if (ADAPT && mv >= 0) {
