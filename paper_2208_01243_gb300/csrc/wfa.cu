@@ -382,7 +382,9 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
             w = lo <= hi ? hi - lo + 1 : 0;
-            if (w && ((size_t)top + (size_t)w) * kEntryElems > hist_cap) { status = kCap; run = false; w = 0; }
+            if (w && ((size_t)top + (size_t)w) * kEntryElems > hist_cap) {
+                status = kCap; run = false; w = 0; hi = lo - 1;
+            }
         }
         const int iters = grp.iterations(w);
         int mv_end = kNeg16;   // M~ on the end diagonal kend, in the lane that computes it
@@ -392,7 +394,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         int dmin = 1 << 30, dmax = -(1 << 30);   // WFA-adaptive: distances of the new entries to the end cell
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
-            if (run && k <= hi) {
+            if (k <= hi) {   // a group that does not run this score has an empty range (hi < lo)
                 // a candidate offset h is valid iff 0 <= h <= min(m, n + k) (h <= m and v = h - k <= n): one
                 // unsigned comparison, since an invalid source entry is kNeg16 and stays negative after + 1
                 const unsigned hmax = (unsigned)min(m, n + k);
