@@ -900,9 +900,14 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         if (warps == 0) { *warps_used = 0; return cudaSuccess; }   // not one block's scratch fits: caller reports it
         a.nwarps = (uint32_t)warps;
         // the launch spreads the whole scratch over its warps: what a pair may need stays pair_bytes, and
-        // the rest holds finished pairs until their tracebacks run side by side
+        // the rest holds finished pairs until their tracebacks run side by side.  The kernel counts a group's
+        // arena in 16-byte units in 32 bits, so the spread stops at 32 GiB per group (far more than the 32
+        // pending pairs of any realistic workload need); a plan that needs more for one pair keeps its size.
         a.pair_bytes = G > 32 ? warp_bytes * (size_t)(G / 32) : (warp_bytes / (size_t)(32 / G)) & ~(size_t)15;
-        a.warp_bytes = std::max(warp_bytes, (scratch_bytes / warps) & ~(size_t)15);
+        const size_t max_group = ((size_t)32 << 30) - 16;
+        const size_t max_warp = G > 32 ? max_group / (size_t)(G / 32) : max_group * (size_t)(32 / G);
+        a.warp_bytes = std::min(std::max(warp_bytes, (scratch_bytes / warps) & ~(size_t)15),
+                                std::max(warp_bytes, max_warp & ~(size_t)15));
         kernel<<<(unsigned)(warps / 8), 256, smem, st>>>(a);
         err = cudaGetLastError();
         if (err != cudaSuccess) return err;
