@@ -73,6 +73,9 @@ def _load():
         lib.oracle_wfa_adaptive.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i32, i32, i32, i32, i64,
                                             i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8), p, u32,
                                             ctypes.POINTER(u32)]
+        lib.oracle_wfa_adaptive_kept.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i32, i32, i32, i32,
+                                                 i64, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8),
+                                                 p, i64, ctypes.POINTER(i64)]
         lib.oracle_wfa_adaptive_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, i32, i32, p, p, p, p,
                                                   p, ctypes.c_int]
         lib.oracle_genasm.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i64, i32, i32, ctypes.POINTER(i32),
@@ -132,6 +135,24 @@ def wfa_adaptive(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int =
     if r:
         raise RuntimeError(f"oracle_wfa_adaptive failed: {r}")
     return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
+
+
+def wfa_adaptive_kept(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int = -1, limit: int = 1 << 62,
+                      min_len: int = ADAPT_MIN_LEN, max_dist: int = ADAPT_MAX_DIST):
+    """One pair through the WFA-adaptive -> (score, flags, {s: (lo, hi)}): the diagonal range kept at every score
+    (scaled by gcd(x, o, e)) whose wavefront is not empty, up to the score the pair finished at."""
+    lib = _load()
+    _, x, o, e = penalties
+    sc = ctypes.c_int32(); fl = ctypes.c_uint8(); nk = ctypes.c_int64()
+    cap = 4 * (len(read) + len(target)) * max(x, o + e, 1) + 8
+    buf = np.zeros(2 * cap, np.int32)
+    r = lib.oracle_wfa_adaptive_kept(bytes(read), len(read), bytes(target), len(target), x, o, e, band, limit,
+                                     min_len, max_dist, ctypes.byref(sc), ctypes.byref(fl),
+                                     ctypes.c_void_p(buf.ctypes.data), cap, ctypes.byref(nk))
+    if r:
+        raise RuntimeError(f"oracle_wfa_adaptive_kept failed: {r}")
+    kept = {s: (int(buf[2 * s]), int(buf[2 * s + 1])) for s in range(nk.value) if buf[2 * s] <= buf[2 * s + 1]}
+    return sc.value, fl.value, kept
 
 
 def wfa_adaptive_batch(pairs, penalties, limits: np.ndarray, band: int = -1, min_len: int = ADAPT_MIN_LEN,

@@ -240,7 +240,12 @@ int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32
  *
  * Pinned by: with pruning off the score equals the full-matrix DP optimum
  * and the CIGAR re-costs to it (brute force and DP tests); with pruning the
- * CIGAR is a valid alignment that re-costs to the reported score.
+ * CIGAR is a valid alignment that re-costs to the reported score, and
+ * hand-worked cases (tests/golden/adaptive_prune.txt) fix the pruning step
+ * itself: the kept range at every score, the score and the ops, including a
+ * tie exactly max_distance behind, a width exactly min_length, distances at the
+ * extended offset, both ends trimmed, far interior diagonals kept, a pair
+ * rejected because its end diagonal was pruned and one pruned above its optimum.
  * --------------------------------------------------------------------------- */
 
 static int32_t gcd32(int32_t a, int32_t b) { while (b) { int32_t t = a % b; a = b; b = t; } return a < 0 ? -a : a; }
@@ -266,11 +271,15 @@ static int32_t wfa_extend_plain(const char *P, int32_t n, const char *T, int32_t
     return h;
 }
 
-int oracle_wfa_adaptive(const char *P, uint32_t un, const char *T, uint32_t um, int32_t x, int32_t o, int32_t e,
-                        int32_t band, int64_t limit, int32_t lmin, int32_t dmax, int32_t *score, uint8_t *flags,
-                        uint32_t *cigar, uint32_t cap, uint32_t *ncig) {
+/* kept (may be NULL): for s = 0, 1, ... the diagonal range [lo, hi] kept at score s (lo > hi: empty), two
+ * entries per score, up to the score the pair finished at (or the last score tried); *nkept: scores written. */
+static int wfa_adaptive_run(const char *P, uint32_t un, const char *T, uint32_t um, int32_t x, int32_t o, int32_t e,
+                            int32_t band, int64_t limit, int32_t lmin, int32_t dmax, int32_t *score, uint8_t *flags,
+                            uint32_t *cigar, uint32_t cap, uint32_t *ncig, int32_t *kept, int64_t kept_cap,
+                            int64_t *nkept) {
     const int32_t n = (int32_t)un, m = (int32_t)um;
     *score = -1; *flags = 0; *ncig = 0;
+    if (nkept) *nkept = 0;
     const int32_t kend = m - n;
     if (band >= 0 && (kend > band || -kend > band)) { *flags = 1; return 0; }
     int32_t g = gcd32(gcd32(x, o), e);
@@ -419,9 +428,32 @@ int oracle_wfa_adaptive(const char *P, uint32_t un, const char *T, uint32_t um, 
         free(ops);
     }
 done:
+    if (kept && rc == 0) {
+        /* scores computed: up to the finishing one, else every score up to S */
+        const int64_t last = found >= 0 ? found : S;
+        int64_t t = 0;
+        for (; t <= last && t < kept_cap; ++t) { kept[2 * t] = F[t].lo; kept[2 * t + 1] = F[t].hi; }
+        if (nkept) *nkept = t;
+    }
     for (int64_t t = 0; t <= S; ++t) { free(F[t].M); free(F[t].I); free(F[t].D); }
     free(F);
     return rc;
+}
+
+int oracle_wfa_adaptive(const char *P, uint32_t un, const char *T, uint32_t um, int32_t x, int32_t o, int32_t e,
+                        int32_t band, int64_t limit, int32_t lmin, int32_t dmax, int32_t *score, uint8_t *flags,
+                        uint32_t *cigar, uint32_t cap, uint32_t *ncig) {
+    return wfa_adaptive_run(P, un, T, um, x, o, e, band, limit, lmin, dmax, score, flags, cigar, cap, ncig, NULL, 0,
+                            NULL);
+}
+
+/* The same, also reporting the diagonal range kept at every score (see wfa_adaptive_run). */
+int oracle_wfa_adaptive_kept(const char *P, uint32_t un, const char *T, uint32_t um, int32_t x, int32_t o, int32_t e,
+                             int32_t band, int64_t limit, int32_t lmin, int32_t dmax, int32_t *score, uint8_t *flags,
+                             int32_t *kept, int64_t kept_cap, int64_t *nkept) {
+    uint32_t ncig = 0;
+    return wfa_adaptive_run(P, un, T, um, x, o, e, band, limit, lmin, dmax, score, flags, NULL, 0, &ncig, kept,
+                            kept_cap, nkept);
 }
 
 /* ---- batch driver for the adaptive WFA (same layout as oracle_align_batch) ---- */

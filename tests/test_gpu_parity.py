@@ -385,3 +385,23 @@ def test_wfa_adaptive_paper_costs_150bp(aligner, oracle_lib, gen_lib):
     assert_same(dev, orc, what="wfa adaptive 150bp paper costs")
     exact = oracle_results(p, pen, lim)
     assert (dev[0] == exact[0]).mean() > 0.99
+
+
+@pytest.mark.parametrize("lanes", [0, 1, 4, 32, 256])
+def test_wfa_adaptive_hand_worked_pruning(aligner, oracle_lib, lanes):
+    """The hand-worked pruning cases (tests/golden/adaptive_prune.txt) through the CUDA kernel: score, flags and ops."""
+    import paper_2208_01243_gb300 as aim
+    from test_oracle_adaptive import GOLDEN_ROWS
+    aim.aim_set_wfa_group(aligner.ctx, lanes)
+    try:
+        for r, t, pen, lim, lmin, dmax, score, ops, kept in GOLDEN_ROWS:
+            p = gen.from_strings([r.decode()], [t.decode()])
+            aim.aim_set_wfa_adaptive(aligner.ctx, lmin, dmax)
+            dev = device_results(p, "wfa_adaptive", pen, -1, max_score=lim, aligner=aligner)
+            if score < 0:
+                assert (dev[0][0], dev[1][0]) == (-1, oracle.F_REJECTED), (r, t)
+            else:
+                assert (dev[0][0], dev[1][0], decode(dev[2][0])) == (score, 0, ops), (r, t, lanes)
+    finally:
+        aim.aim_set_wfa_group(aligner.ctx, 0)
+        aim.aim_set_wfa_adaptive(aligner.ctx, 10, 50)
