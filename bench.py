@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per pair for the plain WFA calls (0: library choice)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
+    ap.add_argument("--serve-probe-seconds", type=float, default=4.0,
+                    help="duration of each open-loop rate tried while searching the serving peak")
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving wavefront-state budget (GiB)")
     return ap.parse_args()
 
@@ -353,6 +355,7 @@ def run_ours(args, w, algo):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    measured_int_peak = aim.aim_measure_int_peak(local)   # the roofline's denominator, on this device
 
     stream = torch.cuda.current_stream()
     clocks = ClockSampler(local)
@@ -428,102 +431,52 @@ def run_ours(args, w, algo):
                  "batched_pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c}}
         del gd
 
-    # ---- end to end through the same call: pinned host inputs in, results out, copies timed.  The steps run as
-    # a double-buffered pipeline over two device buffer sets: step i+1's inputs copy in on one copy stream while
-    # step i aligns on the compute stream, and step i's results copy out on a second copy stream meanwhile.
-    # Every step still copies its own inputs in and its own results out inside the timed region.
-    hp = {k: torch.from_numpy(np.ascontiguousarray(v).view(
-        {np.dtype(np.uint64): np.int64, np.dtype(np.uint32): np.int32}.get(np.asarray(v).dtype, np.asarray(v).dtype)))
-        .pin_memory() for k, v in host.items()}
-    h2d = sum(v.numel() * v.element_size() for v in hp.values())
-    d2h = sum(v.numel() * v.element_size() for v in out.values())
-    # set 0: the buffers the device-resident run used (a batched plan is bound to them); set 1: a second copy
-    din = [d if batched else {k: torch.empty_like(v, device=dev) for k, v in hp.items()},
-           {k: torch.empty_like(v, device=dev) for k, v in hp.items()}]
-    dout = [out, {k: torch.empty_like(v) for k, v in out.items()}]
-    hout = [{k: torch.empty(v.shape, dtype=v.dtype, pin_memory=True) for k, v in out.items()} for _ in range(2)]
-    for k in hp:   # planning packs and buckets the bound inputs, so the second set holds them first
-        din[1][k].copy_(hp[k])
-    torch.cuda.synchronize()
-    plan1 = None
-    if batched:   # the second plan takes the lanes per bucket the first one tuned (cached in the context)
-        plan1 = aim.aim_batch_plan(al.ctx, din[1]["reads"], din[1]["targets"], din[1]["ro"], din[1]["to"],
-                                   din[1]["rl"], din[1]["tl"], max_len, pen, max_edits, din[1].get("pp"),
-                                   dout[1]["scores"], dout[1]["cigars"], coff_d, dout[1]["lens"], dout[1]["flags"],
-                                   scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=False)
-    plans = [plan, plan1]
-    cs = torch.cuda.current_stream()
-    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    # ---- end to end through the host-buffer entry point (aim_align_batch_host): pinned host inputs in, every
+    # result back in pinned host memory, the transfers inside the call.  The library cuts the batch into chunks and
+    # pipelines them through two device slots (one chunk's copies beside another's alignment); the first call plans
+    # the slots, so it is a warm-up.  e2e.serial is the same call with the whole batch as one chunk (copy in, align,
+    # copy out, in sequence).
+    if plan is not None:
+        aim.aim_batch_destroy(plan)     # the device-resident run is done; the host path plans its own slots
+        plan = None
 
-    def align_set(b):
-        if batched:
-            aim.aim_batch_run(plans[b], cs)
-        else:
-            src, o = din[b], dout[b]
-            aim.aim_align_batch_ascii(al.ctx, src["reads"], src["targets"], src["ro"], src["to"], src["rl"],
-                                      src["tl"], max_len, algo, pen, max_edits, src.get("pp"), o["scores"],
-                                      o["cigars"], coff_d, o["lens"], o["flags"], stream=cs)
+    def pinned(a):
+        a = np.ascontiguousarray(a)
+        t = torch.empty(max(a.nbytes, 1), dtype=torch.uint8, pin_memory=True)
+        v = t.numpy()[:a.nbytes].view(a.dtype)
+        v[...] = a
+        return v
 
-    def e2e_run(n_steps):
-        """n_steps pipelined steps; returns the elapsed ms from before the first copy in to after the last copy
-        out."""
-        ev = lambda: torch.cuda.Event(enable_timing=False)
-        aligned = [None, None]    # per set: its last step's alignment finished (inputs free, results ready)
-        copied = [None, None]     # per set: its last step's results are in host memory (outputs free)
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0.record(cs)
-        s_in.wait_event(t0)
-        for i in range(n_steps):
-            b = i % 2
-            if aligned[b] is not None:
-                s_in.wait_event(aligned[b])
-            with torch.cuda.stream(s_in):
-                for k in hp:
-                    din[b][k].copy_(hp[k], non_blocking=True)
-            loaded = ev(); loaded.record(s_in)
-            cs.wait_event(loaded)
-            if copied[b] is not None:
-                cs.wait_event(copied[b])
-            align_set(b)
-            aligned[b] = ev(); aligned[b].record(cs)
-            s_out.wait_event(aligned[b])
-            with torch.cuda.stream(s_out):
-                for k in out:
-                    hout[b][k].copy_(dout[b][k], non_blocking=True)
-            copied[b] = ev(); copied[b].record(s_out)
-        for c in copied:
-            if c is not None:
-                cs.wait_event(c)
-        t1.record(cs)
+    def pinned_zeros(dtype, n):
+        return pinned(np.zeros(n, dtype))
+    hin = {"reads": pinned(p.reads), "targets": pinned(p.targets), "ro": pinned(p.read_off),
+           "to": pinned(p.target_off), "rl": pinned(p.read_len), "tl": pinned(p.target_len),
+           "pp": pinned(per_pair.astype(np.int32)) if per_pair is not None else None,
+           "coff": pinned(coff.astype(np.uint64))}
+    hres = {"scores": pinned_zeros(np.int32, n_pairs), "flags": pinned_zeros(np.uint8, n_pairs),
+            "lens": pinned_zeros(np.uint32, n_pairs), "cigars": pinned_zeros(np.uint32, int(coff[-1]))}
+
+    def host_step(chunk=0):
+        return aim.aim_align_batch_host(al.ctx, hin["reads"], hin["targets"], hin["ro"], hin["to"], hin["rl"],
+                                        hin["tl"], max_len, algo, pen, max_edits, hin["pp"], hres["scores"],
+                                        hres["cigars"], hin["coff"], hres["lens"], hres["flags"], chunk_pairs=chunk)
+
+    def host_timed(chunk):
+        for _ in range(max(2, args.warmup)):
+            host_step(chunk)
+        barrier(); torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            moved = host_step(chunk)
         torch.cuda.synchronize()
-        return t0.elapsed_time(t1)
-
-    e2e_run(max(2, args.warmup))
-    barrier(); torch.cuda.synchronize()
-    e2e_ms = _dist_max(e2e_run(args.steps) / args.steps, dev, world)
-    for b in range(min(2, args.steps)):
-        assert np.array_equal(hout[b]["scores"].numpy(), res_scores), "e2e results differ from the device-resident run"
-        assert np.array_equal(hout[b]["flags"].numpy(), res_flags), "e2e flags differ from the device-resident run"
-
-    # the same steps one after another (copy in, align, copy out), for comparison
-    def serial_step():
-        for k in hp:
-            din[0][k].copy_(hp[k], non_blocking=True)
-        align_set(0)
-        for k in out:
-            hout[0][k].copy_(dout[0][k], non_blocking=True)
-    serial_step()
-    torch.cuda.synchronize(); barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(cs)
-    for _ in range(args.steps):
-        serial_step()
-    e1.record(cs)
-    torch.cuda.synchronize(); barrier()
-    serial_ms = _dist_max(e0.elapsed_time(e1) / args.steps, dev, world)
-    if plan1 is not None:
-        aim.aim_batch_destroy(plan1)
-    del din, dout
+        dt = (time.perf_counter() - t0) * 1e3 / args.steps
+        assert np.array_equal(hres["scores"], res_scores), "host-buffer results differ from the device-resident run"
+        assert np.array_equal(hres["flags"], res_flags), "host-buffer flags differ from the device-resident run"
+        assert np.array_equal(hres["lens"], res_lens.view(np.uint32)), "host-buffer run counts differ"
+        barrier()
+        return _dist_max(dt, dev, world), moved
+    e2e_ms, (h2d, d2h) = host_timed(0)
+    serial_ms, _ = host_timed(n_pairs)
 
     if rank != 0:
         if plan is not None:
@@ -531,11 +484,13 @@ def run_ours(args, w, algo):
         al.close()
         return 0
 
-    # ---- roofline of the alignment kernel: algorithmic integer ops per launch / its mean launch time
+    # ---- roofline of the alignment kernel: algorithmic integer ops per launch / its mean launch time, against the
+    # int32 ALU throughput measured on this device by the library's microbenchmark (aim_measure_int_peak)
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     sm_max = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0
-    peak_ops = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6
+    derived_ops = props.multi_processor_count * INT32_LANES_PER_SM * sm_max * 1e6
+    peak_ops, peak_ms, peak_mix = measured_int_peak
     launches = max(align_n, 1)
     if algo in ("wfa", "wfa_adaptive"):
         ops = stats["wf_entries"] * OPS_WF_ENTRY + stats["extend_windows"] * OPS_EXT_WINDOW
@@ -554,8 +509,11 @@ def run_ours(args, w, algo):
             "frac": achieved / (peak_ops / 1e12), "traffic": (tr["dram_bytes_per_launch"] if tr else None),
             "kernel": kernel, "kernel_ms": kern_s * 1e3, "kernel_launches_timed": align_n,
             "ops_per_launch": ops_per_launch,
-            "peak_note": f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} int32 lanes x {sm_max:.0f} MHz "
-                         "(derived from unit counts and the max SM clock; no measured int32 peak exists)",
+            "peak_note": f"measured: independent int32 chains filling all {props.multi_processor_count} SMs "
+                         f"(aim_measure_int_peak, before the timed region): add/max/xor {peak_mix[0] / 1e12:.2f} T/s, "
+                         f"add/xor/shift {peak_mix[1] / 1e12:.2f} T/s, the higher one is the peak; for context, "
+                         f"{props.multi_processor_count} SMs x {INT32_LANES_PER_SM} lanes x {sm_max:.0f} MHz = "
+                         f"{derived_ops / 1e12:.1f} T/s",
             "work_per_launch": {k: v // launches for k, v in stats.items()},
             "pack_ms_per_launch": pack_ms / max(pack_n, 1) if pack_n else None}
     packed_words = int(((p.read_len.astype(np.int64) + 31) // 32).sum()
@@ -578,10 +536,12 @@ def run_ours(args, w, algo):
             "roofline": roof,
             "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-                    "form": "double-buffered: step i+1's inputs copy in and step i's results copy out while step i "
-                            "aligns (two copy streams, two device buffer sets)",
+                    "form": "aim_align_batch_host: one C-ABI call per step on pinned host buffers (ASCII pairs in, "
+                            "scores/flags/CIGARs out); the library pipelines chunks through two device slots so "
+                            "copies overlap alignment" + ("; WFA in the batched form per chunk" if algo == "wfa"
+                                                          else "; plain form per chunk"),
                     "serial": {"value": world * n_pairs / (serial_ms / 1e3), "ms_per_step": serial_ms,
-                               "form": "copy in, align, copy out, one step after another"}},
+                               "form": "the same call with the whole batch as one chunk: copy in, align, copy out"}},
             "gpu_launches": args.steps * launches_per_step,
             "clocks": clk}
     if plain is not None:
@@ -611,8 +571,10 @@ def run_ours(args, w, algo):
 
 def serving(args, local):
     """Poisson arrivals of requests (1-4096 pairs, log-uniform; reads 100-10,000 bp log-uniform; 1-10 % edits;
-    thresholds at 10 % of length) through the continuous-batching server: peak = closed-loop throughput with
-    a backlog of requests, then p50/p99 latency and sustained alignments/s at 50/80/95 % of that peak."""
+    thresholds at 10 % of length) through the continuous-batching server.  The peak is the highest open-loop rate
+    whose queue stays bounded: Poisson arrivals at falling fractions of the closed-loop throughput (a backlog of
+    requests submitted at once) until latency no longer grows over the run and the server keeps up; then p50/p99
+    latency, sustained alignments/s and the queue length over time at 50/80/95 % of that peak."""
     import torch
     import paper_2208_01243_gb300 as aim
     w = gen.SERVE_LONG
@@ -636,8 +598,10 @@ def serving(args, local):
                 out[3], coff), k
 
     def run(arrivals, sizes):
+        """Submit at the given times; returns latencies (s, submission order), pairs, wall time (first submission to
+        last completion) and queue samples (s since start, requests queued or running)."""
         t0 = time.perf_counter()
-        tickets = []
+        tickets, queue = [], []
         for a, k in zip(arrivals, sizes):
             req, k = make_request(int(k))
             now = time.perf_counter() - t0
@@ -645,36 +609,73 @@ def serving(args, local):
                 time.sleep(a - now)
             t, keep = aim.aim_server_submit(srv, *req)
             tickets.append((t, keep, k))
+            st = aim.aim_server_stats(srv)
+            queue.append((time.perf_counter() - t0, st["queued"] + st["running"]))
         lats = [aim.aim_server_wait(srv, t) for t, _, _ in tickets]
         wall = time.perf_counter() - t0
         pairs = sum(k for _, _, k in tickets)
-        return np.array(lats), pairs, wall
+        return np.array(lats), pairs, wall, queue
 
-    # peak: a backlog of requests submitted at once (about a second of work, so start and drain matter little)
+    def offered(rate_pairs, seconds, seed):
+        """Poisson arrivals offering rate_pairs pairs/s for about `seconds` (gaps and sizes as drawn, time axis
+        scaled so the offered rate is exact)."""
+        rate = rate_pairs / mean_req
+        count = max(20, int(rate * seconds))
+        arr, sz = gen.arrivals(seed, count, rate)
+        arr = arr * (float(sz.sum()) / rate_pairs / float(arr[-1]))
+        return arr, sz
+
+    # closed loop: a backlog of requests submitted at once (about a second of work)
     _, sizes = gen.arrivals(505, 480, 1.0)
     run(np.zeros(16), sizes[:16])                               # warm-up
-    lat, pairs, wall = run(np.zeros(len(sizes)), sizes)
-    peak = pairs / wall
+    lat, pairs, wall, _ = run(np.zeros(len(sizes)), sizes)
+    closed = pairs / wall
     mean_req = float(sizes.mean())
+
+    # open-loop peak: the highest offered rate at which the queue stays bounded
+    trials = []
+    peak = None
+    for j, frac in enumerate((0.95, 0.9, 0.85, 0.8, 0.75, 0.7, 0.6, 0.5)):
+        arr, sz = offered(frac * closed, args.serve_probe_seconds, 700 + j)
+        lat, pairs, wall, queue = run(arr, sz)
+        q = len(lat) // 4
+        first, last = float(np.median(lat[:q])), float(np.median(lat[-q:]))
+        sustained = pairs / wall
+        rate = float(sz.sum()) / float(arr[-1])
+        bounded = last <= 2.0 * first + 0.02 and sustained >= 0.95 * rate
+        trials.append({"offered_pairs_per_s": rate, "fraction_of_closed_loop": frac, "bounded": bool(bounded),
+                       "sustained_alignments_per_s": sustained, "p50_first_quarter_ms": first * 1e3,
+                       "p50_last_quarter_ms": last * 1e3, "max_queue": int(max(x[1] for x in queue))})
+        if bounded:
+            peak = rate
+            break
+    if peak is None:
+        peak = trials[-1]["offered_pairs_per_s"]
     levels = {}
     for frac in (0.5, 0.8, 0.95):
-        rate = frac * peak / mean_req                          # requests per second
-        count = max(20, int(rate * args.serve_seconds))
-        arr, sz = gen.arrivals(600 + int(frac * 100), count, rate)
-        if count > 1:   # Poisson gaps and sizes as drawn, the time axis scaled so the offered rate is exactly frac * peak
-            arr = arr * (float(sz.sum()) / (frac * peak) / float(arr[-1]))
-        lat, pairs, wall = run(arr, sz)
-        levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": float(sz.sum()) / float(arr[-1]) if count > 1 else
-                                         frac * peak, "requests": count,
-                                         "sustained_alignments_per_s": pairs / wall,
+        arr, sz = offered(frac * peak, args.serve_seconds, 600 + int(frac * 100))
+        lat, pairs, wall, queue = run(arr, sz)
+        # queue length over time: requests queued or running, sampled at submissions, as (s, count) every ~0.25 s
+        qs, nxt = [], 0.0
+        for t, c in queue:
+            if t >= nxt:
+                qs.append([round(t, 2), int(c)])
+                nxt = t + 0.25
+        levels[f"{int(frac * 100)}%"] = {"offered_pairs_per_s": float(sz.sum()) / float(arr[-1]),
+                                         "requests": len(sz), "sustained_alignments_per_s": pairs / wall,
                                          "p50_latency_ms": float(np.percentile(lat, 50) * 1e3),
-                                         "p99_latency_ms": float(np.percentile(lat, 99) * 1e3)}
+                                         "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                                         "queue_over_time": qs}
     st = aim.aim_server_stats(srv)
     aim.aim_server_destroy(srv)
     aim.aim_destroy(ctx)
     return {"workload": "serve_100_10000bp_1_10pct: Poisson requests of 1-4096 pairs (log-uniform), reads "
                         "100-10,000 bp (log-uniform), 1-10 % edits, WFA 4/6/2, thresholds ceil(0.1*len)",
-            "wavefront_budget_gib": args.serve_budget_gb, "peak_alignments_per_s": peak, "mean_pairs_per_request": mean_req,
+            "wavefront_budget_gib": args.serve_budget_gb, "peak_alignments_per_s": peak,
+            "peak_rule": "highest open-loop Poisson rate (falling fractions of the closed-loop throughput) whose "
+                         "median latency in the last quarter of the run stays within 2x that of the first quarter "
+                         "+ 20 ms and whose sustained throughput is >= 95 % of the offered rate",
+            "closed_loop_alignments_per_s": closed, "peak_search": trials, "mean_pairs_per_request": mean_req,
             "loads": levels, "failed": st["failed"],
             "latency": "server clock from submission to results in host memory (includes queueing, copies)"}
 

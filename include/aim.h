@@ -183,6 +183,40 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
                           aim_stream_t stream);
 
 /*
+ * Host-buffer form: aim_align_batch_ascii from HOST memory to HOST memory in
+ * one blocking call, the transfers inside it (the paper's timed region covers
+ * the transfer of the pairs in, alignment, traceback and the transfer of the
+ * scores and operations back: Section 2.2, Steps 2-6; Section 3.1).
+ *   Every pointer except ctx and pen is host memory.  Inputs as for
+ *   aim_align_batch_ascii (byte offsets into reads/targets, any layout);
+ *   cigar_offsets has num_pairs + 1 non-decreasing entries and pair i's runs go
+ *   to out_cigars + cigar_offsets[i] (entries past its run count are written as
+ *   zero).  Pinned (page-locked) host buffers let the copies overlap the
+ *   kernels; pageable ones work but copy synchronously.
+ *   chunk_pairs   pairs per chunk (0: an eighth of the batch, at least 65,536)
+ *   bytes_moved   optional host[2]: bytes copied host-to-device and device-to-host
+ * The batch goes through the device in chunks, two device slots in turn: while
+ * one chunk aligns, the next one's inputs copy in and the previous one's
+ * results copy out.  AIM_ALGO_WFA_AFFINE runs the batched form (each slot holds
+ * a batch plan, autotuned on the first chunk; a short last chunk is padded with
+ * empty pairs; each slot's plan takes half of the context workspace as its
+ * scratch, so one chunk's launches overlap the next one's); the other
+ * algorithms run the plain form per chunk.  The slots, streams and plans stay
+ * in the context for later calls of the same shape (algorithm, costs,
+ * thresholds, max_length, chunk size), whose first call pays for planning;
+ * they are freed by aim_destroy or replaced by a call of another shape.
+ * Nothing else may use the context during the call.  Returns once every
+ * result is in host memory; results equal aim_align_batch_ascii's bit for bit.
+ */
+AIM_API int aim_align_batch_host(aim_ctx *ctx, const uint8_t *reads, const uint8_t *targets,
+                                 const uint64_t *read_char_offsets, const uint64_t *target_char_offsets,
+                                 const uint32_t *read_lengths, const uint32_t *target_lengths, uint32_t num_pairs,
+                                 uint32_t max_length, int algo, const aim_penalties_t *pen, int32_t max_edits,
+                                 const int32_t *max_edits_per_pair, int32_t *out_scores, uint32_t *out_cigars,
+                                 const uint64_t *cigar_offsets, uint32_t *out_cigar_lens, uint8_t *out_flags,
+                                 uint32_t chunk_pairs, uint64_t *bytes_moved);
+
+/*
  * WFA-adaptive parameters of a context (defaults 10 and 50; the paper gives
  * none).  After wavefront s (unless the pair finished at s), if it spans at
  * least min_length diagonals, each diagonal's distance to the end cell,
@@ -314,7 +348,8 @@ typedef struct {
 /* pen: costs and band for every request (max_score must be < 0: thresholds are per pair). */
 AIM_API int aim_server_create(aim_ctx *ctx, const aim_penalties_t *pen, size_t wavefront_budget_bytes,
                               size_t io_budget_bytes, aim_server **out);
-/* Copies the request's inputs and queues it; the output buffers must stay valid until it completes.
+/* Copies the request's inputs and queues it; the output buffers must stay valid until it completes (CIGAR
+ * entries past a pair's run count are written as zero).
  * AIM_ERR_NOMEM: one pair's wavefront scratch or the request's I/O exceeds the server's budgets. */
 AIM_API int aim_server_submit(aim_server *server, const aim_request *request, uint64_t *ticket);
 /* *done = 1 once the request's results are in its output buffers; then the ticket is released and
@@ -363,6 +398,20 @@ AIM_API int aim_timing_enable(aim_ctx *ctx, int on);
 AIM_API int aim_timing_read(aim_ctx *ctx, int kind, double *total_ms /* host */, int *launches /* host */);
 
 /*
+ * Measured int32 ALU throughput of `device` (a measurement helper: the
+ * denominator of the roofline fraction reported for the alignment kernels,
+ * whose work is integer add/max/compare/logic, not a dense contraction).
+ * A kernel fills every SM with independent dependency chains of int32
+ * operations, in two mixes: add/max/xor (the cell updates) and add/xor/shift/add
+ * (the extend's window arithmetic).  *ops_per_s is the higher rate, in
+ * source-level int32 operations per second (the unit of the work counters
+ * above), each mix's rate the best of five timed launches; *kernel_ms
+ * (optional) is that launch's duration and per_mix (optional, host[2]) each
+ * mix's rate.  Synchronous; it allocates and frees a few KB of device memory.
+ */
+AIM_API int aim_measure_int_peak(int device, double *ops_per_s, double *kernel_ms, double *per_mix);
+
+/*
  * aim_wfa_align_static -- the gap-affine wavefront aligner (as aim_align_batch
  * with AIM_ALGO_WFA_AFFINE) for callers that cannot allocate device memory.
  * The paper has no counterpart; this is a deployment convenience.
@@ -382,7 +431,10 @@ AIM_API int aim_timing_read(aim_ctx *ctx, int kind, double *total_ms /* host */,
  *
  * Set-up: the first call on each device (run it with that device current)
  * looks up the array's device address and caches it; make that first call
- * before any stream capture.
+ * before any stream capture.  A reset context (cudaDeviceReset) or another
+ * context on the device holds the array at another address: every call made
+ * outside stream capture looks the address up again, so after a reset make one
+ * call outside capture before capturing any.
  *
  * Limits: if one pair's scratch (from max_length, the threshold and the band;
  * about 5.5 KB for 150 bp reads at 6 edits, about 1.3 MB for 1 kbp at 100 edits)

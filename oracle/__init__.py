@@ -8,6 +8,7 @@ and never imports it.
 Contents:
   aim_oracle.c  full-matrix 3-state DP (Gotoh; NW edit distance as the unit-cost
                 special case) with the canonical backward state-set traceback,
+                the same DP with rows recomputed block by block for long pairs,
                 plus a textbook one-state Levenshtein (Sections 2.4.1, 2.4.2),
                 the WFA-adaptive heuristic written out step by step
                 (Section 2.4.4; exact WFA when pruning is off), and GenASM's
@@ -70,6 +71,11 @@ def _load():
         lib.oracle_levenshtein.restype = i32
         lib.oracle_align_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, p, p, p, p, p,
                                            ctypes.c_int]
+        lib.oracle_align_rows.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i32, i32, i32, i32, i64, i32,
+                                          ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8), p, u32,
+                                          ctypes.POINTER(u32)]
+        lib.oracle_align_rows_batch.argtypes = [p, p, p, p, p, p, u64, i32, i32, i32, i32, p, p, p, p, p, p,
+                                                ctypes.c_int, i32]
         lib.oracle_wfa_adaptive.argtypes = [ctypes.c_char_p, u32, ctypes.c_char_p, u32, i32, i32, i32, i32, i64,
                                             i32, i32, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_uint8), p, u32,
                                             ctypes.POINTER(u32)]
@@ -214,13 +220,30 @@ def genasm_batch(pairs, limits: np.ndarray, W: int = GENASM_W, O: int = GENASM_O
     return scores, flags, off, cig, lens
 
 
+def align_rows(read: bytes, target: bytes, penalties=(0, 4, 6, 2), band: int = -1, limit: int = 1 << 62,
+               rows_per_block: int = 0):
+    """align() for long pairs: the same DP and traceback with rows recomputed block by block from saved rows
+    (memory linear in the target length per block; rows_per_block <= 0: ceil(sqrt(n + 1)))."""
+    lib = _load()
+    _, x, o, e = penalties
+    sc = ctypes.c_int32(); fl = ctypes.c_uint8(); nc = ctypes.c_uint32()
+    cap = len(read) + len(target) + 1
+    buf = np.zeros(cap, np.uint32)
+    r = lib.oracle_align_rows(bytes(read), len(read), bytes(target), len(target), x, o, e, band, limit,
+                              rows_per_block, ctypes.byref(sc), ctypes.byref(fl), ctypes.c_void_p(buf.ctypes.data),
+                              cap, ctypes.byref(nc))
+    if r:
+        raise RuntimeError(f"oracle_align_rows failed: {r}")
+    return sc.value, fl.value, [int(v) for v in buf[:nc.value]]
+
+
 def levenshtein(read: bytes, target: bytes) -> int:
     return int(_load().oracle_levenshtein(bytes(read), len(read), bytes(target), len(target)))
 
 
 def align_batch(pairs, penalties, limits: np.ndarray, band: int = -1, cigar: bool = True, threads: int | None = None,
-                cigar_cap: np.ndarray | None = None):
-    """Align gen.Pairs on host threads.
+                cigar_cap: np.ndarray | None = None, rows_per_block: int | None = None):
+    """Align gen.Pairs on host threads (rows_per_block not None: the row-block form of align_rows, for long pairs).
 
     Returns (scores int32, flags uint8, cigar_off uint64[n+1], cigars uint32, cigar_lens uint32).
     """
@@ -239,9 +262,14 @@ def align_batch(pairs, penalties, limits: np.ndarray, band: int = -1, cigar: boo
     else:
         off = np.zeros(n + 1, np.uint64); cig = np.zeros(0, np.uint32); cp = op = None
     P = lambda a: ctypes.c_void_p(a.ctypes.data)
-    r = lib.oracle_align_batch(P(pairs.reads), P(pairs.read_off), P(pairs.read_len), P(pairs.targets),
-                               P(pairs.target_off), P(pairs.target_len), n, x, o, e, band, P(lim), P(scores),
-                               P(flags), cp, op, P(lens), threads)
+    if rows_per_block is None:
+        r = lib.oracle_align_batch(P(pairs.reads), P(pairs.read_off), P(pairs.read_len), P(pairs.targets),
+                                   P(pairs.target_off), P(pairs.target_len), n, x, o, e, band, P(lim), P(scores),
+                                   P(flags), cp, op, P(lens), threads)
+    else:
+        r = lib.oracle_align_rows_batch(P(pairs.reads), P(pairs.read_off), P(pairs.read_len), P(pairs.targets),
+                                        P(pairs.target_off), P(pairs.target_len), n, x, o, e, band, P(lim),
+                                        P(scores), P(flags), cp, op, P(lens), threads, int(rows_per_block))
     if r:
         raise RuntimeError(f"oracle_align_batch failed: {r}")
     return scores, flags, off, cig, lens

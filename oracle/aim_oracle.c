@@ -139,6 +139,130 @@ int oracle_align(const char *P, uint32_t n, const char *T, uint32_t m, int32_t x
     return 0;
 }
 
+/*
+ * The same alignment (same recurrences, same border, same band, same canonical
+ * backward greedy) for long pairs, with memory linear in m per block of rows
+ * instead of the whole (n+1) x (m+1) matrix: a 10 kbp pair needs 1.2 GB as a
+ * full matrix of three int32 tables, and about 30 MB here.
+ *
+ *   Forward: rows v = 0 .. n in order, each from the row above it exactly as
+ *   in oracle_align (two rows live); every row v with v % K == 0 is saved.
+ *   Traceback: the greedy reads the DP values of the cell it stands on, and its
+ *   rows only decrease.  The rows of the block [bK, bK + K - 1] holding the
+ *   current row are recomputed from the saved row bK by the same row step, so
+ *   each value read equals the full matrix's value.
+ *
+ * K = ceil(sqrt(n + 1)) when rows_per_block <= 0.  Pinned against oracle_align
+ * (scores, flags and CIGARs) on pairs up to 1 kbp, with several K.
+ */
+
+/* Row v of the three tables from row v-1 (ignored for v = 0), as in oracle_align. */
+static void row_step(const char *P, const char *T, uint32_t m, int32_t x, int32_t o, int32_t e, int32_t band,
+                     uint32_t v, const int32_t *pM, const int32_t *pI, const int32_t *pD, int32_t *cM, int32_t *cI,
+                     int32_t *cD) {
+    for (uint32_t h = 0; h <= m; ++h) {
+        int32_t Mv = INF, Iv = INF, Dv = INF;
+        int64_t k = (int64_t)h - (int64_t)v;
+        int inband = band < 0 || (k <= band && -k <= band);
+        if (inband) {
+            if (v == 0 && h == 0) {
+                Mv = 0;
+            } else {
+                if (v >= 1 && h >= 1) {
+                    int32_t d = (P[v - 1] == T[h - 1]) ? 0 : x;
+                    Mv = cap_inf(min3(pM[h - 1], pI[h - 1], pD[h - 1]) + d);
+                }
+                if (v >= 1) Iv = cap_inf(min3(pM[h] + o + e, pD[h] + o + e, pI[h] + e));
+                if (h >= 1) Dv = cap_inf(min3(cM[h - 1] + o + e, cI[h - 1] + o + e, cD[h - 1] + e));
+            }
+        }
+        cM[h] = Mv; cI[h] = Iv; cD[h] = Dv;
+    }
+}
+
+int oracle_align_rows(const char *P, uint32_t n, const char *T, uint32_t m, int32_t x, int32_t o, int32_t e,
+                      int32_t band, int64_t limit, int32_t rows_per_block, int32_t *score, uint8_t *flags,
+                      uint32_t *cigar, uint32_t cap, uint32_t *ncig) {
+    *score = -1; *flags = 0; *ncig = 0;
+    int64_t dnm = (int64_t)m - (int64_t)n;
+    if (band >= 0 && (dnm > band || -dnm > band)) { *flags = 1; return 0; }
+    uint32_t K = (uint32_t)(rows_per_block > 0 ? rows_per_block : 1);
+    if (rows_per_block <= 0) while ((uint64_t)K * K < (uint64_t)n + 1) ++K;
+    const size_t W = (size_t)m + 1, nck = (size_t)n / K + 1;
+    /* saved rows: ck[c] holds row c*K, tables M, I, D one after another */
+    int32_t *ck = (int32_t *)malloc(nck * 3 * W * sizeof(int32_t));
+    /* block rows: blk[r] holds row b*K + r */
+    int32_t *blk = (int32_t *)malloc((size_t)K * 3 * W * sizeof(int32_t));
+    int32_t *two = (int32_t *)malloc(2 * 3 * W * sizeof(int32_t));
+    char *ops = (char *)malloc((size_t)n + m + 1);
+    if (!ck || !blk || !two || !ops) { free(ck); free(blk); free(two); free(ops); return -3; }
+#define TAB(base, t) ((base) + (size_t)(t) * W)
+    int32_t *prev = two, *cur = two + 3 * W;
+    for (uint32_t v = 0; v <= n; ++v) {
+        row_step(P, T, m, x, o, e, band, v, TAB(prev, 0), TAB(prev, 1), TAB(prev, 2), TAB(cur, 0), TAB(cur, 1),
+                 TAB(cur, 2));
+        if (v % K == 0) memcpy(ck + (size_t)(v / K) * 3 * W, cur, 3 * W * sizeof(int32_t));
+        int32_t *t = prev; prev = cur; cur = t;
+    }
+    /* prev holds row n */
+    int32_t s = min3(TAB(prev, 0)[m], TAB(prev, 1)[m], TAB(prev, 2)[m]);
+    if (s >= INF || (int64_t)s > limit) {
+        *flags = 1;
+        free(ck); free(blk); free(two); free(ops);
+        return 0;
+    }
+    *score = s;
+    int64_t reqM = s, reqI = s, reqD = s;
+    uint32_t v = n, h = m, nops = 0;
+    int64_t have = -1;   /* block whose rows blk holds */
+    while (v > 0 || h > 0) {
+        const uint32_t b = v / K;
+        if ((int64_t)b != have) {
+            memcpy(blk, ck + (size_t)b * 3 * W, 3 * W * sizeof(int32_t));
+            for (uint32_t r = 1; r < K && b * K + r <= n; ++r) {
+                int32_t *pr = blk + (size_t)(r - 1) * 3 * W, *cr = blk + (size_t)r * 3 * W;
+                row_step(P, T, m, x, o, e, band, b * K + r, TAB(pr, 0), TAB(pr, 1), TAB(pr, 2), TAB(cr, 0),
+                         TAB(cr, 1), TAB(cr, 2));
+            }
+            have = b;
+        }
+        const int32_t *row = blk + (size_t)(v - b * K) * 3 * W;
+        int tM = reqM >= 0 && TAB(row, 0)[h] == reqM;
+        int tI = reqI >= 0 && TAB(row, 1)[h] == reqI;
+        int tD = reqD >= 0 && TAB(row, 2)[h] == reqD;
+        int match = (v > 0 && h > 0) && P[v - 1] == T[h - 1];
+        char op;
+        if (tM && v > 0 && h > 0 && !match) op = 'X';
+        else if (tI) op = 'I';
+        else if (tD) op = 'D';
+        else if (tM && match) op = 'M';
+        else { free(ck); free(blk); free(two); free(ops); return -5; /* cannot happen: no tight state */ }
+        ops[nops++] = op;
+        if (op == 'X' || op == 'M') {
+            int64_t c = reqM - (op == 'X' ? x : 0);
+            reqM = reqI = reqD = c; --v; --h;
+        } else if (op == 'I') {
+            int64_t c = reqI;
+            reqM = c - o - e; reqD = c - o - e; reqI = c - e; --v;
+        } else {
+            int64_t c = reqD;
+            reqM = c - o - e; reqI = c - o - e; reqD = c - e; --h;
+        }
+    }
+#undef TAB
+    uint32_t runs = 0;
+    for (int64_t i = (int64_t)nops - 1; i >= 0;) {
+        char op = ops[i]; uint32_t len = 0;
+        while (i >= 0 && ops[i] == op) { ++len; --i; }
+        if (cigar && runs < cap) cigar[runs] = (len << 4) | bam_code(op);
+        ++runs;
+    }
+    *ncig = runs;
+    if (cigar && runs > cap) *flags |= 2;
+    free(ck); free(blk); free(two); free(ops);
+    return 0;
+}
+
 /* Textbook one-state Levenshtein distance (two rows), an independent cross-check for the unit-cost case. */
 int32_t oracle_levenshtein(const char *P, uint32_t n, const char *T, uint32_t m) {
     int32_t *prev = (int32_t *)malloc(((size_t)m + 1) * sizeof(int32_t));
@@ -172,6 +296,7 @@ typedef struct {
     uint32_t *cigars; const uint64_t *cigar_off; uint32_t *cigar_lens;
     volatile int64_t next;
     volatile int err;
+    int32_t rows;                  /* 0: full matrix (oracle_align); else oracle_align_rows with this K (< 0: auto) */
 } batch_job;
 
 static void *batch_worker(void *arg) {
@@ -181,9 +306,13 @@ static void *batch_worker(void *arg) {
         if (i >= (int64_t)j->num_pairs) break;
         uint32_t *cig = NULL, cap = 0;
         if (j->cigars) { cig = j->cigars + j->cigar_off[i]; cap = (uint32_t)(j->cigar_off[i + 1] - j->cigar_off[i]); }
-        int r = oracle_align(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
-                             j->target_len[i], j->x, j->o, j->e, j->band, j->limit[i], &j->scores[i], &j->flags[i],
-                             cig, cap, &j->cigar_lens[i]);
+        int r = j->rows == 0
+                    ? oracle_align(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
+                                   j->target_len[i], j->x, j->o, j->e, j->band, j->limit[i], &j->scores[i],
+                                   &j->flags[i], cig, cap, &j->cigar_lens[i])
+                    : oracle_align_rows(j->reads + j->read_off[i], j->read_len[i], j->targets + j->target_off[i],
+                                        j->target_len[i], j->x, j->o, j->e, j->band, j->limit[i], j->rows,
+                                        &j->scores[i], &j->flags[i], cig, cap, &j->cigar_lens[i]);
         if (r) j->err = r;
     }
     return NULL;
@@ -193,12 +322,13 @@ static void *batch_worker(void *arg) {
  * Align num_pairs pairs on `threads` host threads.  cigars/cigar_off may be
  * NULL (scores only); cigar_off has num_pairs + 1 entries when given.
  */
-int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len, const char *targets,
-                       const uint64_t *target_off, const uint32_t *target_len, uint64_t num_pairs, int32_t x,
-                       int32_t o, int32_t e, int32_t band, const int64_t *limit, int32_t *scores, uint8_t *flags,
-                       uint32_t *cigars, const uint64_t *cigar_off, uint32_t *cigar_lens, int threads) {
+static int align_batch_mode(const char *reads, const uint64_t *read_off, const uint32_t *read_len,
+                            const char *targets, const uint64_t *target_off, const uint32_t *target_len,
+                            uint64_t num_pairs, int32_t x, int32_t o, int32_t e, int32_t band, const int64_t *limit,
+                            int32_t *scores, uint8_t *flags, uint32_t *cigars, const uint64_t *cigar_off,
+                            uint32_t *cigar_lens, int threads, int32_t rows) {
     batch_job j = {reads, targets, read_off, target_off, read_len, target_len, num_pairs, x, o, e, band, limit,
-                   scores, flags, cigars, cigar_off, cigar_lens, 0, 0};
+                   scores, flags, cigars, cigar_off, cigar_lens, 0, 0, rows};
     if (threads < 1) threads = 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
     if (!th) return -3;
@@ -209,6 +339,25 @@ int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32
     for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
     free(th);
     return j.err;
+}
+
+int oracle_align_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len, const char *targets,
+                       const uint64_t *target_off, const uint32_t *target_len, uint64_t num_pairs, int32_t x,
+                       int32_t o, int32_t e, int32_t band, const int64_t *limit, int32_t *scores, uint8_t *flags,
+                       uint32_t *cigars, const uint64_t *cigar_off, uint32_t *cigar_lens, int threads) {
+    return align_batch_mode(reads, read_off, read_len, targets, target_off, target_len, num_pairs, x, o, e, band,
+                            limit, scores, flags, cigars, cigar_off, cigar_lens, threads, 0);
+}
+
+/* As oracle_align_batch with oracle_align_rows (rows_per_block <= 0: K = ceil(sqrt(n + 1))). */
+int oracle_align_rows_batch(const char *reads, const uint64_t *read_off, const uint32_t *read_len,
+                            const char *targets, const uint64_t *target_off, const uint32_t *target_len,
+                            uint64_t num_pairs, int32_t x, int32_t o, int32_t e, int32_t band, const int64_t *limit,
+                            int32_t *scores, uint8_t *flags, uint32_t *cigars, const uint64_t *cigar_off,
+                            uint32_t *cigar_lens, int threads, int32_t rows_per_block) {
+    return align_batch_mode(reads, read_off, read_len, targets, target_off, target_len, num_pairs, x, o, e, band,
+                            limit, scores, flags, cigars, cigar_off, cigar_lens, threads,
+                            rows_per_block > 0 ? rows_per_block : -1);
 }
 
 /* ---------------------------------------------------------------------------

@@ -89,6 +89,10 @@ def _lib():
         lib.aim_stats_read.argtypes = [p, p]
         lib.aim_timing_enable.argtypes = [p, ctypes.c_int]
         lib.aim_timing_read.argtypes = [p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
+        lib.aim_align_batch_host.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.c_int,
+                                             ctypes.POINTER(aim_penalties_t), i32, p, p, p, p, p, p, u32, p]
+        lib.aim_measure_int_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double), p]
         _LIB = lib
     return _LIB
 
@@ -324,6 +328,50 @@ def aim_timing_read(ctx, kind: int) -> tuple[float, int]:
     ms = ctypes.c_double(); n = ctypes.c_int()
     _check(_lib().aim_timing_read(ctx, kind, ctypes.byref(ms), ctypes.byref(n)), "aim_timing_read")
     return ms.value, n.value
+
+
+def aim_align_batch_host(ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths, target_lengths,
+                         max_length, algo, pen, max_edits, max_edits_per_pair, out_scores, out_cigars, cigar_offsets,
+                         out_cigar_lens, out_flags, chunk_pairs: int = 0) -> tuple[int, int]:
+    """Host numpy arrays in, host numpy arrays out, transfers inside the call (see aim.h; pinned arrays, e.g.
+    torch.empty(..., pin_memory=True).numpy(), let the copies overlap the kernels).  Returns the bytes copied
+    (host-to-device, device-to-host)."""
+    import numpy as np
+    n = len(read_lengths)
+
+    def h(a, dt, name, optional=False, writable=False):
+        if a is None:
+            if optional:
+                return None
+            raise ValueError(f"{name} is required")
+        if not isinstance(a, np.ndarray) or not a.flags.c_contiguous or a.dtype.itemsize != np.dtype(dt).itemsize:
+            raise TypeError(f"{name} must be a C-contiguous numpy array of {np.dtype(dt)}")
+        if writable and not a.flags.writeable:
+            raise TypeError(f"{name} must be writable")
+        return ctypes.c_void_p(a.ctypes.data)
+    moved = np.zeros(2, np.uint64)
+    a = ALGO[algo] if isinstance(algo, str) else int(algo)
+    _check(_lib().aim_align_batch_host(
+        ctx, h(reads, np.uint8, "reads"), h(targets, np.uint8, "targets"),
+        h(read_char_offsets, np.uint64, "read_char_offsets"), h(target_char_offsets, np.uint64, "target_char_offsets"),
+        h(read_lengths, np.uint32, "read_lengths"), h(target_lengths, np.uint32, "target_lengths"),
+        ctypes.c_uint32(n), ctypes.c_uint32(max_length), ctypes.c_int(a), ctypes.byref(pen),
+        ctypes.c_int32(max_edits), h(max_edits_per_pair, np.int32, "max_edits_per_pair", True),
+        h(out_scores, np.int32, "out_scores", writable=True), h(out_cigars, np.uint32, "out_cigars", True, True),
+        h(cigar_offsets, np.uint64, "cigar_offsets", True), h(out_cigar_lens, np.uint32, "out_cigar_lens", True, True),
+        h(out_flags, np.uint8, "out_flags", writable=True), ctypes.c_uint32(chunk_pairs),
+        ctypes.c_void_p(moved.ctypes.data)), "aim_align_batch_host")
+    return int(moved[0]), int(moved[1])
+
+
+def aim_measure_int_peak(device: int = 0) -> tuple[float, float, list[float]]:
+    """(int32 operations per second, kernel ms, [add/max/xor rate, add/xor/shift rate]) of the library's ALU
+    microbenchmark on `device`."""
+    import numpy as np
+    ops = ctypes.c_double(); ms = ctypes.c_double(); mix = np.zeros(2, np.float64)
+    _check(_lib().aim_measure_int_peak(int(device), ctypes.byref(ops), ctypes.byref(ms),
+                                       ctypes.c_void_p(mix.ctypes.data)), "aim_measure_int_peak")
+    return ops.value, ms.value, mix.tolist()
 
 
 def _align_args(num_pairs, max_length, algo, pen, max_edits, max_edits_per_pair, out_scores, out_cigars,

@@ -271,6 +271,7 @@ struct aim_ctx {
     int genasm_w, genasm_o;       // GenASM window and overlap
     int batch_compact;            // batch plans: 0 tuner decides on compact first passes, 1 always, 2 never
     void* tune_cache;             // autotuner choices (owned; see batch.cu)
+    void* host_pipe;              // buffers, streams and plans of aim_align_batch_host (owned; see host.cu)
 };
 
 namespace aim {
@@ -291,6 +292,13 @@ int time_slot(aim_ctx* ctx, int kind);
 cudaEvent_t timing_start_event(aim_ctx* ctx, int kind, int slot);
 cudaEvent_t timing_stop_event(aim_ctx* ctx, int kind, int slot);
 void free_tune_cache(void* cache);
+void free_host_pipe(void* pipe);
+int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, const uint64_t* read_char_offsets,
+                    const uint64_t* target_char_offsets, const uint32_t* read_lengths, const uint32_t* target_lengths,
+                    uint32_t num_pairs, uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits,
+                    const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
+                    const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
+                    int autotune, uint8_t* ext_scratch, size_t ext_scratch_bytes, aim_batch** out);
 
 struct DeviceGuardImpl {
     int prev = -1;

@@ -269,6 +269,7 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     c->genasm_w = 64;
     c->genasm_o = 24;
     c->batch_compact = 0;
+    c->host_pipe = nullptr;
     *out = c;
     return AIM_OK;
 }
@@ -277,6 +278,7 @@ int aim_destroy(aim_ctx* ctx) {
     if (!ctx) return AIM_OK;
     DeviceGuard g(ctx->device);
     cudaError_t e = cudaDeviceSynchronize();
+    aim::free_host_pipe(ctx->host_pipe);
     cudaFree(ctx->ws);
     for (KernelTimes* t : ctx->times) {
         if (!t) continue;

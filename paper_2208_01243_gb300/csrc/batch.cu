@@ -377,15 +377,17 @@ void free_tune_cache(void* cache) { delete static_cast<std::map<TuneKey, TuneCho
 
 }  // namespace aim
 
-extern "C" {
+namespace aim {
 
-int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, const uint64_t* read_char_offsets,
-                   const uint64_t* target_char_offsets, const uint32_t* read_lengths, const uint32_t* target_lengths,
-                   uint32_t num_pairs, uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits,
-                   const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
-                   const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
-                   int autotune, aim_batch** out) {
-    using namespace aim;
+// aim_batch_plan, with the scratch optionally supplied by the caller (ext_scratch, ext_scratch_bytes) instead of
+// allocated with the plan: plans whose runs never overlap (the host-buffer pipeline's slots, which share one
+// compute stream) can then share one region.
+int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, const uint64_t* read_char_offsets,
+                    const uint64_t* target_char_offsets, const uint32_t* read_lengths, const uint32_t* target_lengths,
+                    uint32_t num_pairs, uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits,
+                    const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
+                    const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
+                    int autotune, uint8_t* ext_scratch, size_t ext_scratch_bytes, aim_batch** out) {
     if (!out) return AIM_ERR_ARG;
     *out = nullptr;
     if (!ctx || !pen || pen->match != 0 || pen->mismatch < 1 || pen->gap_open < 0 || pen->gap_extend < 1)
@@ -428,8 +430,8 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     const size_t flag_bytes = align_up(num_pairs, 256);
     const size_t small_bytes = align_up(10 * (kBuckets + 1) * sizeof(uint32_t), 256);
     const size_t order_bytes = align_up((size_t)num_pairs * sizeof(uint32_t), 256);
-    b->scratch_bytes = scratch_bytes ? scratch_bytes : ctx->ws_bytes;
-    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 2 * order_bytes + b->scratch_bytes;
+    b->scratch_bytes = ext_scratch ? ext_scratch_bytes : scratch_bytes ? scratch_bytes : ctx->ws_bytes;
+    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 2 * order_bytes + (ext_scratch ? 0 : b->scratch_bytes);
     cudaError_t e = cudaMalloc(&b->mem, b->mem_bytes);
     if (e != cudaSuccess) { cudaGetLastError(); free_batch(b); return AIM_ERR_NOMEM; }
     uint8_t* p = b->mem;
@@ -445,7 +447,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     b->gbounds = sm + 9 * (kBuckets + 1);
     b->order = reinterpret_cast<uint32_t*>(p); p += order_bytes;
     b->rorder = reinterpret_cast<uint32_t*>(p); p += order_bytes;
-    b->scratch = p;
+    b->scratch = ext_scratch ? ext_scratch : p;
     b->P = PairsView{b->pr, b->pt, nullptr, nullptr, read_lengths, target_lengths, b->br, b->bt, num_pairs, max_length};
     b->P.stride = b->stride;
     b->O = OutView{out_scores, out_cigars, cigar_offsets, out_cigar_lens, out_flags, stats_of(ctx)};
@@ -555,6 +557,22 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
     }
     *out = b;
     return AIM_OK;
+}
+
+}  // namespace aim
+
+extern "C" {
+
+int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, const uint64_t* read_char_offsets,
+                   const uint64_t* target_char_offsets, const uint32_t* read_lengths, const uint32_t* target_lengths,
+                   uint32_t num_pairs, uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits,
+                   const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
+                   const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
+                   int autotune, aim_batch** out) {
+    return aim::batch_plan_impl(ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths,
+                                target_lengths, num_pairs, max_length, pen, max_edits, max_edits_per_pair, out_scores,
+                                out_cigars, cigar_offsets, out_cigar_lens, out_flags, scratch_bytes, autotune, nullptr,
+                                0, out);
 }
 
 int aim_batch_run(aim_batch* b, aim_stream_t stream) {

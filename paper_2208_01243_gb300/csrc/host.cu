@@ -1,0 +1,314 @@
+// aim_align_batch_host: the whole batch from host memory to host memory in
+// one call, with the transfers inside it (the paper's timed region runs from
+// the parallel transfer of the pairs to the memory banks, through alignment
+// and traceback, to the transfer of scores and operations back: Section 2.2,
+// Steps 2-6, and Section 3.1).
+//
+// The batch is cut into chunks of C pairs, aligned through two device slots
+// in turn.  Each slot holds device copies of one chunk's inputs (ASCII bytes,
+// offsets rebased to the chunk, lengths, thresholds, CIGAR offsets) and
+// outputs.  A copy-in stream, a copy-out stream and one compute stream per
+// slot form the pipeline: while chunk j aligns in one slot, the copy-in
+// stream fills the other slot with chunk j + 1 and the copy-out stream
+// returns chunk j - 1's results, so the copy engines work beside the SMs, and
+// chunk j + 1's launches start while the last long pairs of chunk j finish.
+// Events order each slot's reuse: new inputs only once the slot's previous
+// alignment has read its inputs, and a new alignment only once the slot's
+// previous results have left.
+//
+// The wavefront algorithm runs in the batched form: each slot owns a batch
+// plan (bucketed queues, lanes per pair from the context's autotuner, CUDA
+// graph) bound to its buffers, planned on the first chunk it holds and then
+// replayed with each new chunk's contents; a short last chunk is padded with
+// empty pairs.  Each plan draws its scratch from its own half of the context
+// workspace, so the two slots' launches may overlap.  The other algorithms run
+// the plain ASCII form on each chunk; those share the workspace, so both slots
+// then use one compute stream.  Slots, streams and plans stay in the context
+// for later calls of the same shape.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "aim_internal.cuh"
+
+namespace aim {
+namespace {
+
+struct Slot {
+    // device copies of one chunk
+    uint8_t *reads, *targets;
+    uint64_t *roff, *toff, *coff;
+    uint32_t *rlen, *tlen, *lens, *cigars;
+    int32_t *me, *scores;
+    uint8_t* flags;
+    // pinned host staging of the chunk's metadata, copied in with one transfer:
+    // roff, toff, coff (C + 1) as uint64, then rlen, tlen, me as 32-bit words
+    uint8_t* stage;
+    aim_batch* plan;
+    cudaEvent_t in_done, comp_done, out_done;
+    bool used;
+};
+
+struct HostPipe {
+    // shape the slots were built for
+    int algo;
+    aim_penalties_t pen;
+    int32_t max_edits;
+    bool per_pair, cigars;
+    uint32_t max_length, chunk;
+    uint64_t read_cap, target_cap, cigar_cap;   // bytes, bytes, runs per slot
+    uint8_t* mem;
+    cudaStream_t h2d, d2h, comp[2];   // comp[1] == comp[0] when the slots share the workspace
+    Slot slot[2];
+};
+
+size_t meta_bytes(uint32_t C) { return (size_t)(3 * (size_t)C + 1) * 8 + 3 * (size_t)C * 4; }
+
+void destroy_pipe(HostPipe* hp) {
+    if (!hp) return;
+    for (cudaStream_t c : hp->comp)
+        if (c) cudaStreamSynchronize(c);
+    if (hp->h2d) cudaStreamSynchronize(hp->h2d);
+    if (hp->d2h) cudaStreamSynchronize(hp->d2h);
+    for (Slot& s : hp->slot) {
+        if (s.plan) aim_batch_destroy(s.plan);
+        if (s.stage) cudaFreeHost(s.stage);
+        if (s.in_done) cudaEventDestroy(s.in_done);
+        if (s.comp_done) cudaEventDestroy(s.comp_done);
+        if (s.out_done) cudaEventDestroy(s.out_done);
+    }
+    if (hp->h2d) cudaStreamDestroy(hp->h2d);
+    if (hp->comp[0]) cudaStreamDestroy(hp->comp[0]);
+    if (hp->comp[1] && hp->comp[1] != hp->comp[0]) cudaStreamDestroy(hp->comp[1]);
+    if (hp->d2h) cudaStreamDestroy(hp->d2h);
+    if (hp->mem) cudaFree(hp->mem);
+    delete hp;
+}
+
+bool same_shape(const HostPipe* hp, int algo, const aim_penalties_t* pen, int32_t max_edits, bool per_pair,
+                bool cigars, uint32_t max_length, uint32_t chunk, uint64_t rc, uint64_t tc, uint64_t cc) {
+    return hp && hp->algo == algo && std::memcmp(&hp->pen, pen, sizeof(*pen)) == 0 && hp->max_edits == max_edits &&
+           hp->per_pair == per_pair && hp->cigars == cigars && hp->max_length == max_length && hp->chunk == chunk &&
+           hp->read_cap >= rc && hp->target_cap >= tc && hp->cigar_cap >= cc;
+}
+
+HostPipe* make_pipe(int algo, const aim_penalties_t* pen, int32_t max_edits, bool per_pair, bool cigars,
+                    uint32_t max_length, uint32_t C, uint64_t rc, uint64_t tc, uint64_t cc, cudaError_t* err) {
+    HostPipe* hp = new (std::nothrow) HostPipe();
+    if (!hp) { *err = cudaErrorMemoryAllocation; return nullptr; }
+    std::memset(hp, 0, sizeof(*hp));
+    hp->algo = algo; hp->pen = *pen; hp->max_edits = max_edits; hp->per_pair = per_pair; hp->cigars = cigars;
+    hp->max_length = max_length; hp->chunk = C;
+    hp->read_cap = std::max<uint64_t>(rc, 1); hp->target_cap = std::max<uint64_t>(tc, 1);
+    hp->cigar_cap = std::max<uint64_t>(cc, 1);
+    const size_t a = 256;
+    const size_t per_slot = align_up(hp->read_cap, a) + align_up(hp->target_cap, a) +
+                            3 * align_up((size_t)C * 8 + 8, a) + 4 * align_up((size_t)C * 4, a) +
+                            align_up((size_t)C * 4, a) + align_up(C, a) + align_up(hp->cigar_cap * 4, a);
+    cudaError_t e = cudaMalloc(&hp->mem, 2 * per_slot);
+    uint8_t* p = hp->mem;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+        Slot& s = hp->slot[k];
+        s.reads = p; p += align_up(hp->read_cap, a);
+        s.targets = p; p += align_up(hp->target_cap, a);
+        s.roff = reinterpret_cast<uint64_t*>(p); p += align_up((size_t)C * 8 + 8, a);
+        s.toff = reinterpret_cast<uint64_t*>(p); p += align_up((size_t)C * 8 + 8, a);
+        s.coff = reinterpret_cast<uint64_t*>(p); p += align_up((size_t)C * 8 + 8, a);
+        s.rlen = reinterpret_cast<uint32_t*>(p); p += align_up((size_t)C * 4, a);
+        s.tlen = reinterpret_cast<uint32_t*>(p); p += align_up((size_t)C * 4, a);
+        s.me = reinterpret_cast<int32_t*>(p); p += align_up((size_t)C * 4, a);
+        s.lens = reinterpret_cast<uint32_t*>(p); p += align_up((size_t)C * 4, a);
+        s.scores = reinterpret_cast<int32_t*>(p); p += align_up((size_t)C * 4, a);
+        s.flags = p; p += align_up(C, a);
+        s.cigars = reinterpret_cast<uint32_t*>(p); p += align_up(hp->cigar_cap * 4, a);
+        e = cudaMallocHost(&s.stage, meta_bytes(C));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.comp_done, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.out_done, cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->comp[0], cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        if (algo == AIM_ALGO_WFA_AFFINE) e = cudaStreamCreateWithFlags(&hp->comp[1], cudaStreamNonBlocking);
+        else hp->comp[1] = hp->comp[0];
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&hp->d2h, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { cudaGetLastError(); destroy_pipe(hp); *err = e; return nullptr; }
+    *err = cudaSuccess;
+    return hp;
+}
+
+// byte range [lo, hi) holding sequences [c0, c1) of a host layout
+void byte_range(const uint64_t* off, const uint32_t* len, uint32_t c0, uint32_t c1, uint64_t* lo, uint64_t* hi) {
+    uint64_t l = UINT64_MAX, h = 0;
+    for (uint32_t i = c0; i < c1; ++i) {
+        l = std::min<uint64_t>(l, off[i]);
+        h = std::max<uint64_t>(h, off[i] + len[i]);
+    }
+    if (l > h) l = h = 0;
+    *lo = l; *hi = h;
+}
+
+}  // namespace
+
+void free_host_pipe(void* pipe) { destroy_pipe(static_cast<HostPipe*>(pipe)); }
+
+}  // namespace aim
+
+extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets,
+                                    const uint64_t* read_char_offsets, const uint64_t* target_char_offsets,
+                                    const uint32_t* read_lengths, const uint32_t* target_lengths, uint32_t num_pairs,
+                                    uint32_t max_length, int algo, const aim_penalties_t* pen, int32_t max_edits,
+                                    const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
+                                    const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags,
+                                    uint32_t chunk_pairs, uint64_t* bytes_moved) {
+    using namespace aim;
+    if (bytes_moved) bytes_moved[0] = bytes_moved[1] = 0;
+    if (!ctx || !pen || algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_GENASM) return AIM_ERR_ARG;
+    if (num_pairs == 0) return AIM_OK;
+    if (!reads || !targets || !read_char_offsets || !target_char_offsets || !read_lengths || !target_lengths ||
+        !out_scores || !out_flags || ((out_cigars == nullptr) != (cigar_offsets == nullptr)))
+        return AIM_ERR_ARG;
+    if (max_edits_per_pair && max_edits < 0) return AIM_ERR_ARG;
+    for (uint32_t i = 0; cigar_offsets && i < num_pairs; ++i)
+        if (cigar_offsets[i + 1] < cigar_offsets[i]) return AIM_ERR_ARG;   // capacities are differences
+    DeviceGuardImpl guard(ctx->device);
+    if (!guard.ok) return AIM_ERR_CUDA;
+
+    // chunks: C pairs (default: an eighth of the batch, at least 65,536 pairs), and the largest byte and run
+    // ranges any chunk needs
+    uint32_t C = chunk_pairs ? chunk_pairs : std::max<uint32_t>((num_pairs + 7) / 8, 65536u);
+    C = std::min(C, num_pairs);
+    const uint32_t nchunks = (num_pairs + C - 1) / C;
+    uint64_t rc = 0, tc = 0, cc = 0;
+    for (uint32_t j = 0; j < nchunks; ++j) {
+        const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C);
+        uint64_t lo, hi;
+        byte_range(read_char_offsets, read_lengths, c0, c1, &lo, &hi);
+        rc = std::max(rc, hi - lo);
+        byte_range(target_char_offsets, target_lengths, c0, c1, &lo, &hi);
+        tc = std::max(tc, hi - lo);
+        if (cigar_offsets) cc = std::max(cc, cigar_offsets[c1] - cigar_offsets[c0]);
+    }
+    const bool wfa_batched = algo == AIM_ALGO_WFA_AFFINE;
+    HostPipe* hp = static_cast<HostPipe*>(ctx->host_pipe);
+    if (!same_shape(hp, algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C,
+                    rc, tc, cc)) {
+        destroy_pipe(hp);
+        ctx->host_pipe = nullptr;
+        cudaError_t e;
+        hp = make_pipe(algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C, rc,
+                       tc, cc, &e);
+        if (!hp) return e == cudaErrorMemoryAllocation ? AIM_ERR_NOMEM : cuda_status(e);
+        ctx->host_pipe = hp;
+    }
+
+    uint64_t h2d = 0, d2h = 0;
+    cudaError_t e = cudaSuccess;
+    int rc_status = AIM_OK;
+    for (uint32_t j = 0; j < nchunks && e == cudaSuccess && rc_status == AIM_OK; ++j) {
+        Slot& s = hp->slot[j & 1];
+        cudaStream_t comp = hp->comp[j & 1];
+        const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C), k = c1 - c0;
+        // the slot's staging was read by its previous copy-in
+        if (s.used) e = cudaEventSynchronize(s.in_done);
+        if (e != cudaSuccess) break;
+        uint64_t rlo, rhi, tlo, thi;
+        byte_range(read_char_offsets, read_lengths, c0, c1, &rlo, &rhi);
+        byte_range(target_char_offsets, target_lengths, c0, c1, &tlo, &thi);
+        // metadata rebased to the chunk; padding (a short last chunk in the batched form) as empty pairs
+        uint64_t* m_roff = reinterpret_cast<uint64_t*>(s.stage);
+        uint64_t* m_toff = m_roff + C;
+        uint64_t* m_coff = m_toff + C;
+        uint32_t* m_rlen = reinterpret_cast<uint32_t*>(m_coff + C + 1);
+        uint32_t* m_tlen = m_rlen + C;
+        int32_t* m_me = reinterpret_cast<int32_t*>(m_tlen + C);
+        const uint64_t cbase = cigar_offsets ? cigar_offsets[c0] : 0;
+        for (uint32_t i = 0; i < k; ++i) {
+            m_roff[i] = read_char_offsets[c0 + i] - rlo;
+            m_toff[i] = target_char_offsets[c0 + i] - tlo;
+            m_rlen[i] = read_lengths[c0 + i];
+            m_tlen[i] = target_lengths[c0 + i];
+            m_me[i] = max_edits_per_pair ? max_edits_per_pair[c0 + i] : 0;
+            m_coff[i] = cigar_offsets ? cigar_offsets[c0 + i] - cbase : 0;
+        }
+        const uint64_t cend = cigar_offsets ? cigar_offsets[c1] - cbase : 0;
+        const uint32_t padded = wfa_batched ? C : k;
+        for (uint32_t i = k; i < padded; ++i) {
+            m_roff[i] = m_toff[i] = 0;
+            m_rlen[i] = m_tlen[i] = 0;
+            m_me[i] = 0;
+            m_coff[i] = cend;
+        }
+        m_coff[padded] = cend;
+        // copy in, once the slot's previous alignment has read its inputs
+        if (s.used) e = cudaStreamWaitEvent(hp->h2d, s.comp_done, 0);
+        auto in = [&](void* dst, const void* src, size_t bytes) {
+            if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, hp->h2d);
+            h2d += bytes;
+        };
+        in(s.reads, reads + rlo, rhi - rlo);
+        in(s.targets, targets + tlo, thi - tlo);
+        in(s.roff, m_roff, (size_t)padded * 8);
+        in(s.toff, m_toff, (size_t)padded * 8);
+        if (cigar_offsets) in(s.coff, m_coff, ((size_t)padded + 1) * 8);
+        in(s.rlen, m_rlen, (size_t)padded * 4);
+        in(s.tlen, m_tlen, (size_t)padded * 4);
+        if (max_edits_per_pair) in(s.me, m_me, (size_t)padded * 4);
+        if (e == cudaSuccess) e = cudaEventRecord(s.in_done, hp->h2d);
+        if (e != cudaSuccess) break;
+        // align, once the inputs are in and the slot's previous results have left
+        e = cudaStreamWaitEvent(comp, s.in_done, 0);
+        if (e == cudaSuccess && s.used) e = cudaStreamWaitEvent(comp, s.out_done, 0);
+        if (e != cudaSuccess) break;
+        // runs past each pair's count read as zero in the host buffer, as with the device entry points
+        if (cigar_offsets && cend) e = cudaMemsetAsync(s.cigars, 0, cend * 4, comp);
+        if (e != cudaSuccess) break;
+        if (wfa_batched) {
+            if (!s.plan) {
+                // planned on the chunk it first holds (planning packs and buckets the bound inputs); the second
+                // slot's plan takes the lanes the first one tuned from the context's cache.  Each slot's plan
+                // has its own half of the workspace as scratch.
+                e = cudaEventSynchronize(s.in_done);
+                if (e != cudaSuccess) break;
+                const size_t half = ((ctx->ws_bytes - kHeaderBytes) / 2) & ~(size_t)255;
+                rc_status = batch_plan_impl(ctx, s.reads, s.targets, s.roff, s.toff, s.rlen, s.tlen, C, max_length,
+                                            pen, max_edits, max_edits_per_pair ? s.me : nullptr, s.scores,
+                                            cigar_offsets ? s.cigars : nullptr, cigar_offsets ? s.coff : nullptr,
+                                            s.lens, s.flags, 0, (j & 1) == 0 ? 1 : 0,
+                                            ctx->ws + kHeaderBytes + (j & 1) * half, half, &s.plan);
+                if (rc_status != AIM_OK) break;
+            }
+            rc_status = aim_batch_run(s.plan, comp);
+        } else {
+            rc_status = aim_align_batch_ascii(ctx, s.reads, s.targets, s.roff, s.toff, s.rlen, s.tlen, k, max_length,
+                                              algo, pen, max_edits, max_edits_per_pair ? s.me : nullptr, s.scores,
+                                              cigar_offsets ? s.cigars : nullptr, cigar_offsets ? s.coff : nullptr,
+                                              s.lens, s.flags, comp);
+        }
+        if (rc_status != AIM_OK) break;
+        e = cudaEventRecord(s.comp_done, comp);
+        // copy out, once aligned
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(hp->d2h, s.comp_done, 0);
+        auto out = [&](void* dst, const void* src, size_t bytes) {
+            if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, hp->d2h);
+            d2h += bytes;
+        };
+        out(out_scores + c0, s.scores, (size_t)k * 4);
+        out(out_flags + c0, s.flags, k);
+        if (out_cigar_lens) out(out_cigar_lens + c0, s.lens, (size_t)k * 4);
+        if (cigar_offsets) out(out_cigars + cbase, s.cigars, cend * 4);
+        if (e == cudaSuccess) e = cudaEventRecord(s.out_done, hp->d2h);
+        s.used = true;
+    }
+    // every result in host memory before returning (also after an error, so no copy outlives the call)
+    const cudaError_t e1 = cudaStreamSynchronize(hp->h2d);
+    cudaError_t e2 = cudaStreamSynchronize(hp->comp[0]);
+    if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(hp->comp[1]);
+    const cudaError_t e3 = cudaStreamSynchronize(hp->d2h);
+    if (bytes_moved) { bytes_moved[0] = h2d; bytes_moved[1] = d2h; }
+    if (rc_status != AIM_OK) return rc_status;
+    if (e == cudaSuccess) e = e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3;
+    return cuda_status(e);
+}

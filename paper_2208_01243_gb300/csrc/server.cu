@@ -276,6 +276,9 @@ int launch_request(aim_server* s, Request* r) {
     std::memcpy(h + L.order, r->order.data(), r->n * 4);
     cudaStream_t st = r->stream;
     cudaError_t e = cudaMemcpyAsync(d, h, L.in_bytes, cudaMemcpyHostToDevice, st);
+    // the whole CIGAR region is copied back: runs past each pair's count read as zero, not as an earlier request's
+    if (e == cudaSuccess && r->out_cigars && r->cigar_total)
+        e = cudaMemsetAsync(d + L.cigars, 0, r->cigar_total * 4, st);
     if (e == cudaSuccess)
         e = launch_pack(d + L.reads, reinterpret_cast<const uint64_t*>(d + L.roff),
                         reinterpret_cast<const uint32_t*>(d + L.rl), r->n, reinterpret_cast<uint64_t*>(d + L.packed_r),

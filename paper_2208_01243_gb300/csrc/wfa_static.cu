@@ -15,7 +15,12 @@
 //
 // Host code cannot use the array's name as a device address, so on the first
 // call on each device (that device current) the array's address is looked up
-// with cudaGetSymbolAddress and cached.
+// with cudaGetSymbolAddress and cached.  A context reset (cudaDeviceReset) or
+// another context on the device loads the module again, possibly at another
+// address, so every later call that is not being captured into a graph looks
+// the address up again (a cheap host-side lookup once the module is loaded);
+// a call made during stream capture uses the address of the last call made
+// outside capture.
 #include <algorithm>
 #include <cstdint>
 #include <mutex>
@@ -36,14 +41,22 @@ int g_num_sms[kMaxDevices];
 
 int static_status(cudaError_t e) { return e == cudaSuccess ? AIM_OK : AIM_ERR_CUDA; }
 
-// Device address of the static scratch on the current device (looked up once per device).
-int scratch_for_current_device(uint8_t** addr, int* sms) {
+// Device address of the static scratch on the current device: looked up on the first call on the device and
+// again on every call whose stream is not capturing (so a reset context is never addressed through a stale
+// pointer); during capture, the address of the last lookup.
+int scratch_for_current_device(cudaStream_t st, uint8_t** addr, int* sms) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return static_status(e);
     if (dev < 0 || dev >= kMaxDevices) return AIM_ERR_UNSUPPORTED;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) {          // e.g. the legacy stream queried while another stream captures
+        cudaGetLastError();
+        cap = cudaStreamCaptureStatusActive;
+    }
     std::lock_guard<std::mutex> lock(g_lookup_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_wfa_static_scratch);
         if (e != cudaSuccess || p == nullptr) return AIM_ERR_CUDA;
@@ -103,7 +116,7 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
 
     uint8_t* base = nullptr;
     int sms = 0;
-    int rc = scratch_for_current_device(&base, &sms);
+    int rc = scratch_for_current_device((cudaStream_t)stream, &base, &sms);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     uint32_t* counter = reinterpret_cast<uint32_t*>(base);

@@ -88,3 +88,55 @@ def assert_same(dev, orc, idx=None, what=""):
         raise AssertionError(f"{what}: {len(bad)} pairs differ; first pair {i}: device score {ds[i]} flags {df[i]} "
                              f"runs {list(druns[i])[:12]} vs oracle score {os_[j]} flags {of[j]} "
                              f"runs {list(oruns[j])[:12]}")
+
+
+def runs_capacity(penalties, max_edits: np.ndarray, unit: bool = False) -> np.ndarray:
+    """CIGAR runs an accepted pair can need: every edit run costs at least min(x, o+e), so a pair under the limit
+    L = max_edits * max(x, o+e) has at most 2 * (L // min(x, o+e)) + 1 runs (unit costs: 2 * max_edits + 1)."""
+    me = np.asarray(max_edits, np.int64)
+    if unit:
+        return 2 * me + 1
+    _, x, o, e = penalties
+    return 2 * ((me * max(x, o + e)) // min(x, o + e)) + 1
+
+
+def device_flat(p: gen.Pairs, algo: str, penalties, max_edits: int, cap: np.ndarray, per_pair=None, band: int = -1,
+                aligner=None):
+    """The CUDA path over all pairs with one flat CIGAR array (pair i's runs at off[i], capacity cap[i]) ->
+    (scores, flags, lens, cigars, off), zero past each pair's runs."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    n = len(p)
+    ml = int(max(int(p.read_len.max(initial=0)), int(p.target_len.max(initial=0)), 1))
+    off = np.zeros(n + 1, np.int64); off[1:] = np.cumsum(cap)
+    reads, targets, ro, to, rl, tl, coff = aim.upload(p.reads, p.targets, p.read_off, p.target_off, p.read_len,
+                                                      p.target_len, off)
+    dev = rl.device
+    scores = torch.full((n,), -7, dtype=torch.int32, device=dev)
+    flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
+    lens = torch.zeros(n, dtype=torch.int32, device=dev)
+    cig = torch.zeros(max(int(off[-1]), 1), dtype=torch.int32, device=dev)
+    pp = aim.upload(per_pair.astype(np.int32))[0] if per_pair is not None else None
+    aim.aim_align_batch_ascii(aligner.ctx, reads, targets, ro, to, rl, tl, ml, algo,
+                              aim.penalties(penalties[1], penalties[2], penalties[3], band=band), max_edits, pp,
+                              scores, cig, coff, lens, flags)
+    torch.cuda.synchronize()
+    return (scores.cpu().numpy(), flags.cpu().numpy(), lens.cpu().numpy().view(np.uint32),
+            cig.cpu().numpy().view(np.uint32)[:int(off[-1])], off)
+
+
+def assert_flat_same(dev, orc, what=""):
+    """Element by element: scores, flags, run counts and every CIGAR run (both sides zero past each pair's runs)."""
+    ds, df, dl, dc, doff = dev
+    os_, of, ooff, oc, ol = orc
+    assert np.array_equal(np.asarray(doff, np.int64), np.asarray(ooff, np.int64)), f"{what}: CIGAR offsets differ"
+    bad = np.nonzero((ds != os_) | (df != of) | (dl != ol))[0]
+    if len(bad) == 0 and not np.array_equal(dc, oc):
+        pos = int(np.nonzero(dc != oc)[0][0])
+        bad = np.array([int(np.searchsorted(np.asarray(ooff, np.int64), pos, side="right") - 1)])
+    if len(bad):
+        i = int(bad[0])
+        a, b = int(ooff[i]), int(ooff[i + 1])
+        raise AssertionError(f"{what}: {len(bad)} pair(s) differ; first pair {i}: device ({ds[i]}, {df[i]}, "
+                             f"{dl[i]} runs {list(dc[a:a + 8])}) oracle ({os_[i]}, {of[i]}, {ol[i]} runs "
+                             f"{list(oc[a:a + 8])})")

@@ -7,7 +7,9 @@ start-up) use aim_wfa_align_static, which runs the same wavefront kernel on a
 fixed scratch array inside the library.  Two calls in a row, on different
 batches, must give exactly what the context-based entry point gives: the
 shared scratch keeps the previous call's contents, so the second call checks
-that nothing leaks from one call into the next.  This file is collected last.
+that nothing leaks from one call into the next.  The second call runs on a
+non-default stream, and the device's free memory and torch's allocation count
+must be the same before and after it.  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -61,15 +63,22 @@ def test_static_scratch_entry_point_matches_context_entry_point():
     pu = gen.generate(gen.WFA_UNEVEN, 701)
     me = gen.per_pair_max_edits(gen.WFA_UNEVEN, pu)
     batches.append((pu, int(me.max()), me))
+    side = torch.cuda.Stream()
     for call, (p, max_edits, per_pair) in enumerate(batches):       # two calls in a row
         b = _device_batch(aim, al, p, per_pair)
         ref, got = _outputs(b), _outputs(b)
         aim.aim_align_batch(al.ctx, b["pr"], b["pt"], b["wro"], b["wto"], b["rl"], b["tl"], b["max_len"], "wfa", pen,
                             max_edits, b["pp"], ref["scores"], ref["cigars"], b["coff"], ref["lens"], ref["flags"])
+        torch.cuda.synchronize()
+        free0, allocated0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        # the first call on the default stream, the second on another stream
+        stream = None if call == 0 else side
         aim.aim_wfa_align_static(b["pr"], b["pt"], b["wro"], b["wto"], b["rl"], b["tl"], b["max_len"], pen,
                                  max_edits, b["pp"], got["scores"], got["cigars"], b["coff"], got["lens"],
-                                 got["flags"])
+                                 got["flags"], stream=stream)
         torch.cuda.synchronize()
+        if call > 0:          # after the first call (module loaded, address looked up) nothing is allocated
+            assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == allocated0
         for k in ref:
             assert torch.equal(ref[k], got[k]), f"call {call}: {k} differs"
         assert int((ref["flags"] == 0).sum()) > 0
