@@ -11,7 +11,10 @@ namespace aim {
 constexpr int kWarp = 32;
 constexpr int16_t kNeg16 = -16384;           // invalid wavefront offset (any value < 0 is invalid)
 constexpr int32_t kInf = 1 << 28;            // DP infinity
-constexpr uint32_t kMaxWfaLength = 32000;    // offsets are stored as int16
+constexpr uint32_t kMaxWfaLength16 = 32000;  // the 8-byte wavefront entries store offsets as int16
+constexpr uint32_t kMaxWfaLength16c = 16382; // the 16-bit compact history stores h + 1 in 14 bits
+constexpr uint32_t kCompactMinLength = 2048; // reads longer than this use a compact history (exact, >= 32 lanes)
+constexpr uint32_t kMaxWfaLength = 1u << 20; // the wavefront algorithms' length limit (32-bit compact history)
 constexpr int kMaxDpBand = 127;              // DP kernels: 2*band+1 diagonals over R <= 4 lane blocks
 
 // BAM CIGAR op codes
@@ -118,11 +121,13 @@ struct WfaPlan {
     int x, oe, e;        // scaled mismatch, open+extend, extend
     int64_t smax;        // largest scaled score any pair may reach
     int band;            // < 0: none
-    size_t hist_elems;   // int16 elements of wavefront history per pair (worst case; kEntryElems per entry)
+    uint32_t max_length; // longest read or target of the call
+    size_t hist_entries; // wavefront history entries (score, diagonal) per pair, worst case
+    uint32_t live_w;     // compact forms: entries per live-ring slot (a power of 2 above the widest wavefront)
+    uint32_t live_slots; // compact forms: live-ring slots (a power of 2 above the farthest source score)
     int runs_cap;        // CIGAR runs staged per pair
     size_t meta_bytes;   // per-score (lo, hi, base, width) records, int4 each
     size_t runs_bytes;   // run staging
-    size_t group_bytes;  // scratch of one pair in flight: meta + runs + history
     int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
     int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end
     int retry_only;      // launch aligns only the pairs a previous pass flagged AIM_F_STEP_CAP
@@ -130,11 +135,18 @@ struct WfaPlan {
 // the plan with its history sized for wavefronts at most `width` diagonals wide (a compact first pass)
 WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width);
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
-size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax);
-// lanes per pair suited to the widest wavefront the plan allows (4, 8, 16, 32 or 256; 1 and 2 are valid too)
+size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax);
+// lanes per pair suited to the widest wavefront the plan allows (4, 8, 16, 32 or 256; 1 and 2 are valid too;
+// at least 32 beyond kMaxWfaLength16)
 int wfa_default_group(const WfaPlan& p, uint32_t max_length);
+// storage form of a launch with `group` lanes per pair: 0 8-byte entries, 1 16-bit compact, 2 32-bit compact
+int wfa_format(const WfaPlan& p, int group);
+size_t wfa_live_bytes(const WfaPlan& p, int fmt);
+// scratch one pair may need with `group` lanes per pair (its history sized for p.hist_entries, or `entries`)
+size_t wfa_pair_bytes(const WfaPlan& p, int group);
+size_t wfa_pair_bytes_capped(const WfaPlan& p, int group, size_t entries);
 // scratch per warp for `group` lanes per pair (256: the block's 8 warps share one pair's scratch)
-size_t wfa_warp_bytes(int group, size_t group_bytes);
+size_t wfa_warp_bytes(int group, size_t pair_bytes);
 
 struct WfaArgs {
     int X, OE, E, g;
@@ -153,6 +165,8 @@ struct WfaArgs {
     uint32_t seq_slot_words;   // words per sequence copy in shared memory (0: the extend reads global memory)
     uint32_t meta_ring;        // records per group in a shared-memory ring of recent scores (power of 2; 0: none)
     uint32_t ring_off;         // byte offset of the rings in dynamic shared memory (after the sequence copies)
+    uint32_t live_w, live_slots;   // compact histories: live-ring slot width and slot count (powers of 2)
+    size_t live_bytes;             // compact histories: bytes of a pair's live ring (at the end of its region)
     const uint32_t* order;     // pair index at each queue position, or null (identity)
     const uint32_t* bounds;    // bucket b covers queue positions [bounds[b], bounds[b+1]); null: one bucket of all
     uint32_t* counters;        // one claim counter per bucket, zero at launch

@@ -144,12 +144,16 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
                                  counter, ctx->num_sms, st, &warps);
     } else if (algo == AIM_ALGO_WFA_AFFINE || algo == AIM_ALGO_WFA_ADAPTIVE) {
         if (P.max_length > aim::kMaxWfaLength) return AIM_ERR_UNSUPPORTED;
+        // WFA-adaptive keeps 8-byte wavefront entries (int16 offsets)
+        if (algo == AIM_ALGO_WFA_ADAPTIVE && P.max_length > aim::kMaxWfaLength16) return AIM_ERR_UNSUPPORTED;
         aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, P.max_length, r.max_limit);
-        // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits
+        // launches use whole blocks of 8 warps: widen the groups until 8 warps' scratch fits (and to 32 lanes
+        // for reads beyond the 8-byte entries' int16 offsets)
         auto fit_group = [&](const aim::WfaPlan& pl, int g0) {
-            int g = g0;
-            while (g <= 32 && 8 * aim::wfa_warp_bytes(g, pl.group_bytes) > scratch_bytes) g = g == 32 ? 256 : g * 2;
-            return 8 * aim::wfa_warp_bytes(g, pl.group_bytes) > scratch_bytes ? 0 : g;
+            int g = P.max_length > aim::kMaxWfaLength16 ? std::max(g0, 32) : g0;
+            while (g <= 32 && 8 * aim::wfa_warp_bytes(g, aim::wfa_pair_bytes(pl, g)) > scratch_bytes)
+                g = g == 32 ? 256 : g * 2;
+            return 8 * aim::wfa_warp_bytes(g, aim::wfa_pair_bytes(pl, g)) > scratch_bytes ? 0 : g;
         };
         if (algo == AIM_ALGO_WFA_ADAPTIVE) {
             plan.adapt_min_len = ctx->adapt_min_len;

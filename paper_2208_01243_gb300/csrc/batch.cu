@@ -139,34 +139,35 @@ __global__ void __launch_bounds__(256) bucket_scatter_kernel(PairsView P, LimitV
 // scratch one pair of bucket b can need (bounds of its classes, capped by the plan's worst case)
 // (every wavefront of a pair in width class wc is at most 64/128/256 diagonals wide, and a
 // pair in work class kc computes fewer than 2^(3(kc+1)) entries per component)
-size_t bucket_group_bytes(const WfaPlan& plan, int b, uint32_t max_length) {
+size_t bucket_pair_bytes(const WfaPlan& plan, int b, int G) {
     const int kc = kWorkClasses - 1 - b / kWidthClasses;
     const int wc = kWidthClasses - 1 - b % kWidthClasses;
-    size_t hist = plan.hist_elems;
+    size_t hist = plan.hist_entries;
     if (kc < kWorkClasses - 1) {
         const size_t cmax = ((size_t)1 << (3 * (kc + 1))) - 1;
-        hist = std::min(hist, kEntryElems * (cmax + 1));
+        hist = std::min(hist, cmax + 1);
     }
     if (wc < kWidthClasses - 1) {
         const size_t wmax = (size_t)64 << wc;
-        hist = std::min(hist, kEntryElems * (((size_t)plan.smax + 1) * wmax + 1));
+        hist = std::min(hist, ((size_t)plan.smax + 1) * wmax + 1);
     }
-    (void)max_length;
-    return align_up(plan.meta_bytes + plan.runs_bytes + hist * sizeof(int16_t), 16);
+    return wfa_pair_bytes_capped(plan, G, hist);
 }
 
 constexpr int kCompactDiagonalsPerLane = 16;   // first-pass history: wavefronts of about 16 diagonals per lane
 
 // scratch one pair of bucket b gets in a compact first pass with G lanes per pair
-size_t bucket_compact_bytes(const WfaPlan& plan, int b, int G, uint32_t max_length) {
-    const size_t full = bucket_group_bytes(plan, b, max_length);
-    const size_t compact = wfa_plan_compact(plan, (int64_t)kCompactDiagonalsPerLane * G).group_bytes;
+size_t bucket_compact_bytes(const WfaPlan& plan, int b, int G) {
+    const size_t full = bucket_pair_bytes(plan, b, G);
+    const size_t compact = wfa_pair_bytes(wfa_plan_compact(plan, (int64_t)kCompactDiagonalsPerLane * G), G);
     return std::min(full, compact);
 }
 
-int default_group_for_bucket(int b) {
+// reads beyond the 8-byte entries' int16 offsets need at least 32 lanes per pair (a compact history)
+int default_group_for_bucket(int b, uint32_t max_length) {
     const int wc = kWidthClasses - 1 - b % kWidthClasses;
-    return wc == 0 ? 4 : wc == 1 ? 8 : wc == 2 ? 16 : 32;
+    const int g = wc == 0 ? 4 : wc == 1 ? 8 : wc == 2 ? 16 : 32;
+    return max_length > kMaxWfaLength16 ? std::max(g, 32) : g;
 }
 
 }  // namespace
@@ -296,8 +297,9 @@ cudaError_t trial(aim_batch* b, const WfaPlan& plan, const uint32_t tb[2], int G
 // a compact first pass with G1 lanes for bucket k: it must save scratch, use no more lanes than the full pass,
 // and fit the device several times over
 bool compact_allowed(const aim_batch* b, int k, int G1, int g_full) {
-    const size_t full = bucket_group_bytes(b->plan, k, b->max_length);
-    const size_t need = bucket_compact_bytes(b->plan, k, G1, b->max_length);
+    if (b->max_length > kMaxWfaLength16 && G1 < 32) return false;
+    const size_t full = bucket_pair_bytes(b->plan, k, g_full);
+    const size_t need = bucket_compact_bytes(b->plan, k, G1);
     if (need >= full || G1 > g_full) return false;
     const size_t min_warps = (size_t)b->ctx->num_sms * 8;
     return wfa_warp_bytes(G1, need) * min_warps <= b->scratch_bytes &&
@@ -319,7 +321,6 @@ int autotune(aim_batch* b) {
         // latency of a handful of pairs
         const uint32_t sample = std::min<uint32_t>(count, (uint32_t)std::max<size_t>(4096, 16 * min_warps * 4));
         const uint32_t tb[2] = {bounds[k], bounds[k] + sample};
-        const size_t full = bucket_group_bytes(b->plan, k, b->max_length);
         float best = 1e30f;
         int best_g = b->groups[k];
         // lanes per pair worth trying for this width class: at most ~64 diagonals per lane and score step
@@ -327,8 +328,8 @@ int autotune(aim_batch* b) {
         const int gmin = wc == 0 ? 1 : wc == 1 ? 2 : wc == 2 ? 4 : 8;
         const int gmax = wc == 0 ? 8 : wc == 1 ? 16 : wc == 2 ? 32 : 256;
         for (int G : kCandidates) {
-            if (G < gmin || G > gmax) continue;
-            const size_t wb = wfa_warp_bytes(G, full);
+            if (G < gmin || G > gmax || (b->max_length > kMaxWfaLength16 && G < 32)) continue;
+            const size_t wb = wfa_warp_bytes(G, bucket_pair_bytes(b->plan, k, G));
             if (wb * min_warps > b->scratch_bytes) continue;
             float ms = 0.f;
             for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) e = trial(b, b->plan, tb, G, wb, t0, t1, &ms);
@@ -337,10 +338,10 @@ int autotune(aim_batch* b) {
         // compact first pass with fewer lanes, then the full-scratch pass over the pairs that outgrew it
         int best_g1 = 0;
         if (b->ctx->batch_compact != 2) {
-            const size_t wb_full = wfa_warp_bytes(best_g, full);
+            const size_t wb_full = wfa_warp_bytes(best_g, bucket_pair_bytes(b->plan, k, best_g));
             for (int G1 : {4, 8, 16, 32}) {
                 if (!compact_allowed(b, k, G1, best_g)) continue;
-                const size_t wb = wfa_warp_bytes(G1, bucket_compact_bytes(b->plan, k, G1, b->max_length));
+                const size_t wb = wfa_warp_bytes(G1, bucket_compact_bytes(b->plan, k, G1));
                 if (b->ctx->batch_compact == 1) { best_g1 = G1; break; }   // forced: the fewest lanes that fit
                 float ms1 = 0.f, ms2 = 0.f;
                 for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -417,7 +418,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
 
     // groups: cached choice, else the width-class default in one pass
     for (int k = 0; k < kBuckets; ++k) {
-        b->groups[k] = default_group_for_bucket(k);
+        b->groups[k] = default_group_for_bucket(k, max_length);
         b->groups1[k] = 0;
         if (ctx->tune_cache) {
             auto& c = tune_cache(ctx);
@@ -477,7 +478,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
     // scratch per warp of the full pass: the largest need over all buckets (a replay may see a different mix)
     size_t wb = 0;
     for (int k = 0; k < kBuckets; ++k)
-        wb = std::max(wb, wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k, max_length)));
+        wb = std::max(wb, wfa_warp_bytes(b->groups[k], bucket_pair_bytes(b->plan, k, b->groups[k])));
     b->warp_bytes = wb;
     if (wb > b->scratch_bytes) { free_batch(b); return AIM_ERR_NOMEM; }
     // with a compact first pass, its scratch per warp covers the buckets seen at planning; a pair of another
@@ -490,10 +491,9 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
         for (int k = 0; k < kBuckets; ++k) {
             if (!b->host_counts[k]) continue;
             wb1 = std::max(wb1, b->groups1[k] ? wfa_warp_bytes(b->groups1[k], bucket_compact_bytes(b->plan, k,
-                                                                                               b->groups1[k],
-                                                                                               max_length))
-                                              : wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k,
-                                                                                                max_length)));
+                                                                                               b->groups1[k]))
+                                              : wfa_warp_bytes(b->groups[k], bucket_pair_bytes(b->plan, k,
+                                                                                               b->groups[k])));
         }
         b->warp_bytes1 = std::max<size_t>(wb1, 16);
     } else {
@@ -513,7 +513,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
             for (int k = 0; k < kBuckets; ++k) {
                 if (b->groups[k] != b->ggroup[j]) continue;
                 b->bp.perm[k] = (int8_t)next++;
-                wbj = std::max(wbj, wfa_warp_bytes(b->groups[k], bucket_group_bytes(b->plan, k, max_length)));
+                wbj = std::max(wbj, wfa_warp_bytes(b->groups[k], bucket_pair_bytes(b->plan, k, b->groups[k])));
             }
             b->gwarp_bytes[j] = wbj;
         }

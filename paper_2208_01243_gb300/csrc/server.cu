@@ -527,10 +527,10 @@ int aim_server_submit(aim_server* s, const aim_request* q, uint64_t* ticket) {
         job.begin = i; job.count = j - i;
         job.plan = plan_wfa(s->costs, s->pen.band, jl, (int64_t)jme * ecost);
         job.group = wfa_default_group(job.plan, jl);
-        job.warp_bytes = wfa_warp_bytes(job.group, job.plan.group_bytes);
+        job.warp_bytes = wfa_warp_bytes(job.group, wfa_pair_bytes(job.plan, job.group));
         if (job.warp_bytes > s->scratch.size() / 64 && job.group < 32) {   // one pair per warp when scratch is scarce
             job.group = 32;
-            job.warp_bytes = job.plan.group_bytes;
+            job.warp_bytes = wfa_pair_bytes(job.plan, 32);
         }
         // warps wanted: every pair in flight at once (a 256-lane group uses 8 warps), within the device's capacity
         const size_t want = job.group > 32 ? (size_t)job.count * (job.group / 32)

@@ -96,6 +96,49 @@ __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, i
     return hist[(f.base + k) * kEntryElems + c];
 }
 
+// Storage forms of the wavefronts (one kernel instance each):
+//   kFmt8   every wavefront kept whole: one 8-byte entry (M~, I~, D~ as int16 and a spare slot) per (score,
+//           diagonal), which the forward pass reads back and the traceback reads (short reads: offsets < 32,768).
+//   kFmt16  long reads: the forward pass reads and writes the last few wavefronts whole in a small "live" ring of
+//           slots (entries as in kFmt8), and the history keeps one 16-bit word per (score, diagonal): h + 1 of M~
+//           in bits 0-13 (0: invalid; reads up to 16,382 bp) and two source bits, set when I~ (bit 14) or D~
+//           (bit 15) came from the gap extension rather than the opening.  The traceback rebuilds I~ and D~ by
+//           following those bits back to the gap's opening.  A quarter of kFmt8's history bytes.
+//   kFmt32  the same with 32-bit words (h + 1 in bits 0-29, source bits 30 and 31) and int32 live entries, for
+//           reads beyond 16,382 bp: half of kFmt8's bytes, and no 32,000 bp limit.
+enum : int { kFmt8 = 0, kFmt16 = 1, kFmt32 = 2 };
+template <int FMT>
+struct FmtT {                       // kFmt8, kFmt16
+    using V = int16_t;              // live value type
+    using H = uint16_t;             // history word (compact forms)
+    static constexpr int kNeg = kNeg16;
+    static constexpr int kBits = 14;
+};
+template <>
+struct FmtT<kFmt32> {
+    using V = int32_t;
+    using H = uint32_t;
+    static constexpr int kNeg = -(1 << 30);
+    static constexpr int kBits = 30;
+};
+
+// component c of wavefront f at diagonal k in a live ring slot, or a negative value.  A slot holds diagonal k at
+// entry f.w + k (f.w: the slot's first entry plus its centre; every diagonal a pair reaches by score smax lies
+// within smax / E + 1 of 0, and a slot is wider than twice that).
+template <int FMT>
+__device__ __forceinline__ int live_get(const typename FmtT<FMT>::V* live, const Wf& f, int c, int k) {
+    if ((unsigned)(k - f.lo) >= (unsigned)f.cnt) return FmtT<FMT>::kNeg;
+    return live[(size_t)(f.w + k) * kEntryElems + c];
+}
+
+// a compact history word for offset mv (negative: invalid) and the two source bits
+template <int FMT>
+__device__ __forceinline__ typename FmtT<FMT>::H hist_word(int mv, bool ins_ext, bool del_ext) {
+    using H = typename FmtT<FMT>::H;
+    constexpr int B = FmtT<FMT>::kBits;
+    return (H)((uint32_t)(mv >= 0 ? mv + 1 : 0) | ((uint32_t)ins_ext << B) | ((uint32_t)del_ext << (B + 1)));
+}
+
 // 32 bases starting at base pos of a sequence of nwords words in global memory, for pos inside the sequence
 // (so word pos / 32 exists); the word after it reads as 0 past the end.  (lo >> 1) >> (63 - sh) is
 // lo >> (64 - sh) for sh > 0 and 0 for sh == 0, with no branch.
@@ -267,15 +310,27 @@ struct Forward {
 // ADAPT: WFA-adaptive pruning (a kernel of its own, so the exact algorithm carries none of its registers).
 // STAGE: each group first copies its pair's packed read and target into its slot of s_seq (the launch gives
 // every group a slot of 2 * seq_slot_words words) and the extend reads the copies.
-template <int G, bool ADAPT, bool STAGE>
+template <int G, bool ADAPT, bool STAGE, int FMT>
 __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* region, size_t region_bytes, uint32_t q0,
                                                 uint32_t qend, uint32_t lane, Counters& st) {
     static_assert(!STAGE || G <= 32, "sequence staging is per group of a warp");
+    static_assert(FMT == kFmt8 || (!ADAPT && !STAGE), "compact histories are for the exact, unstaged kernels");
+    using V = typename FmtT<FMT>::V;
+    using H = typename FmtT<FMT>::H;
+    constexpr int kNeg = FmtT<FMT>::kNeg;
     const Group<G> grp(lane);
     const int g = grp.index(lane), gl = grp.gl;
     int* meta = reinterpret_cast<int*>(region);
+    // kFmt8: the history holds every wavefront whole and the forward pass reads it back.  Compact forms: the live
+    // ring sits at the end of the region (each forward pass of the group uses the same place), the history of
+    // compact words after the run staging.
     int16_t* hist = reinterpret_cast<int16_t*>(region + a.meta_bytes + a.runs_bytes);
-    const size_t hist_cap = (region_bytes - a.meta_bytes - a.runs_bytes) / sizeof(int16_t);
+    H* hc = reinterpret_cast<H*>(region + a.meta_bytes + a.runs_bytes);
+    V* live = reinterpret_cast<V*>(region + region_bytes - (FMT == kFmt8 ? 0 : a.live_bytes));
+    const size_t hist_cap = FMT == kFmt8
+        ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
+        : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
+    const int center = (int)(a.live_w / 2);
     const int X = a.X, OE = a.OE, E = a.E;
 
     const uint32_t q = q0 + (uint32_t)g;
@@ -351,7 +406,13 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         const int m0 = extend<STAGE>(seqs, n, m, 0, 0, w0);
         st.windows += w0;
         ++st.cells;
-        hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
+        if constexpr (FMT == kFmt8) {
+            hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
+        } else {   // live slot 0 at diagonal 0; history word 0
+            V* e0 = live + (size_t)center * kEntryElems;
+            e0[0] = (V)m0; e0[1] = (V)kNeg; e0[2] = (V)kNeg; e0[3] = 0;
+            hc[0] = hist_word<FMT>(m0, false, false);
+        }
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
         if (kRing && ring) ring[0] = make_int4(0, 0, 0, 1);
         found0 = (kend == 0 && m0 >= m);
@@ -376,13 +437,20 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             } else {
                 fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
             }
+            if constexpr (FMT != kFmt8) {   // Wf.w becomes the entry of diagonal 0 in the source's live slot
+                const uint32_t sm = a.live_slots - 1;
+                fx.w = (int)(((uint32_t)(s - X) & sm) * a.live_w) + center;
+                fo.w = (int)(((uint32_t)(s - OE) & sm) * a.live_w) + center;
+                fe.w = (int)(((uint32_t)(s - E) & sm) * a.live_w) + center;
+            }
             lo = 1 << 30; hi = -(1 << 30);
             if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
             if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
             w = lo <= hi ? hi - lo + 1 : 0;
-            if (w && ((size_t)top + (size_t)w) * kEntryElems > hist_cap) {
+            if (w && ((size_t)top + (size_t)w > hist_cap ||
+                      (FMT != kFmt8 && (lo + center < 0 || hi + center >= (int)a.live_w)))) {
                 status = kCap; run = false; w = 0; hi = lo - 1;
             }
         }
@@ -390,6 +458,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         int mv_end = kNeg16;   // M~ on the end diagonal kend, in the lane that computes it
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
+        const int live_slot = FMT == kFmt8 ? 0 : (int)(((uint32_t)s & (a.live_slots - 1)) * a.live_w) + center;
         uint32_t n_windows = 0;
         int dmin = 1 << 30, dmax = -(1 << 30);   // WFA-adaptive: distances of the new entries to the end cell
         for (int it = 0; it < iters; ++it) {
@@ -398,17 +467,38 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 // a candidate offset h is valid iff 0 <= h <= min(m, n + k) (h <= m and v = h - k <= n): one
                 // unsigned comparison, since an invalid source entry is kNeg16 and stays negative after + 1
                 const unsigned hmax = (unsigned)min(m, n + k);
-                int ins = max(wf_get(hist, fo, 0, k + 1), wf_get(hist, fe, 1, k + 1));
-                if ((unsigned)ins > hmax) ins = kNeg16;
-                int del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1)) + 1;
-                if ((unsigned)del > hmax) del = kNeg16;
-                int mis = wf_get(hist, fx, 0, k) + 1;
-                if ((unsigned)mis > hmax) mis = kNeg16;
+                int ins, del, mis;
+                bool ins_ext = false, del_ext = false;
+                if constexpr (FMT == kFmt8) {
+                    ins = max(wf_get(hist, fo, 0, k + 1), wf_get(hist, fe, 1, k + 1));
+                    del = max(wf_get(hist, fo, 0, k - 1), wf_get(hist, fe, 2, k - 1)) + 1;
+                    mis = wf_get(hist, fx, 0, k) + 1;
+                } else {   // sources from the live ring; the source bits record which term won (ties: the opening)
+                    const int oi = live_get<FMT>(live, fo, 0, k + 1), ei = live_get<FMT>(live, fe, 1, k + 1);
+                    const int od = live_get<FMT>(live, fo, 0, k - 1), ed = live_get<FMT>(live, fe, 2, k - 1);
+                    ins_ext = ei > oi; del_ext = ed > od;
+                    ins = max(oi, ei);
+                    del = max(od, ed) + 1;
+                    mis = live_get<FMT>(live, fx, 0, k) + 1;
+                }
+                if ((unsigned)ins > hmax) ins = kNeg;
+                if ((unsigned)del > hmax) del = kNeg;
+                if ((unsigned)mis > hmax) mis = kNeg;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
-                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);   // f0 stays kNeg16 if invalid
-                *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
-                    (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
-                // (the spare slot, bits 48-63, takes del's sign bits: nothing reads it)
+                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);   // f0 stays negative if invalid
+                if constexpr (FMT == kFmt8) {
+                    *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
+                        (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
+                    // (the spare slot, bits 48-63, takes del's sign bits: nothing reads it)
+                } else {
+                    V* e = live + (size_t)(live_slot + k) * kEntryElems;
+                    if constexpr (FMT == kFmt16)
+                        *reinterpret_cast<uint64_t*>(e) = (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) |
+                                                          ((uint64_t)(uint32_t)del << 32);
+                    else
+                        *reinterpret_cast<int4*>(e) = make_int4(mv, ins, del, 0);
+                    hc[base + k] = hist_word<FMT>(mv, ins_ext, del_ext);
+                }
                 if (k == kend) mv_end = mv;
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
                 if (ADAPT && mv >= 0) {
@@ -568,6 +658,102 @@ __device__ uint32_t traceback(const WfaArgs& a, uint8_t* region, uint32_t pi, in
     return nruns;
 }
 
+// Canonical traceback of a pair aligned with a compact history (kFmt16, kFmt32): the same tight tests as the
+// kFmt8 traceback, taken in the order X, I, D, M and evaluated one after another.  M~ comes from the history word;
+// I~[c, k] follows the I source bits back along the gap, (c, k) -> (c - E, k + 1), to the score where the gap
+// opened, and is M~[c' - OE, k' + 1] there, dropped if it leaves the matrix at k; D~[c, k] likewise along
+// (c - E, k - 1), adding one target base per step back.  (A source bit is set only when the extension's value
+// was valid and larger, so every step back stays inside the stored wavefronts.)
+template <int FMT>
+__device__ __noinline__ uint32_t traceback_compact(const WfaArgs& a, uint8_t* region, uint32_t pi, int final_s, bool& ok) {
+    using H = typename FmtT<FMT>::H;
+    constexpr int B = FmtT<FMT>::kBits;
+    constexpr uint32_t kField = (1u << B) - 1;
+    constexpr int kNeg = FmtT<FMT>::kNeg;
+    const int* meta = reinterpret_cast<const int*>(region);
+    uint32_t* staged = reinterpret_cast<uint32_t*>(region + a.meta_bytes);
+    const H* hc = reinterpret_cast<const H*>(region + a.meta_bytes + a.runs_bytes);
+    const int n = (int)a.P.read_len[pi], m = (int)a.P.target_len[pi];
+    const int X = a.X, OE = a.OE, E = a.E;
+    // history word of (c, k), or false outside the stored wavefront
+    auto word = [&](int c, int k, uint32_t& e) -> bool {
+        if (c < 0) return false;
+        const Wf f = load_wf(meta, c);
+        if ((unsigned)(k - f.lo) >= (unsigned)f.cnt) return false;
+        e = hc[f.base + k];
+        return true;
+    };
+    auto mval = [&](int c, int k) -> int {
+        uint32_t e;
+        if (!word(c, k, e)) return kNeg;
+        const uint32_t v = e & kField;
+        return v ? (int)v - 1 : kNeg;
+    };
+    auto ival = [&](int c, int k) -> int {
+        int cc = c, kk = k;
+        uint32_t e;
+        for (int guard = 0;; ++guard) {
+            if (guard > n + m + 1 || !word(cc, kk, e)) return kNeg;
+            if (!((e >> B) & 1u)) break;
+            cc -= E; kk += 1;
+        }
+        const int v = mval(cc - OE, kk + 1);
+        return (unsigned)v > (unsigned)min(m, n + k) ? kNeg : v;
+    };
+    auto dval = [&](int c, int k) -> int {
+        int cc = c, kk = k, j = 0;
+        uint32_t e;
+        for (;; ++j) {
+            if (j > n + m + 1 || !word(cc, kk, e)) return kNeg;
+            if (!((e >> (B + 1)) & 1u)) break;
+            cc -= E; kk -= 1;
+        }
+        const int v = mval(cc - OE, kk - 1);
+        if (v < 0) return kNeg;
+        const int d = v + 1 + j;
+        return (unsigned)d > (unsigned)min(m, n + k) ? kNeg : d;
+    };
+    const uint64_t* Pg = read_words(a.P, pi);
+    const uint64_t* Tg = target_words(a.P, pi);
+    const uint32_t gwP = (uint32_t)(n + 31) >> 5, gwT = (uint32_t)(m + 31) >> 5;
+    RunWriter wr;
+    wr.init(staged, a.runs_cap);
+    int v = n, h = m, cM = final_s, cI = final_s, cD = final_s;
+    while (v > 0 || h > 0) {
+        const int k = h - v;
+        const bool diag = v > 0 && h > 0;
+        const bool match = diag && base_at(Pg, v - 1) == base_at(Tg, h - 1);
+        if (diag && !match && mval(cM - X, k) >= h - 1) {
+            const int c = cM - X;
+            cM = cI = cD = c; --v; --h;
+            wr.put(kOpMismatch, 1);
+        } else if (v > 0 && ival(cI, k) >= h) {
+            const int c = cI;
+            cM = c - OE; cD = c - OE; cI = c - E; --v;
+            wr.put(kOpIns, 1);
+        } else if (h > 0 && dval(cD, k) >= h) {
+            const int c = cD;
+            cM = c - OE; cI = c - OE; cD = c - E; --h;
+            wr.put(kOpDel, 1);
+        } else if (match && mval(cM, k) >= h - 1) {
+            const int c = cM;
+            const int stop = max(ival(cM, k), dval(cM, k));
+            int run = match_run_back(Pg, gwP, v, Tg, gwT, h);
+            if (run > h - stop) run = h - stop;
+            if (run < 1) { ok = false; break; }
+            v -= run; h -= run;
+            cM = cI = cD = c;
+            wr.put(kOpMatch, (uint32_t)run);
+        } else {
+            ok = false;
+            break;
+        }
+    }
+    wr.finish();
+    ok = ok && wr.n <= wr.cap;
+    return wr.n;
+}
+
 // Result of a finished pair: score, flags, run count, and its runs (staged end-first) copied start-first by
 // lanes gl, gl + G, ... of its group; every lane of the group calls this with the same values.
 __device__ __forceinline__ void emit_done(const WfaArgs& a, uint32_t pi, int final_s, uint32_t nruns, bool ok,
@@ -598,7 +784,7 @@ __shared__ int4 s_pend[256];
 
 // Whole warp: lane gl of each group traces back the group's pending pair gl (so up to 32 tracebacks run side
 // by side instead of one per group), then the group writes each pair's result.
-template <int G, bool ADAPT>
+template <int G, bool ADAPT, int FMT>
 __device__ __forceinline__ void finish_pending(const WfaArgs& a, const Group<G>& grp, uint8_t* arena,
                                                const int4* pend, int npend) {
     __syncwarp();
@@ -609,7 +795,8 @@ __device__ __forceinline__ void finish_pending(const WfaArgs& a, const Group<G>&
     if (gl < npend) {
         const int4 r = pend[gl];
         pi = (uint32_t)r.x; final_s = r.y; off = (uint32_t)r.z;
-        nruns = traceback<ADAPT>(a, arena + ((size_t)off << 4), pi, final_s, ok);
+        if constexpr (FMT == kFmt8) nruns = traceback<ADAPT>(a, arena + ((size_t)off << 4), pi, final_s, ok);
+        else nruns = traceback_compact<FMT>(a, arena + ((size_t)off << 4), pi, final_s, ok);
     }
     __syncwarp();
     for (int j = 0; j < G; ++j) {
@@ -630,8 +817,10 @@ __device__ __forceinline__ void finish_pending(const WfaArgs& a, const Group<G>&
 // for a group of up to 32 lanes, one per warp for a whole block), once its arena has less room left than
 // one pair may need (pair_bytes), or when the bucket is drained.  A pair's forward pass therefore always has
 // at least pair_bytes, as without deferral.
-template <int G, bool ADAPT, bool STAGE>
+template <int G, bool ADAPT, bool STAGE, int FMT>
 __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane, Counters& st) {
+    // bytes of history per entry of a finished pair (a compact form's live ring is not kept)
+    constexpr size_t kEntryBytes = FMT == kFmt8 ? kEntryElems * sizeof(int16_t) : sizeof(typename FmtT<FMT>::H);
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     if constexpr (G > 32) {
@@ -653,7 +842,9 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
             if ((threadIdx.x & 31) == 0 && w < npend) {
                 const int4 r = s_bpend[w];
                 bool ok = true;
-                const uint32_t nr = traceback<ADAPT>(a, block_slot + ((size_t)r.z << 4), (uint32_t)r.x, r.y, ok);
+                uint32_t nr;
+                if constexpr (FMT == kFmt8) nr = traceback<ADAPT>(a, block_slot + ((size_t)r.z << 4), (uint32_t)r.x, r.y, ok);
+                else nr = traceback_compact<FMT>(a, block_slot + ((size_t)r.z << 4), (uint32_t)r.x, r.y, ok);
                 s_bres[w] = make_uint2(nr, ok ? 1u : 0u);
             }
             __syncthreads();
@@ -677,12 +868,12 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
                 used16 = 0;
                 npend = 0;
             }
-            const Forward f = forward_pair<G, ADAPT, false>(a, block_slot + ((size_t)used16 << 4),
+            const Forward f = forward_pair<G, ADAPT, false, FMT>(a, block_slot + ((size_t)used16 << 4),
                                                             (size_t)(arena16 - used16) << 4, begin + pos, end, lane, st);
             if (f.status == kDone) {
                 if (threadIdx.x == 0) s_bpend[npend] = make_int4((int)f.pi, f.final_s, (int)used16, 0);
                 ++npend;
-                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryElems * sizeof(int16_t) + 15) >> 4);
+                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryBytes + 15) >> 4);
             } else if (f.status != kIdle && threadIdx.x == 0) {
                 emit_failed(a, f.pi, f.status);
             }
@@ -704,40 +895,42 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
             pos = __shfl_sync(kFull, pos, 0);
             if (pos >= end - begin || end <= begin) break;
             if (__any_sync(kFull, npend == G || arena16 - used16 < pair16)) {
-                finish_pending<G, ADAPT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
-                                         s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
+                finish_pending<G, ADAPT, FMT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
+                                              s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
                 used16 = 0;
                 npend = 0;
             }
             uint8_t* region = warp_slot + (((size_t)grp.index(lane) * arena16 + used16) << 4);
             const Forward f =
-                forward_pair<G, ADAPT, STAGE>(a, region, (size_t)(arena16 - used16) << 4, begin + pos, end, lane, st);
+                forward_pair<G, ADAPT, STAGE, FMT>(a, region, (size_t)(arena16 - used16) << 4, begin + pos, end, lane, st);
             if (f.status == kDone) {
                 if (gl == 0)
                     s_pend[(threadIdx.x & ~31u) + grp.index(lane) * G + npend] = make_int4((int)f.pi, f.final_s, (int)used16, 0);
                 ++npend;
-                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryElems * sizeof(int16_t) + 15) >> 4);
+                used16 += (uint32_t)((a.meta_bytes + a.runs_bytes + (size_t)f.top * kEntryBytes + 15) >> 4);
             } else if (f.status != kIdle && gl == 0) {
                 emit_failed(a, f.pi, f.status);
             }
         }
-        finish_pending<G, ADAPT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
-                                 s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
+        finish_pending<G, ADAPT, FMT>(a, grp, warp_slot + ((size_t)grp.index(lane) * arena16 << 4),
+                                      s_pend + (threadIdx.x & ~31u) + grp.index(lane) * G, npend);
     }
 }
 
 // blocks of 256 per SM the register budget must allow: 3 (80 registers).  At 4 (64 registers) the deferred
 // tracebacks made every instance but the plain 32-lane one spill; the exact 32-lane kernel also measured 2.5 %
 // faster at 3 on long pairs, and whole-block groups 4 % faster.
-template <int G, bool ADAPT, bool STAGE>
-constexpr int wfa_min_blocks() { return 3; }
+// The compact-history instances (long reads) carry the live ring's addressing as well: whole-block groups fit
+// 80 registers with the traceback as a separate call; the 32-lane one spills there and is built for 2 blocks per SM.
+template <int G, bool ADAPT, bool STAGE, int FMT>
+constexpr int wfa_min_blocks() { return FMT == kFmt8 || G > 32 ? 3 : 2; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
 // kernel with every variant spilled about 1 KB per thread and ran 14 % slower).
 // STAGE (groups up to 16 lanes): the launch gives each group a shared-memory slot for its pair's sequences.
-template <int G, bool ADAPT, bool STAGE>
-__global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT, STAGE>())) wfa_kernel(WfaArgs a) {
+template <int G, bool ADAPT, bool STAGE, int FMT>
+__global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT, STAGE, FMT>())) wfa_kernel(WfaArgs a) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
@@ -745,10 +938,10 @@ __global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT, STAGE>())) wfa_
     Counters st{0, 0, 0};
     if (a.nbuckets == 1) {
         // one queue range (plain calls, and the batched form's groups): measured 7 % faster than the loop below
-        run_bucket<G, ADAPT, STAGE>(a, 0, warp_slot, lane, st);
+        run_bucket<G, ADAPT, STAGE, FMT>(a, 0, warp_slot, lane, st);
     } else {
         for (int b = 0; b < a.nbuckets; ++b)
-            if ((a.group[b] > 32 ? 256 : a.group[b]) == G) run_bucket<G, ADAPT, STAGE>(a, b, warp_slot, lane, st);
+            if ((a.group[b] > 32 ? 256 : a.group[b]) == G) run_bucket<G, ADAPT, STAGE, FMT>(a, b, warp_slot, lane, st);
     }
     warp_stat_add(a.O.stats, 0, st.cells, lane);
     warp_stat_add(a.O.stats, 1, st.windows, lane);
@@ -758,14 +951,20 @@ __global__ void __launch_bounds__(256, (wfa_min_blocks<G, ADAPT, STAGE>())) wfa_
 template <bool ADAPT, bool STAGE>
 void (*kernel_for(int G))(WfaArgs) {
     switch (G) {
-        case 1: return wfa_kernel<1, ADAPT, STAGE>;
-        case 2: return wfa_kernel<2, ADAPT, STAGE>;
-        case 4: return wfa_kernel<4, ADAPT, STAGE>;
-        case 8: return wfa_kernel<8, ADAPT, STAGE>;
-        case 16: return wfa_kernel<16, ADAPT, STAGE>;
-        case 32: return wfa_kernel<32, ADAPT, false>;
-        default: return wfa_kernel<256, ADAPT, false>;
+        case 1: return wfa_kernel<1, ADAPT, STAGE, kFmt8>;
+        case 2: return wfa_kernel<2, ADAPT, STAGE, kFmt8>;
+        case 4: return wfa_kernel<4, ADAPT, STAGE, kFmt8>;
+        case 8: return wfa_kernel<8, ADAPT, STAGE, kFmt8>;
+        case 16: return wfa_kernel<16, ADAPT, STAGE, kFmt8>;
+        case 32: return wfa_kernel<32, ADAPT, false, kFmt8>;
+        default: return wfa_kernel<256, ADAPT, false, kFmt8>;
     }
+}
+
+// the exact kernels of 32-lane and whole-block groups with a compact history
+void (*compact_kernel_for(int G, int fmt))(WfaArgs) {
+    if (G == 32) return fmt == kFmt16 ? wfa_kernel<32, false, false, kFmt16> : wfa_kernel<32, false, false, kFmt32>;
+    return fmt == kFmt16 ? wfa_kernel<256, false, false, kFmt16> : wfa_kernel<256, false, false, kFmt32>;
 }
 
 // Groups of up to 16 lanes (many pairs per SM) stage their pairs' sequences in shared memory when a block's
@@ -782,12 +981,12 @@ int gcd_i(int a, int b) {
 }  // namespace
 
 // Worst-case entries of the wavefront history of one pair: every wavefront as wide as its sources allow.
-size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax) {
+size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax) {
     const int64_t klo = p.band >= 0 ? -std::min<int64_t>(max_len, p.band) : -max_len;
     const int64_t khi = p.band >= 0 ? std::min<int64_t>(max_len, p.band) : max_len;
     std::vector<int64_t> lo(smax + 1), hi(smax + 1);
     lo[0] = 0; hi[0] = 0;
-    size_t elems = kEntryElems;
+    size_t entries = 1;
     for (int64_t s = 1; s <= smax; ++s) {
         int64_t l = INT64_MAX, h = INT64_MIN;
         auto take = [&](int64_t src, int64_t grow) {
@@ -797,9 +996,9 @@ size_t wfa_hist_elems(const WfaPlan& p, int64_t max_len, int64_t smax) {
         take(s - p.x, 0); take(s - p.oe, 1); take(s - p.e, 1);
         l = std::max(l, klo); h = std::min(h, khi);
         lo[s] = l; hi[s] = h;
-        if (l <= h) elems += kEntryElems * (size_t)(h - l + 1);
+        if (l <= h) entries += (size_t)(h - l + 1);
     }
-    return elems;
+    return entries;
 }
 
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit) {
@@ -813,14 +1012,24 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     int64_t smax = max_limit >= kUnbounded ? trivial : max_limit / p.g;
     if (smax > trivial) smax = trivial;
     p.smax = smax;
-    p.hist_elems = wfa_hist_elems(p, L, smax);
+    p.max_length = max_length;
+    p.hist_entries = wfa_hist_entries(p, L, smax);
+    // the live ring of the compact forms: a power-of-2 slot count above the farthest source (max(X, OE, E)
+    // scores back) and a power-of-2 slot width above the widest wavefront (it grows by at most one diagonal on
+    // each side per E score units: 2 smax / E + 3, within the matrix and the band)
+    int64_t wmax = 2 * (smax / std::max(p.e, 1)) + 3;
+    wmax = std::min<int64_t>(wmax, 2 * L + 1);
+    if (band >= 0) wmax = std::min<int64_t>(wmax, 2 * (int64_t)band + 1);
+    p.live_w = 1;
+    while ((int64_t)p.live_w < wmax) p.live_w <<= 1;
+    p.live_slots = 1;
+    while ((int)p.live_slots < std::max(std::max(p.x, p.oe), p.e) + 1) p.live_slots <<= 1;
     const int64_t minc = std::min<int64_t>(p.x, p.oe);
     int64_t runs = 2 * L + 1;
     if (minc > 0) runs = std::min<int64_t>(runs, 2 * (smax / minc) + 1);
     p.runs_cap = (int)runs;
     p.meta_bytes = align_up((size_t)(smax + 1) * 4 * sizeof(int), 16);
     p.runs_bytes = align_up((size_t)p.runs_cap * sizeof(uint32_t), 16);
-    p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
     p.adapt_min_len = -1;
     p.adapt_max_dist = 0;
     p.retry_only = 0;
@@ -829,18 +1038,39 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
 
 WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width) {
     WfaPlan p = full;
-    const size_t compact = kEntryElems * ((size_t)(full.smax + 1) * (size_t)std::max<int64_t>(width, 1) + 1);
-    if (compact < p.hist_elems) p.hist_elems = compact;
-    p.group_bytes = align_up(p.meta_bytes + p.runs_bytes + p.hist_elems * sizeof(int16_t), 16);
+    const size_t compact = (size_t)(full.smax + 1) * (size_t)std::max<int64_t>(width, 1) + 1;
+    if (compact < p.hist_entries) p.hist_entries = compact;
     return p;
 }
+
+// Storage form for a launch: the exact kernels of 32-lane and whole-block groups keep a compact history for
+// reads longer than kCompactMinLength (the live ring costs more than it saves on short ones); everything else,
+// and the adaptive algorithm, keeps 8-byte entries.
+int wfa_format(const WfaPlan& p, int group) {
+    if (p.adapt_min_len >= 0 || group < 32 || p.max_length <= kCompactMinLength) return kFmt8;
+    return p.max_length <= kMaxWfaLength16c ? kFmt16 : kFmt32;
+}
+
+size_t wfa_live_bytes(const WfaPlan& p, int fmt) {
+    if (fmt == kFmt8) return 0;
+    return align_up((size_t)p.live_slots * p.live_w * kEntryElems * (fmt == kFmt16 ? 2 : 4), 16);
+}
+
+size_t wfa_pair_bytes_capped(const WfaPlan& p, int group, size_t entries) {
+    const int fmt = wfa_format(p, group);
+    const size_t per_entry = fmt == kFmt8 ? kEntryElems * sizeof(int16_t) : fmt == kFmt16 ? 2 : 4;
+    return align_up(p.meta_bytes + p.runs_bytes + wfa_live_bytes(p, fmt) + entries * per_entry, 16);
+}
+
+size_t wfa_pair_bytes(const WfaPlan& p, int group) { return wfa_pair_bytes_capped(p, group, p.hist_entries); }
 
 int wfa_default_group(const WfaPlan& p, uint32_t max_length) {
     // widest wavefront a pair can reach: 2 * smax / E + 1 diagonals, clamped by the matrix and the band
     int64_t w = 2 * (p.smax / std::max(p.e, 1)) + 1;
     w = std::min<int64_t>(w, 2 * (int64_t)max_length + 1);
     if (p.band >= 0) w = std::min<int64_t>(w, 2 * (int64_t)p.band + 1);
-    return w <= 64 ? 4 : w <= 128 ? 8 : w <= 256 ? 16 : w <= 1024 ? 32 : 256;
+    const int g = w <= 64 ? 4 : w <= 128 ? 8 : w <= 256 ? 16 : w <= 1024 ? 32 : 256;
+    return max_length > kMaxWfaLength16 ? std::max(g, 32) : g;   // int16 offsets: reads up to 32,000 bp
 }
 
 cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const LimitView& L, const OutView& O,
@@ -858,6 +1088,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
     a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
     a.retry_only = plan.retry_only;
+    a.live_w = plan.live_w; a.live_slots = plan.live_slots;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int16_t)(b < nbuckets ? groups[b] : 32);
     const bool adapt = plan.adapt_min_len >= 0;
     int launched = 0;
@@ -876,7 +1107,11 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         size_t smem = (size_t)8 * (32 / std::min(G, 32)) * 2 * slot_words * sizeof(uint64_t);
         if (G > kStageMaxGroup || smem > kStageBytes) smem = 0;
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
-        void (*kernel)(WfaArgs) = adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
+        const int fmt = wfa_format(plan, G);
+        a.live_bytes = wfa_live_bytes(plan, fmt);
+        if (fmt != kFmt8) smem = 0;
+        void (*kernel)(WfaArgs) = fmt != kFmt8 ? compact_kernel_for(G, fmt)
+                                : adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
                                         : (smem ? kernel_for<false, true>(G) : kernel_for<false, false>(G));
         // exact staged launches: a ring of the last R score records per group, R a power of 2 above the
         // farthest source (max(X, OE)), after the sequence copies, when a block's rings fit beside them in 48 KB
@@ -917,15 +1152,15 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     return cudaSuccess;
 }
 
-size_t wfa_warp_bytes(int group, size_t group_bytes) {
-    if (group > 32) return align_up((group_bytes + (size_t)(group / 32) - 1) / (size_t)(group / 32), 16);
-    return (size_t)(32 / group) * group_bytes;
+size_t wfa_warp_bytes(int group, size_t pair_bytes) {
+    if (group > 32) return align_up((pair_bytes + (size_t)(group / 32) - 1) / (size_t)(group / 32), 16);
+    return (size_t)(32 / group) * pair_bytes;
 }
 
 cudaError_t launch_wfa(const WfaPlan& plan, int group, const PairsView& P, const LimitView& L, const OutView& O,
                        uint8_t* scratch, size_t scratch_bytes, uint32_t* counter, int num_sms, cudaStream_t st,
                        int* warps_used) {
-    const size_t warp_bytes = wfa_warp_bytes(group, plan.group_bytes);
+    const size_t warp_bytes = wfa_warp_bytes(group, wfa_pair_bytes(plan, group));
     return launch_wfa_buckets(plan, P, L, O, nullptr, nullptr, &group, 1, warp_bytes, scratch, scratch_bytes,
                               counter, num_sms, st, warps_used);
 }

@@ -110,9 +110,10 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
     const aim::WfaPlan plan = aim::plan_wfa(costs, pen->band, max_length, max_limit);
     const size_t capacity = kStaticScratchBytes - kStaticHeaderBytes;
     int group = aim::wfa_default_group(plan, max_length);
-    while (group <= 32 && 8 * aim::wfa_warp_bytes(group, plan.group_bytes) > capacity)
+    while (group <= 32 && 8 * aim::wfa_warp_bytes(group, aim::wfa_pair_bytes(plan, group)) > capacity)
         group = group == 32 ? 256 : group * 2;
-    if (8 * aim::wfa_warp_bytes(group, plan.group_bytes) > capacity) return AIM_ERR_NOMEM;   // one pair is too big
+    if (8 * aim::wfa_warp_bytes(group, aim::wfa_pair_bytes(plan, group)) > capacity)
+        return AIM_ERR_NOMEM;   // one pair is too big
 
     uint8_t* base = nullptr;
     int sms = 0;

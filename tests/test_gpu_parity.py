@@ -320,20 +320,19 @@ def test_long_reads_match_oracle(aligner, oracle_lib, gen_lib, lanes):
 
 
 def test_reads_beyond_10kbp_exact_score(aligner, oracle_lib, gen_lib):
-    """20-31 kbp pairs at 1-2 % edits (past the serving workload's 10 kbp; offsets are int16, so up to 32,000 bp):
-    the score equals the exact step-by-step WFA oracle (the full matrix would not fit), and the CIGAR is a valid
-    alignment that re-costs to it."""
+    """20-31 kbp pairs at 1-2 % edits (past the serving workload's 10 kbp): score, flags and the canonical CIGAR
+    equal the row-block oracle's (the full matrix would not fit), and the CIGAR re-costs to the score."""
     w = gen.Workload("wfa_20_31kbp_1_2pct", 91, 6, 20_000, 31_000, 0.01, 0.02, 0.0, "wfa", AFF, None,
                      max_edits_frac=0.02)
     p = gen.generate(w)
     me = gen.per_pair_max_edits(w, p)
     dev = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, aligner=aligner)
+    lim = np.array([oracle.limit_for(AFF, int(k)) for k in me], np.int64)
+    s, f, off, cig, lens = oracle.align_batch(p, AFF, lim, rows_per_block=0)
+    assert_same(dev, (s, f, [cig[off[i]:off[i] + lens[i]].astype(np.uint32) for i in range(len(p))]),
+                what="20-31 kbp")
     for i in range(len(p)):
-        r, t = p.read(i), p.target(i)
-        s, f, _ = oracle.wfa_adaptive(r, t, AFF, limit=oracle.limit_for(AFF, int(me[i])), min_len=-1)
-        assert (dev[0][i], dev[1][i]) == (s, f), i
-        ops = decode(dev[2][i])
-        assert cost(ops, r, t, AFF) == s
+        assert cost(decode(dev[2][i]), p.read(i), p.target(i), AFF) == dev[0][i]
 
 
 @pytest.mark.parametrize("algo,pen,band", [("gotoh", (0, 3, 0, 4), -1),       # NW linear gap, x=3, e=4 (Section 2.4.1)
