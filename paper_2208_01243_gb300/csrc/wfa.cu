@@ -448,6 +448,15 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
+            if constexpr (!ADAPT) {
+                // threshold: a path through diagonal k at score s still has to reach the end diagonal, a gap of
+                // |k - kend| bases costing at least E each, so only diagonals within (S - s) / E of kend can lie on
+                // an alignment of score <= S.  The sources of every entry kept lie within the same bound, so each
+                // kept entry has its exact value, and the traceback only reads entries on optimal paths (a prefix
+                // of cost c at diagonal k has c + E |k - kend| <= optimum <= S).
+                const int reach = (S - s) / E;
+                lo = max(lo, kend - reach); hi = min(hi, kend + reach);
+            }
             w = lo <= hi ? hi - lo + 1 : 0;
             if (w && ((size_t)top + (size_t)w > hist_cap ||
                       (FMT != kFmt8 && (lo + center < 0 || hi + center >= (int)a.live_w)))) {
