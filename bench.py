@@ -38,9 +38,9 @@ import gen  # noqa: E402
 
 WORKLOADS = {"wfa_150bp": gen.WFA_150BP, "edit_nw_100bp": gen.EDIT_NW_100BP,
              "gotoh_250bp": gen.GOTOH_WFA_250BP, "wfa_250bp": gen.GOTOH_WFA_250BP, "wfa_uneven": gen.WFA_UNEVEN,
-             "wfa_uneven_plain": gen.WFA_UNEVEN}
+             "wfa_uneven_plain": gen.WFA_UNEVEN, "wfa_long": gen.WFA_LONG}
 ALGO_OF = {"wfa_150bp": "wfa", "edit_nw_100bp": "edit", "gotoh_250bp": "gotoh", "wfa_250bp": "wfa",
-           "wfa_uneven": "wfa", "wfa_uneven_plain": "wfa"}
+           "wfa_uneven": "wfa", "wfa_uneven_plain": "wfa", "wfa_long": "wfa"}
 # WFA-adaptive in the shapes of Table 3, with the UPMEM throughput the paper prints for each (alignments/s,
 # 2560 DPUs, host<->DPU transfer included)
 TABLE3_UPMEM = {(150, 2): 12.97e6, (150, 5): 7.03e6, (1000, 2): 1.10e6, (1000, 5): 434e3, (10000, 2): 66.9e3,
@@ -193,6 +193,9 @@ def run_reference(args, w, algo):
     sample = {"edit": 60_000, "gotoh": 20_000, "wfa": 40_000, "wfa_adaptive": 40_000, "genasm": 60_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 2_000
+    long_pairs = w.len_max > 2000 and algo not in ("wfa_adaptive", "genasm")
+    if long_pairs:
+        sample = 64
     if algo in ("wfa_adaptive", "genasm"):
         sample = max(200, min(sample, 8_000_000 // max(w.len_max, 1)))
     pen = oracle.UNIT if algo in ("edit", "genasm") else w.penalties
@@ -209,7 +212,7 @@ def run_reference(args, w, algo):
         elif algo == "genasm":
             oracle.genasm_batch(p, lim, threads=cores)
         else:
-            oracle.align_batch(p, pen, lim, band=band, threads=cores)
+            oracle.align_batch(p, pen, lim, band=band, threads=cores, rows_per_block=0 if long_pairs else None)
         dt = time.perf_counter() - t0
         if step >= args.warmup:
             times.append(dt)
@@ -237,6 +240,9 @@ def cpu_baseline(w, algo):
     sample = {"edit": 300_000, "gotoh": 100_000, "wfa": 200_000, "wfa_adaptive": 200_000, "genasm": 400_000}[algo]
     if w is gen.WFA_UNEVEN:
         sample = 40_000   # full-matrix DP over 100-1000 bp pairs: about 25 s of CPU work on 16 cores
+    long_pairs = w.len_max > 2000 and algo not in ("wfa_adaptive", "genasm")
+    if long_pairs:
+        sample = 800      # 2-10 kbp: about 0.2 s of DP per pair, rows recomputed block by block (linear memory)
     if algo in ("wfa_adaptive", "genasm"):
         sample = max(500, min(sample, 40_000_000 // max(w.len_max, 1)))
     p = gen.generate(w, sample)
@@ -251,8 +257,10 @@ def cpu_baseline(w, algo):
         oracle.genasm_batch(p, lim, threads=cores)
         what = "windowed suffix edit-distance tables + forward traceback"
     else:
-        oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores)
-        what = "full-matrix DP + canonical traceback"
+        oracle.align_batch(p, pen, lim, band=w.band if algo == "gotoh" else -1, threads=cores,
+                           rows_per_block=0 if long_pairs else None)
+        what = ("row-block DP (rows recomputed from saved rows) + canonical traceback" if long_pairs
+                else "full-matrix DP + canonical traceback")
     dt = time.perf_counter() - t0
     return {"value": sample / dt, "unit": "alignments/s", "cores": cores, "kind": "oracle",
             "sample": f"first {sample} pairs of the workload, {what}, {dt:.1f} s wall on {cores} threads"}
@@ -422,9 +430,35 @@ def run_ours(args, w, algo):
             same &= bool(np.array_equal(t["out"]["scores"].cpu().numpy(), res_scores[idx]))
             same &= bool(np.array_equal(t["out"]["flags"].cpu().numpy(), res_flags[idx]))
             same &= bool(np.array_equal(t["out"]["lens"].cpu().numpy(), res_lens[idx]))
+        # the plain one-launch-per-batch form: one aim_align_batch_ascii call over the whole batch (lanes per pair
+        # from the longest pair's worst case, no bucketing)
+        def one_launch():
+            aim.aim_align_batch_ascii(al.ctx, d["reads"], d["targets"], d["ro"], d["to"], d["rl"], d["tl"], max_len,
+                                      "wfa", pen, max_edits, d.get("pp"), out1["scores"], out1["cigars"], coff_d,
+                                      out1["lens"], out1["flags"])
+        out1 = {k: torch.empty_like(v) for k, v in out.items()}
+        for _ in range(args.warmup):
+            one_launch()
+        torch.cuda.synchronize(); barrier()
+        q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        q0.record(stream)
+        for _ in range(args.steps):
+            one_launch()
+        q1.record(stream)
+        torch.cuda.synchronize(); barrier()
+        oms = _dist_max(q0.elapsed_time(q1) / args.steps, dev, world)
+        same1 = (bool(np.array_equal(out1["scores"].cpu().numpy(), res_scores))
+                 and bool(np.array_equal(out1["flags"].cpu().numpy(), res_flags))
+                 and bool(np.array_equal(out1["lens"].cpu().numpy(), res_lens)))
+        del out1
         plain = {"value": world * n_pairs / (pms / 1e3), "unit": "alignments/s", "ms_per_step": pms,
                  "launches_per_step": len(gd) * 3, "length_groups": len(gd), "results_identical": same,
                  "batched_over_plain": pms / ms,
+                 "one_launch": {"value": world * n_pairs / (oms / 1e3), "ms_per_step": oms, "launches_per_step": 3,
+                                "results_identical": same1, "batched_over_one_launch": oms / ms,
+                                "form": "one aim_align_batch_ascii call over the whole batch (the plain "
+                                        "one-launch-per-batch form: one lanes-per-pair value for all pairs, no "
+                                        "bucketing)"},
                  "batched_lanes_per_bucket": {str(k): g for k, (g, c) in enumerate(zip(groups, counts)) if c},
                  "batched_compact_first_pass": {str(k): [f, g] for k, (f, g, c) in
                                                 enumerate(zip(first_pass, full_pass, counts)) if c and f},

@@ -91,6 +91,10 @@ SERVE_LONG = Workload("serve_100_10000bp_1_10pct", 5, 0, 100, 10_000, 0.01, 0.10
                       "wfa", (0, 4, 6, 2), None, max_edits_frac=0.10)
 ALL = [EDIT_NW_100BP, WFA_150BP, GOTOH_WFA_250BP, WFA_UNEVEN, SERVE_LONG]
 
+# Long reads on their own (the serving workload's long end): 2-10 kbp, 1-10 % edits, thresholds at 10 % of length.
+WFA_LONG = Workload("wfa_long_2000_10000bp_1_10pct_20k", 63, 20_000, 2000, 10_000, 0.01, 0.10, 0.0, "wfa",
+                    (0, 4, 6, 2), None, max_edits_frac=0.10)
+
 # WFA-adaptive in the shapes of the paper's Table 3 (read length x edit rate), with the paper's costs
 # (x=3, o=4, e=1, Section 2.4.4) and thresholds at the edit rate: ceil(rate * length) edits.
 TABLE3 = {

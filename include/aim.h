@@ -217,6 +217,22 @@ AIM_API int aim_align_batch_host(aim_ctx *ctx, const uint8_t *reads, const uint8
                                  uint32_t chunk_pairs, uint64_t *bytes_moved);
 
 /*
+ * Worst-case device scratch of one pair in flight for the gap-affine WFA
+ * (AIM_ALGO_WFA_AFFINE) with `lanes` lanes per pair (as for aim_set_wfa_group;
+ * 0: the library's choice), for pairs no longer than max_length under the
+ * threshold rule above (pen, max_edits; host values): per-score records, CIGAR
+ * run staging and the wavefront history, every wavefront as wide as its
+ * sources allow.  Groups of 32 lanes or whole blocks on reads longer than
+ * 2,048 bp keep a compact history (2 bytes per wavefront entry up to 16,382
+ * bp, 4 beyond, plus a small ring of the last few wavefronts) instead of 8
+ * bytes per entry (Section 3.3: the long-read limit comes from memory).  The
+ * workspace must hold at least 8 warps' worth of it (a whole-block group's
+ * warps share one pair's).  Host-only; no device needed.
+ */
+AIM_API int aim_wfa_scratch_per_pair(uint32_t max_length, const aim_penalties_t *pen, int32_t max_edits, int lanes,
+                                     size_t *bytes);
+
+/*
  * WFA-adaptive parameters of a context (defaults 10 and 50; the paper gives
  * none).  After wavefront s (unless the pair finished at s), if it spans at
  * least min_length diagonals, each diagonal's distance to the end cell,

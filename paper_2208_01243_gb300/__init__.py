@@ -91,6 +91,8 @@ def _lib():
         lib.aim_timing_read.argtypes = [p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]
         lib.aim_align_batch_host.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.c_int,
                                              ctypes.POINTER(aim_penalties_t), i32, p, p, p, p, p, p, u32, p]
+        lib.aim_wfa_scratch_per_pair.argtypes = [u32, ctypes.POINTER(aim_penalties_t), i32, ctypes.c_int,
+                                                 ctypes.POINTER(ctypes.c_size_t)]
         lib.aim_measure_int_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(ctypes.c_double), p]
         _LIB = lib
@@ -362,6 +364,14 @@ def aim_align_batch_host(ctx, reads, targets, read_char_offsets, target_char_off
         h(out_flags, np.uint8, "out_flags", writable=True), ctypes.c_uint32(chunk_pairs),
         ctypes.c_void_p(moved.ctypes.data)), "aim_align_batch_host")
     return int(moved[0]), int(moved[1])
+
+
+def aim_wfa_scratch_per_pair(max_length: int, pen, max_edits: int, lanes: int = 0) -> int:
+    """Worst-case device scratch (bytes) of one WFA pair in flight with `lanes` lanes per pair (see aim.h)."""
+    b = ctypes.c_size_t()
+    _check(_lib().aim_wfa_scratch_per_pair(ctypes.c_uint32(max_length), ctypes.byref(pen), ctypes.c_int32(max_edits),
+                                           int(lanes), ctypes.byref(b)), "aim_wfa_scratch_per_pair")
+    return b.value
 
 
 def aim_measure_int_peak(device: int = 0) -> tuple[float, float, list[float]]:

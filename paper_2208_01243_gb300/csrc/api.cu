@@ -294,6 +294,22 @@ int aim_destroy(aim_ctx* ctx) {
     return cuda_status(e);
 }
 
+int aim_wfa_scratch_per_pair(uint32_t max_length, const aim_penalties_t* pen, int32_t max_edits, int lanes,
+                             size_t* bytes) {
+    if (!bytes || !penalties_ok(pen) || max_length > aim::kMaxWfaLength) return AIM_ERR_ARG;
+    if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32 ||
+          lanes == 256))
+        return AIM_ERR_ARG;
+    Resolved r;
+    const int rc = resolve(AIM_ALGO_WFA_AFFINE, pen, max_edits, nullptr, &r);
+    if (rc) return rc;
+    const aim::WfaPlan plan = aim::plan_wfa(r.costs, pen->band, max_length, r.max_limit);
+    int g = lanes ? lanes : aim::wfa_default_group(plan, max_length);
+    if (max_length > aim::kMaxWfaLength16) g = std::max(g, 32);
+    *bytes = aim::wfa_pair_bytes(plan, g);
+    return AIM_OK;
+}
+
 int aim_set_wfa_group(aim_ctx* ctx, int lanes) {
     if (!ctx || !(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32 ||
                   lanes == 256))

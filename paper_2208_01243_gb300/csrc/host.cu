@@ -29,6 +29,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "aim_internal.cuh"
 
@@ -42,9 +43,6 @@ struct Slot {
     uint32_t *rlen, *tlen, *lens, *cigars;
     int32_t *me, *scores;
     uint8_t* flags;
-    // pinned host staging of the chunk's metadata, copied in with one transfer:
-    // roff, toff, coff (C + 1) as uint64, then rlen, tlen, me as 32-bit words
-    uint8_t* stage;
     aim_batch* plan;
     cudaEvent_t in_done, comp_done, out_done;
     bool used;
@@ -63,7 +61,27 @@ struct HostPipe {
     Slot slot[2];
 };
 
-size_t meta_bytes(uint32_t C) { return (size_t)(3 * (size_t)C + 1) * 8 + 3 * (size_t)C * 4; }
+// A chunk's offsets arrive as the caller wrote them; this rebases them to the chunk's own byte and run ranges and
+// fills the padding of a short last chunk (batched form) with empty pairs whose runs start at the chunk's end.
+__global__ void __launch_bounds__(256) rebase_kernel(uint64_t* roff, uint64_t* toff, uint64_t* coff, uint32_t* rlen,
+                                                     uint32_t* tlen, int32_t* me, uint32_t k, uint32_t padded,
+                                                     uint64_t rlo, uint64_t tlo, uint64_t cbase, uint64_t cend,
+                                                     int per_pair, int cigars) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= padded; i += gridDim.x * blockDim.x) {
+        if (i < k) {
+            roff[i] -= rlo;
+            toff[i] -= tlo;
+            if (cigars) coff[i] -= cbase;
+        } else if (i < padded) {
+            roff[i] = toff[i] = 0;
+            rlen[i] = tlen[i] = 0;
+            if (per_pair) me[i] = 0;
+            if (cigars) coff[i] = cend;
+        } else if (cigars) {
+            coff[i] = cend;   // entry `padded`: the end of the last pair's runs
+        }
+    }
+}
 
 void destroy_pipe(HostPipe* hp) {
     if (!hp) return;
@@ -73,7 +91,6 @@ void destroy_pipe(HostPipe* hp) {
     if (hp->d2h) cudaStreamSynchronize(hp->d2h);
     for (Slot& s : hp->slot) {
         if (s.plan) aim_batch_destroy(s.plan);
-        if (s.stage) cudaFreeHost(s.stage);
         if (s.in_done) cudaEventDestroy(s.in_done);
         if (s.comp_done) cudaEventDestroy(s.comp_done);
         if (s.out_done) cudaEventDestroy(s.out_done);
@@ -122,8 +139,7 @@ HostPipe* make_pipe(int algo, const aim_penalties_t* pen, int32_t max_edits, boo
         s.scores = reinterpret_cast<int32_t*>(p); p += align_up((size_t)C * 4, a);
         s.flags = p; p += align_up(C, a);
         s.cigars = reinterpret_cast<uint32_t*>(p); p += align_up(hp->cigar_cap * 4, a);
-        e = cudaMallocHost(&s.stage, meta_bytes(C));
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming);
+        e = cudaEventCreateWithFlags(&s.in_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.comp_done, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s.out_done, cudaEventDisableTiming);
     }
@@ -182,13 +198,14 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
     C = std::min(C, num_pairs);
     const uint32_t nchunks = (num_pairs + C - 1) / C;
     uint64_t rc = 0, tc = 0, cc = 0;
+    std::vector<uint64_t> ranges(4 * (size_t)nchunks);   // per chunk: read bytes [lo, hi), target bytes [lo, hi)
     for (uint32_t j = 0; j < nchunks; ++j) {
         const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C);
-        uint64_t lo, hi;
-        byte_range(read_char_offsets, read_lengths, c0, c1, &lo, &hi);
-        rc = std::max(rc, hi - lo);
-        byte_range(target_char_offsets, target_lengths, c0, c1, &lo, &hi);
-        tc = std::max(tc, hi - lo);
+        uint64_t* r = &ranges[4 * (size_t)j];
+        byte_range(read_char_offsets, read_lengths, c0, c1, &r[0], &r[1]);
+        byte_range(target_char_offsets, target_lengths, c0, c1, &r[2], &r[3]);
+        rc = std::max(rc, r[1] - r[0]);
+        tc = std::max(tc, r[3] - r[2]);
         if (cigar_offsets) cc = std::max(cc, cigar_offsets[c1] - cigar_offsets[c0]);
     }
     const bool wfa_batched = algo == AIM_ALGO_WFA_AFFINE;
@@ -211,38 +228,12 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
         Slot& s = hp->slot[j & 1];
         cudaStream_t comp = hp->comp[j & 1];
         const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C), k = c1 - c0;
-        // the slot's staging was read by its previous copy-in
-        if (s.used) e = cudaEventSynchronize(s.in_done);
-        if (e != cudaSuccess) break;
-        uint64_t rlo, rhi, tlo, thi;
-        byte_range(read_char_offsets, read_lengths, c0, c1, &rlo, &rhi);
-        byte_range(target_char_offsets, target_lengths, c0, c1, &tlo, &thi);
-        // metadata rebased to the chunk; padding (a short last chunk in the batched form) as empty pairs
-        uint64_t* m_roff = reinterpret_cast<uint64_t*>(s.stage);
-        uint64_t* m_toff = m_roff + C;
-        uint64_t* m_coff = m_toff + C;
-        uint32_t* m_rlen = reinterpret_cast<uint32_t*>(m_coff + C + 1);
-        uint32_t* m_tlen = m_rlen + C;
-        int32_t* m_me = reinterpret_cast<int32_t*>(m_tlen + C);
+        const uint64_t rlo = ranges[4 * (size_t)j], rhi = ranges[4 * (size_t)j + 1];
+        const uint64_t tlo = ranges[4 * (size_t)j + 2], thi = ranges[4 * (size_t)j + 3];
         const uint64_t cbase = cigar_offsets ? cigar_offsets[c0] : 0;
-        for (uint32_t i = 0; i < k; ++i) {
-            m_roff[i] = read_char_offsets[c0 + i] - rlo;
-            m_toff[i] = target_char_offsets[c0 + i] - tlo;
-            m_rlen[i] = read_lengths[c0 + i];
-            m_tlen[i] = target_lengths[c0 + i];
-            m_me[i] = max_edits_per_pair ? max_edits_per_pair[c0 + i] : 0;
-            m_coff[i] = cigar_offsets ? cigar_offsets[c0 + i] - cbase : 0;
-        }
         const uint64_t cend = cigar_offsets ? cigar_offsets[c1] - cbase : 0;
         const uint32_t padded = wfa_batched ? C : k;
-        for (uint32_t i = k; i < padded; ++i) {
-            m_roff[i] = m_toff[i] = 0;
-            m_rlen[i] = m_tlen[i] = 0;
-            m_me[i] = 0;
-            m_coff[i] = cend;
-        }
-        m_coff[padded] = cend;
-        // copy in, once the slot's previous alignment has read its inputs
+        // copy in straight from the caller's arrays, once the slot's previous alignment has read its inputs
         if (s.used) e = cudaStreamWaitEvent(hp->h2d, s.comp_done, 0);
         auto in = [&](void* dst, const void* src, size_t bytes) {
             if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, hp->h2d);
@@ -250,27 +241,35 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
         };
         in(s.reads, reads + rlo, rhi - rlo);
         in(s.targets, targets + tlo, thi - tlo);
-        in(s.roff, m_roff, (size_t)padded * 8);
-        in(s.toff, m_toff, (size_t)padded * 8);
-        if (cigar_offsets) in(s.coff, m_coff, ((size_t)padded + 1) * 8);
-        in(s.rlen, m_rlen, (size_t)padded * 4);
-        in(s.tlen, m_tlen, (size_t)padded * 4);
-        if (max_edits_per_pair) in(s.me, m_me, (size_t)padded * 4);
+        in(s.roff, read_char_offsets + c0, (size_t)k * 8);
+        in(s.toff, target_char_offsets + c0, (size_t)k * 8);
+        if (cigar_offsets) in(s.coff, cigar_offsets + c0, ((size_t)k + 1) * 8);
+        in(s.rlen, read_lengths + c0, (size_t)k * 4);
+        in(s.tlen, target_lengths + c0, (size_t)k * 4);
+        if (max_edits_per_pair) in(s.me, max_edits_per_pair + c0, (size_t)k * 4);
         if (e == cudaSuccess) e = cudaEventRecord(s.in_done, hp->h2d);
         if (e != cudaSuccess) break;
         // align, once the inputs are in and the slot's previous results have left
         e = cudaStreamWaitEvent(comp, s.in_done, 0);
         if (e == cudaSuccess && s.used) e = cudaStreamWaitEvent(comp, s.out_done, 0);
         if (e != cudaSuccess) break;
+        {
+            const unsigned blocks = (unsigned)std::min<uint64_t>(((uint64_t)padded + 256) / 256, 1024);
+            rebase_kernel<<<blocks, 256, 0, comp>>>(s.roff, s.toff, s.coff, s.rlen, s.tlen, s.me, k, padded, rlo, tlo,
+                                                    cbase, cend, max_edits_per_pair != nullptr,
+                                                    cigar_offsets != nullptr);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) break;
+        }
         // runs past each pair's count read as zero in the host buffer, as with the device entry points
         if (cigar_offsets && cend) e = cudaMemsetAsync(s.cigars, 0, cend * 4, comp);
         if (e != cudaSuccess) break;
         if (wfa_batched) {
             if (!s.plan) {
-                // planned on the chunk it first holds (planning packs and buckets the bound inputs); the second
-                // slot's plan takes the lanes the first one tuned from the context's cache.  Each slot's plan
-                // has its own half of the workspace as scratch.
-                e = cudaEventSynchronize(s.in_done);
+                // planned on the chunk it first holds (planning packs and buckets the bound inputs, so they are
+                // rebased first); the second slot's plan takes the lanes the first one tuned from the context's
+                // cache.  Each slot's plan has its own half of the workspace as scratch.
+                e = cudaStreamSynchronize(comp);
                 if (e != cudaSuccess) break;
                 const size_t half = ((ctx->ws_bytes - kHeaderBytes) / 2) & ~(size_t)255;
                 rc_status = batch_plan_impl(ctx, s.reads, s.targets, s.roff, s.toff, s.rlen, s.tlen, C, max_length,

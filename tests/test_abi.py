@@ -40,3 +40,22 @@ def test_host_only_calls_without_gpu():
                                None, None, None) == aim.AIM_ERR_ARG
     assert lib.aim_create(None, 0, 0) == aim.AIM_ERR_ARG
 
+
+
+def test_wfa_scratch_per_pair_compact_history():
+    """Host-only sizing query: on long reads, 32-lane and whole-block groups keep a compact history (2 bytes per
+    wavefront entry up to 16,382 bp, 4 beyond) instead of the 8-byte entries of narrower groups."""
+    import paper_2208_01243_gb300 as aim
+    pen = aim.penalties(4, 6, 2)
+    f8 = aim.aim_wfa_scratch_per_pair(10_000, pen, 1000, lanes=16)
+    c16 = aim.aim_wfa_scratch_per_pair(10_000, pen, 1000, lanes=32)
+    assert c16 == aim.aim_wfa_scratch_per_pair(10_000, pen, 1000, lanes=256)
+    assert f8 / c16 > 3.8                       # 8 -> 2 bytes per entry, plus the records and the live ring
+    c32 = aim.aim_wfa_scratch_per_pair(20_000, pen, 200, lanes=32)
+    f8b = aim.aim_wfa_scratch_per_pair(20_000, pen, 200, lanes=16)
+    assert 1.8 < f8b / c32 < 2.1
+    # short reads keep the 8-byte entries whatever the group
+    assert aim.aim_wfa_scratch_per_pair(150, pen, 6, lanes=32) == aim.aim_wfa_scratch_per_pair(150, pen, 6, lanes=4)
+    # past 32,000 bp only the compact history can hold the offsets: 32 lanes at least, whatever is asked
+    assert aim.aim_wfa_scratch_per_pair(40_000, pen, 100, lanes=4) == aim.aim_wfa_scratch_per_pair(40_000, pen, 100,
+                                                                                                   lanes=32)
