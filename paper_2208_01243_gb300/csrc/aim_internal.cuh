@@ -103,6 +103,7 @@ cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const ui
 struct DpPlan {
     int band;            // effective band b (2b+1 diagonals)
     int blocks;          // lane blocks R (1, 2 or 4)
+    int pairs_per_warp;  // 1, or 2 / 4 for bands up to 15 / 7 (one pair per segment of 16 / 8 lanes)
     bool unit;
     size_t slot_bytes;   // per-warp scratch
 };

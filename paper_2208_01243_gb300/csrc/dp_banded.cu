@@ -1,8 +1,11 @@
 // Banded global DP with traceback: NW edit distance (Section 2.4.1, unit
 // costs) and gap-affine Gotoh with three states M, I, D (Section 2.4.2).
 //
-// One warp aligns one pair.  The band |h - v| <= b holds 2b+1 diagonals;
-// lane j of lane block r owns the two diagonals q = 2(32r + j) and q + 1
+// One warp aligns one pair, or, for narrow bands, 32/GS pairs side by side
+// in segments of GS = 16 or 8 lanes (a band of b <= GS - 1 fits one segment:
+// with band 10, 21 diagonals would otherwise leave two thirds of a warp's
+// lanes idle).  The band |h - v| <= b holds 2b+1 diagonals; lane j of lane
+// block r (of a segment) owns the two diagonals q = 2(GS r + j) and q + 1
 // (q = k + b).  The sweep runs over anti-diagonals d = v + h: cell (v, h)
 // of diagonal k sits on anti-diagonal d with v = (d - k) / 2, so at step d
 // exactly the diagonals with k = d (mod 2) hold a cell, i.e. one of each
@@ -62,11 +65,10 @@ __shared__ int4 s_dp_pend[256];
 
 // Canonical traceback of one finished pair by one lane, from its trace rows; returns the number of runs,
 // staged end-first.  ok turns false if a step finds no tight state (not expected) or the runs overflow.
-template <bool UNIT, int R>
+template <bool UNIT, int RW>
 __device__ uint32_t dp_traceback(const DpArgs& a, const uint8_t* slot, uint32_t* staged, uint32_t pi, uint32_t ends,
                                  bool& ok) {
     using TB = typename std::conditional<UNIT, uint8_t, uint16_t>::type;
-    constexpr int RW = 32 * R;
     const TB* trace = reinterpret_cast<const TB*>(slot);
     const int b = a.band;
     const uint64_t* Pw = read_words(a.P, pi);
@@ -104,40 +106,47 @@ __device__ uint32_t dp_traceback(const DpArgs& a, const uint8_t* slot, uint32_t*
 }
 
 // Whole warp: lane j traces back the pair waiting in slot j (so up to 32 tracebacks run side by side), then
-// the warp writes each pair's result.
-template <bool UNIT, int R>
+// the warp writes each pair's result.  A slot whose record holds pair -1 is empty (its segment's pair was
+// rejected or flagged).
+template <bool UNIT, int RW>
 __device__ __forceinline__ void dp_finish(const DpArgs& a, uint8_t* warp_slots, const int4* pend, uint32_t npend,
                                           uint32_t lane) {
     __syncwarp();   // trace rows and records written by every lane are visible
     uint32_t nruns = 0;
     bool ok = true;
-    if (lane < npend) {
+    if (lane < npend && pend[lane].x >= 0) {
         const int4 r = pend[lane];
         uint8_t* slot = warp_slots + (size_t)lane * a.slot_bytes;
-        nruns = dp_traceback<UNIT, R>(a, slot, reinterpret_cast<uint32_t*>(slot + a.trace_bytes), (uint32_t)r.x,
-                                      (uint32_t)r.z, ok);
+        nruns = dp_traceback<UNIT, RW>(a, slot, reinterpret_cast<uint32_t*>(slot + a.trace_bytes), (uint32_t)r.x,
+                                       (uint32_t)r.z, ok);
     }
     __syncwarp();
     for (uint32_t j = 0; j < npend; ++j) {
         const int4 r = pend[j];
         const uint32_t nj = __shfl_sync(kFull, nruns, j);
         const bool okj = __shfl_sync(kFull, ok ? 1 : 0, j) != 0;
+        if (r.x < 0) continue;
         const uint32_t* staged = reinterpret_cast<const uint32_t*>(warp_slots + (size_t)j * a.slot_bytes + a.trace_bytes);
         write_cigar(a.O, (uint32_t)r.x, r.y, staged, nj, okj, lane);
     }
     __syncwarp();
 }
 
-template <bool UNIT, int R>
-__global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
+// 4 blocks of 256 per SM (64 registers) with one lane block, 2 with two
+template <bool UNIT, int R, int SUB>
+__global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(DpArgs a) {
+    static_assert(SUB == 1 || R == 1, "several pairs per warp only for one lane block");
     using TB = typename std::conditional<UNIT, uint8_t, uint16_t>::type;
-    constexpr int RW = 32 * R;
+    constexpr int GS = 32 / SUB;    // lanes per pair (a segment of the warp)
+    constexpr int RW = GS * R;      // trace entries per anti-diagonal row
     const uint32_t lane = threadIdx.x & 31;
+    const int sl = (int)lane % GS, sg = (int)lane / GS;   // lane within the segment, segment
+    const uint32_t seg = GS == 32 ? kFull : (((1u << GS) - 1u) << (sg * GS));
     const uint32_t gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (gwarp >= a.nwarps) return;
     uint8_t* warp_slots = a.scratch + (size_t)gwarp * a.defer * a.slot_bytes;
     int4* pend = s_dp_pend + (threadIdx.x & ~31u);
-    uint32_t npend = 0;   // finished pairs waiting in slots 0 .. npend-1 (warp-uniform)
+    uint32_t npend = 0;   // slots taken: 0 .. npend-1 (warp-uniform; SUB per round, some possibly empty)
     const int b = a.band;
     const int32_t x = UNIT ? 1 : a.c.x;
     const int32_t oe = UNIT ? 1 : a.c.o + a.c.e;
@@ -145,28 +154,44 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
     unsigned long long st_cells = 0, st_pairs = 0;
 
     for (;;) {
-        uint32_t pi = 0;
-        if (lane == 0) pi = atomicAdd(a.counter, 1u);
-        pi = __shfl_sync(kFull, pi, 0);
-        if (pi >= a.P.num_pairs) break;
-        st_pairs += lane == 0;
-
-        const uint32_t n = a.P.read_len[pi], m = a.P.target_len[pi];
-        const int64_t lim = pair_limit(a.L, pi);
-        const bool bad = pair_bad(a.P, pi) || n > a.P.max_length || m > a.P.max_length || lim == -2;
-        if (bad) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_BAD_PAIR, 0);
-            continue;
+        uint32_t p0 = 0;
+        if (lane == 0) p0 = atomicAdd(a.counter, (uint32_t)SUB);
+        p0 = __shfl_sync(kFull, p0, 0);
+        if (p0 >= a.P.num_pairs) break;
+        const uint32_t pi = p0 + (uint32_t)sg;
+        // this segment's pair: live until it is aligned, rejected or flagged
+        bool live = pi < a.P.num_pairs;
+        uint32_t n = 0, m = 0;
+        int64_t lim = 0;
+        int kend = 0;
+        if (live) {
+            st_pairs += sl == 0;
+            n = a.P.read_len[pi]; m = a.P.target_len[pi];
+            lim = pair_limit(a.L, pi);
+            if (pair_bad(a.P, pi) || n > a.P.max_length || m > a.P.max_length || lim == -2) {
+                if (sl == 0) write_header(a.O, pi, -1, AIM_F_BAD_PAIR, 0);
+                live = false;
+            } else {
+                kend = (int)m - (int)n;
+                if (kend > b || -kend > b) {
+                    if (sl == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
+                    live = false;
+                }
+            }
         }
-        const int kend = (int)m - (int)n;
-        if (kend > b || -kend > b) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
+        const uint32_t slot_i = npend + (uint32_t)sg;
+        if (!__any_sync(kFull, live)) {
+            if constexpr (SUB > 1) {   // the round's slots stay empty
+                if (sl == 0) pend[slot_i] = make_int4(-1, 0, 0, 0);
+                npend += SUB;
+                if (npend + SUB > a.defer) { dp_finish<UNIT, RW>(a, warp_slots, pend, npend, lane); npend = 0; }
+            }
             continue;
         }
         const int32_t limc = lim >= (int64_t)kInf ? kInf - 1 : (int32_t)lim;
-        TB* trace = reinterpret_cast<TB*>(warp_slots + (size_t)npend * a.slot_bytes);
-        const uint64_t* Pw = read_words(a.P, pi);
-        const uint64_t* Tw = target_words(a.P, pi);
+        TB* trace = reinterpret_cast<TB*>(warp_slots + (size_t)slot_i * a.slot_bytes);
+        const uint64_t* Pw = live ? read_words(a.P, pi) : nullptr;
+        const uint64_t* Tw = live ? target_words(a.P, pi) : nullptr;
 
         // per slot (parity p, block r): the latest cell of that diagonal, the anti-diagonal range where the
         // diagonal holds cells of this pair, and the packed words its cells read (advanced, not reloaded)
@@ -179,23 +204,29 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 Ms[pp][r] = Is[pp][r] = Ds[pp][r] = kInf;
-                const int q = 2 * (32 * r + (int)lane) + pp, k = q - b;
+                const int q = 2 * (GS * r + sl) + pp, k = q - b;
                 // cell (v,h) of diagonal k lies on anti-diagonal d = 2v + k: v >= 0, h >= 0, v <= n, h <= m
-                dlo[pp][r] = q <= 2 * b ? (k < 0 ? -k : k) : (1 << 30);
+                dlo[pp][r] = live && q <= 2 * b ? (k < 0 ? -k : k) : (1 << 30);
                 dhi[pp][r] = min(2 * (int)n + k, 2 * (int)m - k);
                 pwi[pp][r] = twi[pp][r] = -1;
                 pw[pp][r] = tw[pp][r] = 0;
             }
         {   // seed: cell (0,0) on diagonal k = 0, q = b
-            const int i0 = b >> 1, p0 = b & 1;
+            const int i0 = b >> 1, p0s = b & 1;
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                if (r == (i0 >> 5) && (int)lane == (i0 & 31)) Ms[p0][r] = 0;
+                if (live && r == (i0 / GS) && sl == (i0 % GS)) Ms[p0s][r] = 0;
         }
-        bool prev_over = false, rejected = false;
-        const int dend = (int)(n + m);
+        bool prev_over = false;
+        const int dend = live ? (int)(n + m) : 0;
+        // several pairs per warp: the sweep runs on past a pair's last anti-diagonal (for the other segments), so the
+        // lane that computes the end cell (n, m) keeps its values here
+        int32_t xM = kInf, xI = kInf, xD = kInf;
+        if (SUB > 1 && live && dend == 0 && sl == (b >> 1) % GS) xM = 0;   // both sequences empty: the seed cell
+        const int dmax = SUB == 1 ? dend : (int)__reduce_max_sync(kFull, (unsigned)dend);
 
-        // one anti-diagonal step on the slots of parity P (P == (d + b) & 1)
+        // one anti-diagonal step on the slots of parity P (P == (d + b) & 1); returns whether every cell of this
+        // segment's pair on it exceeds the limit (true for a segment with no live pair)
         auto step = [&](const int d, auto parity) -> bool {
             constexpr int P = decltype(parity)::value;
             bool over = true;
@@ -203,11 +234,11 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 // neighbour slot on the other parity: P == 0 needs q-1 (lane-1, wrapping to block r-1),
-                // P == 1 needs q+1 (lane+1, wrapping to block r+1)
+                // P == 1 needs q+1 (lane+1, wrapping to block r+1); shuffles stay inside the segment
                 int32_t nM, nI = kInf, nD = kInf;
                 if (P == 0) {
-                    nM = __shfl_up_sync(kFull, Ms[1][r], 1);
-                    if (!UNIT) { nI = __shfl_up_sync(kFull, Is[1][r], 1); nD = __shfl_up_sync(kFull, Ds[1][r], 1); }
+                    nM = __shfl_up_sync(kFull, Ms[1][r], 1, GS);
+                    if (!UNIT) { nI = __shfl_up_sync(kFull, Is[1][r], 1, GS); nD = __shfl_up_sync(kFull, Ds[1][r], 1, GS); }
                     if constexpr (R > 1) {
                         const int rr = r > 0 ? r - 1 : 0;
                         const int32_t wM = __shfl_sync(kFull, r > 0 ? Ms[1][rr] : kInf, 31);
@@ -217,12 +248,12 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                             wD = __shfl_sync(kFull, r > 0 ? Ds[1][rr] : kInf, 31);
                         }
                         if (lane == 0) { nM = wM; nI = wI; nD = wD; }
-                    } else if (lane == 0) {
+                    } else if (sl == 0) {
                         nM = kInf; nI = kInf; nD = kInf;
                     }
                 } else {
-                    nM = __shfl_down_sync(kFull, Ms[0][r], 1);
-                    if (!UNIT) { nI = __shfl_down_sync(kFull, Is[0][r], 1); nD = __shfl_down_sync(kFull, Ds[0][r], 1); }
+                    nM = __shfl_down_sync(kFull, Ms[0][r], 1, GS);
+                    if (!UNIT) { nI = __shfl_down_sync(kFull, Is[0][r], 1, GS); nD = __shfl_down_sync(kFull, Ds[0][r], 1, GS); }
                     if constexpr (R > 1) {
                         const int rr = r + 1 < R ? r + 1 : r;
                         const int32_t wM = __shfl_sync(kFull, r + 1 < R ? Ms[0][rr] : kInf, 0);
@@ -232,7 +263,7 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                             wD = __shfl_sync(kFull, r + 1 < R ? Ds[0][rr] : kInf, 0);
                         }
                         if (lane == 31) { nM = wM; nI = wI; nD = wD; }
-                    } else if (lane == 31) {
+                    } else if (sl == GS - 1) {
                         nM = kInf; nI = kInf; nD = kInf;
                     }
                 }
@@ -242,7 +273,7 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                 const int32_t lM = P ? Ms[0][r] : nM, lI = P ? Is[0][r] : nI, lD = P ? Ds[0][r] : nD;
                 int32_t Mv = kInf, Iv = kInf, Dv = kInf;
                 if (d >= dlo[P][r] && d <= dhi[P][r]) {
-                    const int k = 2 * (32 * r + (int)lane) + P - b;
+                    const int k = 2 * (GS * r + sl) + P - b;
                     const int v = (d - k) >> 1, h = (d + k) >> 1;
                     uint32_t bits = 0;
                     if (v >= 1 && h >= 1) {
@@ -288,78 +319,131 @@ __global__ void __launch_bounds__(256) dp_kernel(DpArgs a) {
                                (Dv == H && H < kInf ? 4u : 0u);
                         Mv = H; Iv = kInf; Dv = kInf;
                     }
-                    trow[32 * r + lane] = (TB)bits;
+                    trow[GS * r + sl] = (TB)bits;
+                    if constexpr (SUB > 1) {
+                        if (d == dend && k == kend) { xM = Mv; xI = Iv; xD = Dv; }
+                    }
                     ++st_cells;
                     over = over && min3(Mv, Iv, Dv) > limc;
                 }
                 Ms[P][r] = Mv; Is[P][r] = Iv; Ds[P][r] = Dv;
             }
-            return __all_sync(kFull, over);
+            if constexpr (SUB == 1) return __all_sync(kFull, over);
+            else return (__ballot_sync(kFull, over) & seg) == seg;
         };
         using P0 = std::integral_constant<int, 0>;
         using P1 = std::integral_constant<int, 1>;
-        int d = 1;
-        if (d <= dend && ((d + b) & 1)) {   // start on parity 1 so the loop below alternates 0, 1
-            const bool o = step(d, P1{});
-            prev_over = o;
-            ++d;
-        }
-        for (; d <= dend && !rejected; d += 2) {
-            bool o = step(d, P0{});
-            if (o && prev_over) { rejected = true; break; }
-            prev_over = o;
-            if (d + 1 > dend) break;
-            o = step(d + 1, P1{});
-            if (o && prev_over) { rejected = true; break; }
-            prev_over = o;
-        }
-        if (rejected) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
-            continue;
+        if constexpr (SUB == 1) {
+            bool rejected = false;
+            int d = 1;
+            if (d <= dend && ((d + b) & 1)) {   // start on parity 1 so the loop below alternates 0, 1
+                prev_over = step(d, P1{});
+                ++d;
+            }
+            for (; d <= dend; d += 2) {
+                bool o = step(d, P0{});
+                if (o && prev_over) { rejected = true; break; }
+                prev_over = o;
+                if (d + 1 > dend) break;
+                o = step(d + 1, P1{});
+                if (o && prev_over) { rejected = true; break; }
+                prev_over = o;
+            }
+            if (rejected) {
+                if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
+                continue;
+            }
+        } else {
+            // a segment whose pair is rejected (two consecutive anti-diagonals over the limit, inside its own
+            // range) stops computing: its ranges are emptied.  The warp runs while any segment's pair is live; a
+            // segment past its own last anti-diagonal has finished and takes no further decision.
+            auto rejects = [&](bool o, int dd) {
+                if (!live || dd > dend) return;
+                if (o && prev_over) {
+                    live = false;
+#pragma unroll
+                    for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                        for (int r = 0; r < R; ++r) dlo[pp][r] = 1 << 30;
+                    if (sl == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
+                }
+                prev_over = o;
+            };
+            int d = 1;
+            if (d <= dmax && ((d + b) & 1)) {
+                rejects(step(d, P1{}), d);
+                ++d;
+            }
+            for (; d <= dmax; d += 2) {
+                rejects(step(d, P0{}), d);
+                if (!__any_sync(kFull, live)) break;
+                if (d + 1 > dmax) break;
+                rejects(step(d + 1, P1{}), d + 1);
+                if (!__any_sync(kFull, live)) break;
+            }
         }
         // values at (n, m)
-        const int qe = kend + b, ie = qe >> 1, pe = qe & 1, re = ie >> 5, je = ie & 31;
+        const int qe = kend + b, ie = qe >> 1, pe = qe & 1, re = ie / GS, je = ie % GS;
         int32_t eM = kInf, eI = kInf, eD = kInf;
+        if constexpr (SUB == 1) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-            if (r == re) {
-                eM = pe ? Ms[1][r] : Ms[0][r]; eI = pe ? Is[1][r] : Is[0][r]; eD = pe ? Ds[1][r] : Ds[0][r];
-            }
-        eM = __shfl_sync(kFull, eM, je); eI = __shfl_sync(kFull, eI, je); eD = __shfl_sync(kFull, eD, je);
-        const int32_t s = min3(eM, eI, eD);
-        if (s > limc) {
-            if (lane == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
-            continue;
+            for (int r = 0; r < R; ++r)
+                if (r == re) {
+                    eM = pe ? Ms[1][r] : Ms[0][r]; eI = pe ? Is[1][r] : Is[0][r]; eD = pe ? Ds[1][r] : Ds[0][r];
+                }
+        } else {
+            (void)re; (void)pe;
+            eM = xM; eI = xI; eD = xD;
         }
-        if (lane == 0) pend[npend] = make_int4((int)pi, s, (int)((eM == s) | (eI == s) << 1 | (eD == s) << 2), 0);
-        if (++npend == a.defer) {
-            dp_finish<UNIT, R>(a, warp_slots, pend, npend, lane);
-            npend = 0;
+        const int src = sg * GS + (live ? je : 0);
+        eM = __shfl_sync(kFull, eM, src); eI = __shfl_sync(kFull, eI, src); eD = __shfl_sync(kFull, eD, src);
+        const int32_t sc = min3(eM, eI, eD);
+        if (live && sc > limc) {
+            if (sl == 0) write_header(a.O, pi, -1, AIM_F_REJECTED, 0);
+            live = false;
+        }
+        if constexpr (SUB == 1) {   // a slot only for an aligned pair
+            if (!live) continue;
+            if (lane == 0) pend[npend] = make_int4((int)pi, sc, (int)((eM == sc) | (eI == sc) << 1 | (eD == sc) << 2), 0);
+            if (++npend == a.defer) {
+                dp_finish<UNIT, RW>(a, warp_slots, pend, npend, lane);
+                npend = 0;
+            }
+        } else {   // a round of SUB slots, empty for a segment whose pair was rejected or flagged
+            if (sl == 0)
+                pend[slot_i] = live ? make_int4((int)pi, sc, (int)((eM == sc) | (eI == sc) << 1 | (eD == sc) << 2), 0)
+                                    : make_int4(-1, 0, 0, 0);
+            npend += SUB;
+            if (npend + SUB > a.defer) {
+                dp_finish<UNIT, RW>(a, warp_slots, pend, npend, lane);
+                npend = 0;
+            }
         }
     }
-    dp_finish<UNIT, R>(a, warp_slots, pend, npend, lane);
+    dp_finish<UNIT, RW>(a, warp_slots, pend, npend, lane);
     warp_stat_add(a.O.stats, 2, st_cells, lane);
     warp_stat_add(a.O.stats, 3, st_pairs, lane);
 }
 
-template <bool UNIT, int R>
+template <bool UNIT, int R, int SUB>
 cudaError_t launch_t(const DpArgs& args0, int num_sms, cudaStream_t st, int* warps_used, size_t scratch_bytes) {
     int bps = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dp_kernel<UNIT, R>, 256, 0);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dp_kernel<UNIT, R, SUB>, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     size_t warps = (size_t)num_sms * bps * 8;
-    const size_t fit = scratch_bytes / args0.slot_bytes;
+    const size_t fit = scratch_bytes / (args0.slot_bytes * SUB);   // a warp needs a slot per segment at least
     if (warps > fit) warps = fit;
-    if (warps > args0.P.num_pairs) warps = args0.P.num_pairs;
+    const size_t need = (args0.P.num_pairs + SUB - 1) / SUB;
+    if (warps > need) warps = need;
     if (warps == 0) { *warps_used = 0; return cudaSuccess; }
     DpArgs a = args0;
     a.nwarps = (uint32_t)warps;
-    // slots per warp: the scratch spread over the launch's warps, up to one per lane
+    // slots per warp: the scratch spread over the launch's warps, up to one per lane, a whole number of rounds
     const size_t per_warp = scratch_bytes / warps / args0.slot_bytes;
-    a.defer = (uint32_t)(per_warp > 32 ? 32 : per_warp);
+    a.defer = (uint32_t)((per_warp > 32 ? 32 : per_warp) / SUB * SUB);
     const unsigned blocks = (unsigned)((warps + 7) / 8);
-    dp_kernel<UNIT, R><<<blocks, 256, 0, st>>>(a);
+    dp_kernel<UNIT, R, SUB><<<blocks, 256, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
 }
@@ -371,9 +455,11 @@ DpPlan plan_dp(bool unit, int band, uint32_t max_length, int64_t max_limit) {
     p.unit = unit;
     p.band = band;
     p.blocks = band <= 31 ? 1 : band <= 63 ? 2 : 4;
+    // narrow bands: several pairs per warp, one per segment of 32 / pairs lanes (2b + 1 diagonals on 2 per lane)
+    p.pairs_per_warp = band <= 7 ? 4 : band <= 15 ? 2 : 1;
     const size_t te = unit ? 1 : 2;
     const size_t rows = 2 * (size_t)max_length + 1;
-    const size_t trace = align_up(rows * 32 * p.blocks * te, 16);
+    const size_t trace = align_up(rows * (32 / p.pairs_per_warp) * p.blocks * te, 16);
     p.slot_bytes = trace;   // run staging appended by launch_dp
     (void)max_limit;
     return p;
@@ -398,13 +484,17 @@ cudaError_t launch_dp(const DpPlan& plan, const Costs& c, const PairsView& P, co
     a.trace_bytes = plan.slot_bytes;
     a.slot_bytes = align_up(plan.slot_bytes + (size_t)cap * 4, 128);
     if (plan.unit) {
-        if (plan.blocks == 1) return launch_t<true, 1>(a, num_sms, st, warps_used, scratch_bytes);
-        if (plan.blocks == 2) return launch_t<true, 2>(a, num_sms, st, warps_used, scratch_bytes);
-        return launch_t<true, 4>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.pairs_per_warp == 4) return launch_t<true, 1, 4>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.pairs_per_warp == 2) return launch_t<true, 1, 2>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.blocks == 1) return launch_t<true, 1, 1>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.blocks == 2) return launch_t<true, 2, 1>(a, num_sms, st, warps_used, scratch_bytes);
+        return launch_t<true, 4, 1>(a, num_sms, st, warps_used, scratch_bytes);
     }
-    if (plan.blocks == 1) return launch_t<false, 1>(a, num_sms, st, warps_used, scratch_bytes);
-    if (plan.blocks == 2) return launch_t<false, 2>(a, num_sms, st, warps_used, scratch_bytes);
-    return launch_t<false, 4>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.pairs_per_warp == 4) return launch_t<false, 1, 4>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.pairs_per_warp == 2) return launch_t<false, 1, 2>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.blocks == 1) return launch_t<false, 1, 1>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.blocks == 2) return launch_t<false, 2, 1>(a, num_sms, st, warps_used, scratch_bytes);
+    return launch_t<false, 4, 1>(a, num_sms, st, warps_used, scratch_bytes);
 }
 
 }  // namespace aim

@@ -404,3 +404,20 @@ def test_wfa_adaptive_hand_worked_pruning(aligner, oracle_lib, lanes):
     finally:
         aim.aim_set_wfa_group(aligner.ctx, 0)
         aim.aim_set_wfa_adaptive(aligner.ctx, 10, 50)
+
+
+@pytest.mark.parametrize("algo,band", [("edit", 6), ("edit", 10), ("gotoh", 7), ("gotoh", 12)])
+def test_dp_several_pairs_per_warp(oracle_lib, gen_lib, algo, band):
+    """Narrow bands run 4 (band <= 7) or 2 (band <= 15) pairs per warp, one per segment of 8 or 16 lanes, each
+    with its own length, early exit and deferred traceback slot; with 40 MiB, 320 MiB and 4 GiB of workspace
+    (one round of slots per flush up to 32 slots)."""
+    w = gen.WFA_150BP
+    p = gen.generate(w, 12_007)
+    pen = AFF if algo == "gotoh" else oracle.UNIT
+    max_edits = band if algo == "edit" else 3
+    lim = np.array([oracle.limit_for(pen, max_edits, unit=algo == "edit")] * len(p), np.int64)
+    orc = oracle_results(p, pen, lim, band=band)
+    assert ((orc[1] & oracle.F_REJECTED) > 0).sum() > 100 and (orc[1] == 0).sum() > 100
+    for ws in (40 << 20, 320 << 20, 4 << 30):
+        dev = device_results(p, algo, pen, max_edits, band=band, workspace=ws)
+        assert_same(dev, orc, what=f"{algo} band {band} workspace={ws >> 20} MiB")
