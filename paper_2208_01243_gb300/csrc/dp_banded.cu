@@ -286,30 +286,30 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
                         if (UNIT) {
                             Mv = cap_inf(dM + delta);
                         } else {
-                            Mv = cap_inf(min3(dM, dI, dD) + delta);
-                            if (Mv < kInf)
-                                bits |= (dM + delta == Mv ? 1u : 0u) | (dI + delta == Mv ? 2u : 0u) |
-                                        (dD + delta == Mv ? 4u : 0u);
+                            // the mismatch cost is common to the three predecessors: compare them with their
+                            // minimum.  (Bits of an unreachable cell are never read: the traceback walks reachable
+                            // cells only, so no test of the value against infinity is needed.)
+                            const int32_t mn = min3(dM, dI, dD);
+                            Mv = cap_inf(mn + delta);
+                            bits |= (dM == mn ? 1u : 0u) | (dI == mn ? 2u : 0u) | (dD == mn ? 4u : 0u);
                         }
                     }
                     if (v >= 1) {
                         if (UNIT) {
                             Iv = cap_inf(uM + 1);
                         } else {
-                            Iv = cap_inf(min3(uM + oe, uD + oe, uI + e));
-                            if (Iv < kInf)
-                                bits |= (uM + oe == Iv ? 8u : 0u) | (uD + oe == Iv ? 16u : 0u) |
-                                        (uI + e == Iv ? 32u : 0u);
+                            const int32_t a0 = uM + oe, a1 = uD + oe, a2 = uI + e, mn = min3(a0, a1, a2);
+                            Iv = cap_inf(mn);
+                            bits |= (a0 == mn ? 8u : 0u) | (a1 == mn ? 16u : 0u) | (a2 == mn ? 32u : 0u);
                         }
                     }
                     if (h >= 1) {
                         if (UNIT) {
                             Dv = cap_inf(lM + 1);
                         } else {
-                            Dv = cap_inf(min3(lM + oe, lI + oe, lD + e));
-                            if (Dv < kInf)
-                                bits |= (lM + oe == Dv ? 64u : 0u) | (lI + oe == Dv ? 128u : 0u) |
-                                        (lD + e == Dv ? 256u : 0u);
+                            const int32_t a0 = lM + oe, a1 = lI + oe, a2 = lD + e, mn = min3(a0, a1, a2);
+                            Dv = cap_inf(mn);
+                            bits |= (a0 == mn ? 64u : 0u) | (a1 == mn ? 128u : 0u) | (a2 == mn ? 256u : 0u);
                         }
                     }
                     if (UNIT) {
