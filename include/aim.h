@@ -330,6 +330,26 @@ AIM_API int aim_batch_info(aim_batch *batch, int *groups /* host[32] */, uint32_
  */
 AIM_API int aim_batch_passes(aim_batch *batch, int *first_pass /* host[32] */, int *full_pass /* host[32] */);
 AIM_API int aim_set_batch_compact(aim_ctx *ctx, int mode);
+/*
+ * Bound pass.  The exact algorithm clamps each wavefront to the diagonals
+ * that can still end within the pair's limit (every gap base costs at least
+ * the gap-extension cost), so a pair whose optimum lies far below its limit
+ * gains little from the clamp.  A bucket can therefore first run a bound
+ * pass: a forward pass of the same recurrences that keeps only the diagonals
+ * within a few bases of the one closest to the end, stores no history and
+ * traces nothing back.  The score at which it reaches the end is that of a
+ * real alignment, so it bounds the optimum from above; the exact pass then
+ * runs with min(limit, bound) as the pair's limit, and its clamp keeps only
+ * a diamond around the optimal paths.  Scores, flags and CIGARs are those of
+ * the exact pass alone.  aim_batch_bound_passes reports, per bucket, the
+ * bound pass's lanes per pair (0: none) and returns the number of buckets
+ * with one.  aim_set_batch_bound sets how later plans of the context choose:
+ * 0 (default) by timed trials when autotuning, 1 always (reads up to 32,000
+ * bp), 2 never.  Plans with a compact first pass run no bound pass.  Work
+ * counters [0] and [1] include the bound pass's entries and windows.
+ */
+AIM_API int aim_batch_bound_passes(aim_batch *batch, int *bound_pass /* host[32] */);
+AIM_API int aim_set_batch_bound(aim_ctx *ctx, int mode);
 AIM_API int aim_batch_destroy(aim_batch *batch);
 
 /*

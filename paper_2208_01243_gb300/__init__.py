@@ -72,6 +72,8 @@ def _lib():
         lib.aim_set_genasm_window.argtypes = [p, ctypes.c_int, ctypes.c_int]
         lib.aim_set_batch_compact.argtypes = [p, ctypes.c_int]
         lib.aim_batch_passes.argtypes = [p, p, p]
+        lib.aim_set_batch_bound.argtypes = [p, ctypes.c_int]
+        lib.aim_batch_bound_passes.argtypes = [p, p]
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
@@ -295,6 +297,21 @@ def aim_batch_passes(plan) -> tuple[list[int], list[int], int]:
     if n < 0:
         _check(n, "aim_batch_passes")
     return first.tolist(), full.tolist(), int(n)
+
+
+def aim_set_batch_bound(ctx, mode: int = 0) -> None:
+    """Batch plans of this context: 0 tuner decides on bound passes, 1 always, 2 never."""
+    _check(_lib().aim_set_batch_bound(ctx, int(mode)), "aim_set_batch_bound")
+
+
+def aim_batch_bound_passes(plan) -> tuple[list[int], int]:
+    """(bound-pass lanes per bucket (0: none), buckets with a bound pass)."""
+    import numpy as np
+    lanes = np.zeros(32, np.int32)
+    n = _lib().aim_batch_bound_passes(plan, ctypes.c_void_p(lanes.ctypes.data))
+    if n < 0:
+        _check(n, "aim_batch_bound_passes")
+    return lanes.tolist(), int(n)
 
 
 def aim_set_genasm_window(ctx, window: int = 64, overlap: int = 24) -> None:

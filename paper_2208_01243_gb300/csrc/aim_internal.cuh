@@ -132,7 +132,17 @@ struct WfaPlan {
     int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
     int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end
     int retry_only;      // launch aligns only the pairs a previous pass flagged AIM_F_STEP_CAP
+    int32_t* bound;      // per pair: a scaled score some alignment reaches (written by a bound pass, -1: none);
+                         // exact launches take min(limit, bound) as the pair's limit when set (null: none)
+    int bound_pass;      // the launch is a bound pass: pruned, no history, no traceback; writes bound
+    int bound_min_len, bound_max_dist;   // the bound pass's pruning (as adapt_min_len, adapt_max_dist)
 };
+// the bound pass's pruning: wavefronts of at least kBoundMinLen diagonals keep those within kBoundMaxDist of the
+// diagonal closest to the end
+constexpr int kBoundMinLen = 4;
+constexpr int kBoundMaxDist = 8;
+// scratch one pair of a bound pass needs (meta records and the live ring)
+size_t wfa_bound_pair_bytes(const WfaPlan& p);
 // the plan with its history sized for wavefronts at most `width` diagonals wide (a compact first pass)
 WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width);
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
@@ -174,6 +184,7 @@ struct WfaArgs {
     int nbuckets;
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive pruning and source-following traceback (min_len < 0: off)
     int retry_only;            // align only pairs whose flag is AIM_F_STEP_CAP (a second pass with larger scratch)
+    int32_t* bound;            // per-pair scaled score bounds: the bound pass writes them, exact passes read them
     int16_t group[kMaxBuckets]; // lanes per pair of each bucket (1..32, or 256: a whole block)
 };
 
@@ -285,6 +296,7 @@ struct aim_ctx {
     int adapt_min_len, adapt_max_dist;   // WFA-adaptive parameters
     int genasm_w, genasm_o;       // GenASM window and overlap
     int batch_compact;            // batch plans: 0 tuner decides on compact first passes, 1 always, 2 never
+    int batch_bound;              // batch plans: 0 tuner decides on bound passes, 1 always, 2 never
     void* tune_cache;             // autotuner choices (owned; see batch.cu)
     void* host_pipe;              // buffers, streams and plans of aim_align_batch_host (owned; see host.cu)
 };

@@ -273,6 +273,7 @@ int aim_create(aim_ctx** out, int device, size_t workspace_bytes) {
     c->genasm_w = 64;
     c->genasm_o = 24;
     c->batch_compact = 0;
+    c->batch_bound = 0;
     c->host_pipe = nullptr;
     *out = c;
     return AIM_OK;
@@ -328,6 +329,12 @@ int aim_set_wfa_adaptive(aim_ctx* ctx, int min_length, int max_distance) {
 int aim_set_batch_compact(aim_ctx* ctx, int mode) {
     if (!ctx || mode < 0 || mode > 2) return AIM_ERR_ARG;
     ctx->batch_compact = mode;
+    return AIM_OK;
+}
+
+int aim_set_batch_bound(aim_ctx* ctx, int mode) {
+    if (!ctx || mode < 0 || mode > 2) return AIM_ERR_ARG;
+    ctx->batch_bound = mode;
     return AIM_OK;
 }
 

@@ -34,6 +34,17 @@
 // flags them AIM_F_STEP_CAP; a count/scan/scatter over those flags builds the
 // second pass's queues on the device).  Both passes run the exact algorithm,
 // so results do not depend on which pairs were retried.
+//
+// Bound pass.  An exact pass clamps every wavefront to the diagonals that can
+// still end within the pair's limit S; a pair whose optimum lies far below S
+// computes wavefronts that the clamp barely touches.  A bound pass first runs
+// a pruned forward pass (no history, no traceback, wavefronts of a few
+// diagonals) whose end score U is the cost of a real alignment, so the
+// optimum is at most U; the exact pass then takes min(S, U) as the pair's
+// limit and clamps its wavefronts to a diamond around the optimal path.  The
+// scores and CIGARs are those of the exact pass alone (the optimum and every
+// entry on an optimal path survive the clamp), so the tuner may add a bound
+// pass to any bucket it makes faster.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -155,6 +166,8 @@ size_t bucket_pair_bytes(const WfaPlan& plan, int b, int G) {
 }
 
 constexpr int kCompactDiagonalsPerLane = 16;   // first-pass history: wavefronts of about 16 diagonals per lane
+constexpr int kBoundDefaultGroup = 8;          // lanes per pair of a forced bound pass
+constexpr float kBoundGain = 0.97f;            // a bound pass must save at least 3 % of the bucket's trial time
 
 // scratch one pair of bucket b gets in a compact first pass with G lanes per pair
 size_t bucket_compact_bytes(const WfaPlan& plan, int b, int G) {
@@ -195,11 +208,14 @@ struct aim_batch {
     size_t scratch_bytes, warp_bytes;   // warp_bytes: the full-scratch pass
     int groups[aim::kBuckets];          // lanes per pair with the bucket's full scratch
     int groups1[aim::kBuckets];         // lanes per pair of a compact first pass (0: the bucket runs in one pass)
+    int bound1[aim::kBuckets];          // lanes per pair of a bound pass before the exact one (0: none)
+    int32_t* bound;                     // per pair: the bound pass's score (scaled), -1: none
     bool two_pass;
     size_t warp_bytes1;                 // the first pass's scratch per warp when two_pass
     uint32_t *rcounts, *rbounds, *rfill, *rclaims, *rorder;   // second-pass queues
     uint32_t* gbounds;                  // queue range of each group of buckets sharing lanes per pair
     int ggroup[aim::kBuckets];          // lanes per pair of each group
+    int gbound[aim::kBuckets];          // lanes per pair of each group's bound pass (0: none)
     size_t gwarp_bytes[aim::kBuckets];  // scratch per warp of each group
     uint32_t host_counts[aim::kBuckets];
     aim::BucketParams bp;
@@ -215,7 +231,7 @@ namespace aim {
 namespace {
 
 using TuneKey = std::tuple<int, int, int, int, int, int64_t>;   // x, o, e, band, bucket, smax
-using TuneChoice = std::pair<int, int>;                         // full-scratch lanes, compact first-pass lanes
+using TuneChoice = std::tuple<int, int, int>;   // full-scratch lanes, compact first-pass lanes, bound-pass lanes
 std::map<TuneKey, TuneChoice>& tune_cache(aim_ctx* ctx) {
     if (!ctx->tune_cache) ctx->tune_cache = new std::map<TuneKey, TuneChoice>();
     return *static_cast<std::map<TuneKey, TuneChoice>*>(ctx->tune_cache);
@@ -240,11 +256,31 @@ cudaError_t enqueue_prepare(aim_batch* b, cudaStream_t st) {
 
 cudaError_t enqueue_align(aim_batch* b, cudaStream_t st, int* warps) {
     if (!b->two_pass) {
-        // one launch per group of buckets sharing lanes per pair, each over one contiguous queue range
+        // one launch per group of buckets sharing lanes per pair (and bound-pass lanes), each over one contiguous
+        // queue range; a group with a bound pass first runs it over the same range (claim counters of their own)
         *warps = 0;
+        bool any_bound = false;
+        for (int j = 0; j < b->bp.ngroups; ++j) any_bound |= b->gbound[j] != 0;
+        if (any_bound) {
+            const cudaError_t e = cudaMemsetAsync(b->rclaims, 0, kBuckets * sizeof(uint32_t), st);
+            if (e != cudaSuccess) return e;
+        }
         for (int j = 0; j < b->bp.ngroups; ++j) {
             int w = 0;
-            const cudaError_t e = launch_wfa_buckets(b->plan, b->P, b->r.lim, b->O, b->order, b->gbounds + j,
+            WfaPlan exact = b->plan;
+            if (b->gbound[j]) {
+                WfaPlan bp = b->plan;
+                bp.bound = b->bound;
+                bp.bound_pass = 1;
+                const size_t wb = wfa_warp_bytes(b->gbound[j], wfa_bound_pair_bytes(b->plan));
+                const cudaError_t e = launch_wfa_buckets(bp, b->P, b->r.lim, b->O, b->order, b->gbounds + j,
+                                                         &b->gbound[j], 1, wb, b->scratch, b->scratch_bytes,
+                                                         b->rclaims + j, b->ctx->num_sms, st, &w);
+                if (e != cudaSuccess) return e;
+                if (w == 0) { *warps = 0; return cudaSuccess; }
+                exact.bound = b->bound;
+            }
+            const cudaError_t e = launch_wfa_buckets(exact, b->P, b->r.lim, b->O, b->order, b->gbounds + j,
                                                      &b->ggroup[j], 1, b->gwarp_bytes[j], b->scratch,
                                                      b->scratch_bytes, b->claims + j, b->ctx->num_sms, st, &w);
             if (e != cudaSuccess) return e;
@@ -351,10 +387,33 @@ int autotune(aim_batch* b) {
                 if (e == cudaSuccess && ms1 + ms2 < best) { best = ms1 + ms2; best_g1 = G1; }
             }
         }
+        // a bound pass, then the exact pass clamped at each pair's bound (only where no compact pass was chosen)
+        int best_gb = 0;
+        if (best_g1 == 0 && b->ctx->batch_bound != 2 && b->max_length <= kMaxWfaLength16 && best_g <= 32) {
+            WfaPlan bp = b->plan, ep = b->plan;
+            bp.bound = ep.bound = b->bound;
+            bp.bound_pass = 1;
+            const size_t wb_full = wfa_warp_bytes(best_g, bucket_pair_bytes(b->plan, k, best_g));
+            const size_t bpb = wfa_bound_pair_bytes(b->plan);
+            if (b->ctx->batch_bound == 1) {
+                best_gb = kBoundDefaultGroup;   // forced: the default lanes, no trials
+            } else {
+                for (int Gb : {4, 8, 16, 32}) {
+                    if (Gb > std::max(best_g, 4) || wfa_warp_bytes(Gb, bpb) * min_warps > b->scratch_bytes) continue;
+                    float ms1 = 0.f, ms2 = 0.f;
+                    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+                        e = trial(b, bp, tb, Gb, wfa_warp_bytes(Gb, bpb), t0, t1, &ms1);
+                        if (e == cudaSuccess) e = trial(b, ep, tb, best_g, wb_full, t0, t1, &ms2);
+                    }
+                    if (e == cudaSuccess && ms1 + ms2 < kBoundGain * best) { best = ms1 + ms2; best_gb = Gb; }
+                }
+            }
+        }
         b->groups[k] = best_g;
         b->groups1[k] = best_g1;
+        b->bound1[k] = best_gb;
         tune_cache(b->ctx)[TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, b->pen.band, k, b->plan.smax)] =
-            TuneChoice(best_g, best_g1);
+            TuneChoice(best_g, best_g1, best_gb);
     }
     cudaEventDestroy(t0);
     cudaEventDestroy(t1);
@@ -420,10 +479,11 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
     for (int k = 0; k < kBuckets; ++k) {
         b->groups[k] = default_group_for_bucket(k, max_length);
         b->groups1[k] = 0;
+        b->bound1[k] = 0;
         if (ctx->tune_cache) {
             auto& c = tune_cache(ctx);
             auto it = c.find(TuneKey(b->r.costs.x, b->r.costs.o, b->r.costs.e, pen->band, k, b->plan.smax));
-            if (it != c.end()) { b->groups[k] = it->second.first; b->groups1[k] = it->second.second; }
+            if (it != c.end()) std::tie(b->groups[k], b->groups1[k], b->bound1[k]) = it->second;
         }
     }
     // owned memory: packed sequences, flags, bucket arrays, order, scratch
@@ -432,7 +492,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
     const size_t small_bytes = align_up(10 * (kBuckets + 1) * sizeof(uint32_t), 256);
     const size_t order_bytes = align_up((size_t)num_pairs * sizeof(uint32_t), 256);
     b->scratch_bytes = ext_scratch ? ext_scratch_bytes : scratch_bytes ? scratch_bytes : ctx->ws_bytes;
-    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 2 * order_bytes + (ext_scratch ? 0 : b->scratch_bytes);
+    b->mem_bytes = 2 * seq_bytes + 2 * flag_bytes + small_bytes + 3 * order_bytes + (ext_scratch ? 0 : b->scratch_bytes);
     cudaError_t e = cudaMalloc(&b->mem, b->mem_bytes);
     if (e != cudaSuccess) { cudaGetLastError(); free_batch(b); return AIM_ERR_NOMEM; }
     uint8_t* p = b->mem;
@@ -448,6 +508,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
     b->gbounds = sm + 9 * (kBuckets + 1);
     b->order = reinterpret_cast<uint32_t*>(p); p += order_bytes;
     b->rorder = reinterpret_cast<uint32_t*>(p); p += order_bytes;
+    b->bound = reinterpret_cast<int32_t*>(p); p += order_bytes;
     b->scratch = ext_scratch ? ext_scratch : p;
     b->P = PairsView{b->pr, b->pt, nullptr, nullptr, read_lengths, target_lengths, b->br, b->bt, num_pairs, max_length};
     b->P.stride = b->stride;
@@ -463,18 +524,24 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
     if (autotune) {
         rc = aim::autotune(b);
         if (rc) { free_batch(b); return rc; }
-    } else if (ctx->batch_compact != 0) {
-        // without trials: forced compact first passes where they fit, or none
+    } else {
+        // without trials: forced compact first passes where they fit, or none; forced bound passes, or none
         for (int k = 0; k < kBuckets; ++k) {
-            b->groups1[k] = 0;
-            if (ctx->batch_compact != 1 || !b->host_counts[k]) continue;
-            for (int G1 : {4, 8, 16, 32})
-                if (compact_allowed(b, k, G1, b->groups[k])) { b->groups1[k] = G1; break; }
+            if (ctx->batch_compact != 0) {
+                b->groups1[k] = 0;
+                if (ctx->batch_compact == 1 && b->host_counts[k])
+                    for (int G1 : {4, 8, 16, 32})
+                        if (compact_allowed(b, k, G1, b->groups[k])) { b->groups1[k] = G1; break; }
+            }
+            if (ctx->batch_bound == 2) b->bound1[k] = 0;
+            if (ctx->batch_bound == 1)   // bound passes run 4 to 32 lanes per pair, whatever the exact pass uses
+                b->bound1[k] = b->max_length <= kMaxWfaLength16 && b->groups[k] <= 32 && !b->groups1[k]
+                                   ? kBoundDefaultGroup : 0;
         }
     }
     // buckets empty at planning keep one pair per warp, so their worst case does not shrink the grid
     for (int k = 0; k < kBuckets; ++k)
-        if (!b->host_counts[k]) { b->groups[k] = 32; b->groups1[k] = 0; }
+        if (!b->host_counts[k]) { b->groups[k] = 32; b->groups1[k] = 0; b->bound1[k] = 0; }
     // scratch per warp of the full pass: the largest need over all buckets (a replay may see a different mix)
     size_t wb = 0;
     for (int k = 0; k < kBuckets; ++k)
@@ -497,21 +564,21 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
         }
         b->warp_bytes1 = std::max<size_t>(wb1, 16);
     } else {
-        // one pass: the buckets sharing lanes per pair become one contiguous queue range (groups in the order
-        // of their heaviest bucket, buckets heaviest first inside), and each group is one launch of the kernel
-        // compiled for its group size, with scratch per warp sized for that group alone
+        // one pass: the buckets sharing lanes per pair (and bound-pass lanes) become one contiguous queue range
+        // (groups in the order of their heaviest bucket, buckets heaviest first inside), and each group is one
+        // launch of the kernel compiled for its group size, with scratch per warp sized for that group alone
         int ng = 0;
         for (int k = 0; k < kBuckets; ++k) {
             bool seen = false;
-            for (int j = 0; j < ng; ++j) seen |= b->ggroup[j] == b->groups[k];
-            if (!seen) b->ggroup[ng++] = b->groups[k];
+            for (int j = 0; j < ng; ++j) seen |= b->ggroup[j] == b->groups[k] && b->gbound[j] == b->bound1[k];
+            if (!seen) { b->ggroup[ng] = b->groups[k]; b->gbound[ng] = b->bound1[k]; ++ng; }
         }
         int next = 0;
         for (int j = 0; j < ng; ++j) {
             b->bp.gstart[j] = (int8_t)next;
             size_t wbj = 16;
             for (int k = 0; k < kBuckets; ++k) {
-                if (b->groups[k] != b->ggroup[j]) continue;
+                if (b->groups[k] != b->ggroup[j] || b->bound1[k] != b->gbound[j]) continue;
                 b->bp.perm[k] = (int8_t)next++;
                 wbj = std::max(wbj, wfa_warp_bytes(b->groups[k], bucket_pair_bytes(b->plan, k, b->groups[k])));
             }
@@ -611,6 +678,16 @@ int aim_batch_passes(aim_batch* b, int* first_pass, int* full_pass) {
         compact += b->groups1[k] != 0;
     }
     return compact;
+}
+
+int aim_batch_bound_passes(aim_batch* b, int* bound_pass) {
+    if (!b || !bound_pass) return AIM_ERR_ARG;
+    int n = 0;
+    for (int k = 0; k < aim::kBuckets; ++k) {
+        bound_pass[k] = b->two_pass ? 0 : b->bound1[k];
+        n += bound_pass[k] != 0;
+    }
+    return n;
 }
 
 int aim_batch_destroy(aim_batch* b) {

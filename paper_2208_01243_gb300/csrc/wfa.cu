@@ -106,9 +106,13 @@ __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, i
 //           following those bits back to the gap's opening.  A quarter of kFmt8's history bytes.
 //   kFmt32  the same with 32-bit words (h + 1 in bits 0-29, source bits 30 and 31) and int32 live entries, for
 //           reads beyond 16,382 bp: half of kFmt8's bytes, and no 32,000 bp limit.
-enum : int { kFmt8 = 0, kFmt16 = 1, kFmt32 = 2 };
+//   kFmtBound  no history at all, only the live ring (int16 entries): the bound pass, a pruned forward pass whose
+//           only result is the score at which it reached the end (an upper bound on the pair's optimum, since
+//           every entry it computes is an offset some path of that score reaches), for a following exact pass to
+//           clamp its wavefronts with.
+enum : int { kFmt8 = 0, kFmt16 = 1, kFmt32 = 2, kFmtBound = 3 };
 template <int FMT>
-struct FmtT {                       // kFmt8, kFmt16
+struct FmtT {                       // kFmt8, kFmt16, kFmtBound
     using V = int16_t;              // live value type
     using H = uint16_t;             // history word (compact forms)
     static constexpr int kNeg = kNeg16;
@@ -314,7 +318,9 @@ template <int G, bool ADAPT, bool STAGE, int FMT>
 __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* region, size_t region_bytes, uint32_t q0,
                                                 uint32_t qend, uint32_t lane, Counters& st) {
     static_assert(!STAGE || G <= 32, "sequence staging is per group of a warp");
-    static_assert(FMT == kFmt8 || (!ADAPT && !STAGE), "compact histories are for the exact, unstaged kernels");
+    static_assert(FMT == kFmt8 || FMT == kFmtBound || (!ADAPT && !STAGE),
+                  "compact histories are for the exact, unstaged kernels");
+    static_assert(FMT != kFmtBound || (ADAPT && G <= 32), "the bound pass prunes, with groups of up to 32 lanes");
     using V = typename FmtT<FMT>::V;
     using H = typename FmtT<FMT>::H;
     constexpr int kNeg = FmtT<FMT>::kNeg;
@@ -327,9 +333,9 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     int16_t* hist = reinterpret_cast<int16_t*>(region + a.meta_bytes + a.runs_bytes);
     H* hc = reinterpret_cast<H*>(region + a.meta_bytes + a.runs_bytes);
     V* live = reinterpret_cast<V*>(region + region_bytes - (FMT == kFmt8 ? 0 : a.live_bytes));
-    const size_t hist_cap = FMT == kFmt8
-        ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
-        : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
+    const size_t hist_cap = FMT == kFmtBound ? ~(size_t)0 >> 1   // no history
+        : FMT == kFmt8 ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
+                       : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
     const int center = (int)(a.live_w / 2);
     const int X = a.X, OE = a.OE, E = a.E;
 
@@ -355,6 +361,14 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             status = kRun;
             int64_t S64 = lim / a.g;
             S = (int)(S64 > a.smax ? a.smax : S64);
+            if constexpr (FMT != kFmtBound) {
+                // a bound pass found an alignment of score ub (scaled): the optimum is at most ub, so a limit of ub
+                // rejects nothing the limit S would accept, and the reach clamp below keeps fewer diagonals
+                if (a.bound) {
+                    const int ub = a.bound[pi];
+                    if (ub >= 0 && ub < S) S = ub;
+                }
+            }
             Pw = read_words(a.P, pi);
             Tw = target_words(a.P, pi);
             nwP = (uint32_t)(n + 31) >> 5;
@@ -362,7 +376,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             klo = a.band >= 0 ? max(-n, -a.band) : -n;
             khi = a.band >= 0 ? min(m, a.band) : m;
         }
-        if (gl == 0) st.pairs += 1;
+        if (gl == 0 && FMT != kFmtBound) st.pairs += 1;
     }
 
     // the extend's view of the pair: with STAGE, the group's copy in shared memory (a spare zero word after
@@ -411,7 +425,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         } else {   // live slot 0 at diagonal 0; history word 0
             V* e0 = live + (size_t)center * kEntryElems;
             e0[0] = (V)m0; e0[1] = (V)kNeg; e0[2] = (V)kNeg; e0[3] = 0;
-            hc[0] = hist_word<FMT>(m0, false, false);
+            if constexpr (FMT != kFmtBound) hc[0] = hist_word<FMT>(m0, false, false);
         }
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
         if (kRing && ring) ring[0] = make_int4(0, 0, 0, 1);
@@ -448,7 +462,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
-            if constexpr (!ADAPT) {
+            if constexpr (!ADAPT || FMT == kFmtBound) {
                 // threshold: a path through diagonal k at score s still has to reach the end diagonal, a gap of
                 // |k - kend| bases costing at least E each, so only diagonals within (S - s) / E of kend can lie on
                 // an alignment of score <= S.  The sources of every entry kept lie within the same bound, so each
@@ -501,12 +515,12 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                     // (the spare slot, bits 48-63, takes del's sign bits: nothing reads it)
                 } else {
                     V* e = live + (size_t)(live_slot + k) * kEntryElems;
-                    if constexpr (FMT == kFmt16)
+                    if constexpr (FMT != kFmt32)
                         *reinterpret_cast<uint64_t*>(e) = (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) |
                                                           ((uint64_t)(uint32_t)del << 32);
                     else
                         *reinterpret_cast<int4*>(e) = make_int4(mv, ins, del, 0);
-                    hc[base + k] = hist_word<FMT>(mv, ins_ext, del_ext);
+                    if constexpr (FMT != kFmtBound) hc[base + k] = hist_word<FMT>(mv, ins_ext, del_ext);
                 }
                 if (k == kend) mv_end = mv;
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
@@ -534,7 +548,8 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 for (int it = 0; it < iters; ++it) {
                     const int k = lo + gl + it * G;
                     if (prune && k >= vlo && k <= vhi) {
-                        const int h = hist[(size_t)(base + k) * kEntryElems];
+                        const int h = FMT == kFmt8 ? hist[(size_t)(base + k) * kEntryElems]
+                                                   : (int)live[(size_t)(live_slot + k) * kEntryElems];
                         if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
                             klo = min(klo, k);
                             khi = max(khi, k);
@@ -832,7 +847,23 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
     constexpr size_t kEntryBytes = FMT == kFmt8 ? kEntryElems * sizeof(int16_t) : sizeof(typename FmtT<FMT>::H);
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
-    if constexpr (G > 32) {
+    if constexpr (FMT == kFmtBound) {
+        // bound pass: each group runs its pairs one after another in the same region (meta records, then the
+        // live ring at its end) and records the score each reached the end at (scaled), or -1: no bound
+        constexpr int P = 32 / G;
+        const Group<G> grp(lane);
+        const uint32_t arena16 = (uint32_t)((a.warp_bytes / P) >> 4);
+        uint8_t* region = warp_slot + ((size_t)grp.index(lane) * arena16 << 4);
+        for (;;) {
+            uint32_t pos = 0;
+            if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
+            pos = __shfl_sync(kFull, pos, 0);
+            if (pos >= end - begin || end <= begin) break;
+            const Forward f =
+                forward_pair<G, ADAPT, STAGE, FMT>(a, region, (size_t)arena16 << 4, begin + pos, end, lane, st);
+            if (f.status != kIdle && grp.gl == 0) a.bound[f.pi] = f.status == kDone ? f.final_s : -1;
+        }
+    } else if constexpr (G > 32) {
         // the whole block takes one pair at a time in its arena (its warps' scratch regions); finished pairs
         // wait there, up to one per warp, and the first lane of warp w traces back the w-th
         constexpr int kWarps = G / 32;
@@ -932,7 +963,7 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
 // The compact-history instances (long reads) carry the live ring's addressing as well: whole-block groups fit
 // 80 registers with the traceback as a separate call; the 32-lane one spills there and is built for 2 blocks per SM.
 template <int G, bool ADAPT, bool STAGE, int FMT>
-constexpr int wfa_min_blocks() { return FMT == kFmt8 || G > 32 ? 3 : 2; }
+constexpr int wfa_min_blocks() { return FMT == kFmt8 || FMT == kFmtBound || G > 32 ? 3 : 2; }
 
 // One persistent launch per group size G: it drains, in order, the buckets whose group size is G.  Only
 // that G is compiled into the kernel, so it carries the registers of one variant instead of all seven (a
@@ -967,6 +998,16 @@ void (*kernel_for(int G))(WfaArgs) {
         case 16: return wfa_kernel<16, ADAPT, STAGE, kFmt8>;
         case 32: return wfa_kernel<32, ADAPT, false, kFmt8>;
         default: return wfa_kernel<256, ADAPT, false, kFmt8>;
+    }
+}
+
+// the bound pass (pruned, no history): groups of 4 to 32 lanes, staged up to 16
+void (*bound_kernel_for(int G, bool stage))(WfaArgs) {
+    switch (G) {
+        case 4: return stage ? wfa_kernel<4, true, true, kFmtBound> : wfa_kernel<4, true, false, kFmtBound>;
+        case 8: return stage ? wfa_kernel<8, true, true, kFmtBound> : wfa_kernel<8, true, false, kFmtBound>;
+        case 16: return stage ? wfa_kernel<16, true, true, kFmtBound> : wfa_kernel<16, true, false, kFmtBound>;
+        default: return wfa_kernel<32, true, false, kFmtBound>;
     }
 }
 
@@ -1042,6 +1083,10 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     p.adapt_min_len = -1;
     p.adapt_max_dist = 0;
     p.retry_only = 0;
+    p.bound = nullptr;
+    p.bound_pass = 0;
+    p.bound_min_len = kBoundMinLen;
+    p.bound_max_dist = kBoundMaxDist;
     return p;
 }
 
@@ -1062,8 +1107,10 @@ int wfa_format(const WfaPlan& p, int group) {
 
 size_t wfa_live_bytes(const WfaPlan& p, int fmt) {
     if (fmt == kFmt8) return 0;
-    return align_up((size_t)p.live_slots * p.live_w * kEntryElems * (fmt == kFmt16 ? 2 : 4), 16);
+    return align_up((size_t)p.live_slots * p.live_w * kEntryElems * (fmt == kFmt32 ? 4 : 2), 16);
 }
+
+size_t wfa_bound_pair_bytes(const WfaPlan& p) { return align_up(p.meta_bytes + wfa_live_bytes(p, kFmtBound), 16); }
 
 size_t wfa_pair_bytes_capped(const WfaPlan& p, int group, size_t entries) {
     const int fmt = wfa_format(p, group);
@@ -1095,7 +1142,13 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.scratch = scratch; a.warp_bytes = warp_bytes;
     a.meta_bytes = plan.meta_bytes; a.runs_bytes = plan.runs_bytes; a.runs_cap = (uint32_t)plan.runs_cap;
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
-    a.adapt_min_len = plan.adapt_min_len; a.adapt_max_dist = plan.adapt_max_dist;
+    // a bound pass prunes with its own parameters and writes plan.bound; exact passes read it when it is set
+    const bool bound_pass = plan.bound_pass != 0;
+    if (bound_pass && (!plan.bound || plan.adapt_min_len >= 0 || P.max_length > kMaxWfaLength16))
+        return cudaErrorInvalidValue;
+    a.adapt_min_len = bound_pass ? plan.bound_min_len : plan.adapt_min_len;
+    a.adapt_max_dist = bound_pass ? plan.bound_max_dist : plan.adapt_max_dist;
+    a.bound = plan.bound;
     a.retry_only = plan.retry_only;
     a.live_w = plan.live_w; a.live_slots = plan.live_slots;
     for (int b = 0; b < kMaxBuckets; ++b) a.group[b] = (int16_t)(b < nbuckets ? groups[b] : 32);
@@ -1116,10 +1169,12 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         size_t smem = (size_t)8 * (32 / std::min(G, 32)) * 2 * slot_words * sizeof(uint64_t);
         if (G > kStageMaxGroup || smem > kStageBytes) smem = 0;
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
-        const int fmt = wfa_format(plan, G);
+        if (bound_pass && (G < 4 || G > 32)) return cudaErrorInvalidValue;
+        const int fmt = bound_pass ? kFmtBound : wfa_format(plan, G);
         a.live_bytes = wfa_live_bytes(plan, fmt);
-        if (fmt != kFmt8) smem = 0;
-        void (*kernel)(WfaArgs) = fmt != kFmt8 ? compact_kernel_for(G, fmt)
+        if (fmt != kFmt8 && fmt != kFmtBound) smem = 0;
+        void (*kernel)(WfaArgs) = bound_pass ? bound_kernel_for(G, smem != 0)
+                                : fmt != kFmt8 ? compact_kernel_for(G, fmt)
                                 : adapt ? (smem ? kernel_for<true, true>(G) : kernel_for<true, false>(G))
                                         : (smem ? kernel_for<false, true>(G) : kernel_for<false, false>(G));
         // exact staged launches: a ring of the last R score records per group, R a power of 2 above the
@@ -1128,7 +1183,10 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         while (R < (uint32_t)std::max(plan.x, plan.oe) + 1) R <<= 1;
         const size_t ring_bytes = (G > 32 ? 1 : (size_t)8 * (32 / G)) * R * sizeof(int4);
         a.meta_ring = 0; a.ring_off = (uint32_t)smem;
-        if (smem && !adapt && R <= 64 && smem + ring_bytes <= (48u << 10)) { a.meta_ring = R; smem += ring_bytes; }
+        if (smem && !adapt && !bound_pass && R <= 64 && smem + ring_bytes <= (48u << 10)) {
+            a.meta_ring = R;
+            smem += ring_bytes;
+        }
         int bps = 0;
         cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kernel, 256, smem);
         if (err != cudaSuccess) return err;

@@ -19,7 +19,7 @@ def _mixed(n_uneven=2_500, n_short=2_003):
     return p, me
 
 
-def _batched(p, me, autotune, runs=2, scratch=0, compact=0, passes=None):
+def _batched(p, me, autotune, runs=2, scratch=0, compact=0, passes=None, bound=0, bounds=None, band=-1):
     import torch
     import paper_2208_01243_gb300 as aim
     n = len(p)
@@ -29,17 +29,21 @@ def _batched(p, me, autotune, runs=2, scratch=0, compact=0, passes=None):
                                                         p.target_len, coff, me.astype(np.int32))
     al = aim.Aligner(0, 1 << 30)
     aim.aim_set_batch_compact(al.ctx, compact)
+    aim.aim_set_batch_bound(al.ctx, bound)
     dev = rl.device
     scores = torch.full((n,), -7, dtype=torch.int32, device=dev)
     flags = torch.full((n,), 255, dtype=torch.uint8, device=dev)
     lens = torch.zeros(n, dtype=torch.int32, device=dev)
     cig = torch.zeros(int(coff[-1]), dtype=torch.int32, device=dev)
     ml = int(max(p.read_len.max(), p.target_len.max()))
-    plan = aim.aim_batch_plan(al.ctx, reads, targets, ro, to, rl, tl, ml, aim.penalties(4, 6, 2), int(me.max()), pp,
-                              scores, cig, cd, lens, flags, scratch_bytes=scratch, autotune=autotune)
+    plan = aim.aim_batch_plan(al.ctx, reads, targets, ro, to, rl, tl, ml, aim.penalties(4, 6, 2, band=band),
+                              int(me.max()), pp, scores, cig, cd, lens, flags, scratch_bytes=scratch,
+                              autotune=autotune)
     groups, counts = aim.aim_batch_info(plan)
     if passes is not None:
         passes.append(aim.aim_batch_passes(plan))
+    if bounds is not None:
+        bounds.append(aim.aim_batch_bound_passes(plan))
     outs = []
     for _ in range(runs):
         scores.fill_(-7); flags.fill_(255)
@@ -91,6 +95,41 @@ def test_compact_first_pass_gives_the_plain_results(oracle_lib, gen_lib, autotun
     passes = []
     outs2, _, _ = _batched(p, me, autotune, runs=1, compact=2, passes=passes, scratch=4 << 30)
     assert passes[0][2] == 0
+    assert np.array_equal(outs2[0][0], plain[0]) and np.array_equal(outs2[0][1], plain[1])
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+@pytest.mark.parametrize("band", [-1, 25])
+def test_bound_pass_gives_the_plain_results(oracle_lib, gen_lib, autotune, band):
+    """Bound passes forced on every bucket: each exact pass runs with min(limit, bound) as its pairs' limit, and
+    every replay equals the plain form (no bound pass) bit for bit, rejected pairs included (a tenth of the
+    150 bp pairs are unrelated and exceed their limit); a sample also equals the oracle."""
+    import __graft_entry__
+    __graft_entry__.build()
+    p, me = _mixed(3_000, 2_003)
+    if band >= 0:
+        keep = np.flatnonzero(np.abs(p.target_len.astype(np.int64) - p.read_len.astype(np.int64)) <= band)
+        p = gen.concat([gen.from_strings([p.read(i)], [p.target(i)]) for i in keep])
+        me = me[keep]
+    bounds = []
+    outs, groups, counts = _batched(p, me, autotune, bound=1, bounds=bounds, scratch=4 << 30, band=band)
+    lanes, n_bound = bounds[0]
+    assert n_bound >= 1 and all(g in (0, 8) for g in lanes)
+    assert all(lanes[k] == 8 for k in range(32) if counts[k] and groups[k] <= 32)
+    plain = device_results(p, "wfa", AFF, int(me.max()), per_pair=me, band=band)
+    assert (plain[1] & 1).sum() > 0                  # some pairs are rejected at their limit
+    for o in outs:
+        assert np.array_equal(o[0], plain[0]) and np.array_equal(o[1], plain[1])
+        assert np.array_equal(o[3], plain[3])
+        assert all(np.array_equal(x, y) for x, y in zip(o[2], plain[2]))
+    idx = np.random.default_rng(9).choice(len(p), 300, replace=False)
+    sub = gen.concat([gen.from_strings([p.read(i)], [p.target(i)]) for i in idx])
+    lim = np.array([oracle.limit_for(AFF, int(me[i])) for i in idx], np.int64)
+    assert_same(outs[-1], oracle_results(sub, AFF, lim, band=band), idx=idx, what="bound pass vs oracle")
+    # never: no bound pass, the same results
+    bounds = []
+    outs2, _, _ = _batched(p, me, autotune, runs=1, bound=2, bounds=bounds, scratch=4 << 30, band=band)
+    assert bounds[0][1] == 0
     assert np.array_equal(outs2[0][0], plain[0]) and np.array_equal(outs2[0][1], plain[1])
 
 
