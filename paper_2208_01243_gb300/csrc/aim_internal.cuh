@@ -26,14 +26,23 @@ __device__ __forceinline__ uint32_t base_at(const uint64_t* __restrict__ w, uint
     return (uint32_t)(__ldg(w + (i >> 5)) >> (62 - 2 * (i & 31))) & 3u;
 }
 
+// The 64 bits that start sh bits (0..63) into the 128-bit value hi:lo, built from 32-bit halves with two
+// funnel shifts: for sh < 32 the halves (hi.1, hi.0, lo.1) shift by sh, else (hi.0, lo.1, lo.0) by sh - 32.
+// This is (hi << sh) | (lo >> (64 - sh)) (just hi for sh == 0) without 64-bit variable shifts.
+__device__ __forceinline__ uint64_t join_window(uint64_t hi, uint64_t lo, uint32_t sh) {
+    const uint32_t h1 = (uint32_t)(hi >> 32), h0 = (uint32_t)hi, l1 = (uint32_t)(lo >> 32), l0 = (uint32_t)lo;
+    const bool up = (sh & 32u) != 0;
+    const uint32_t a = up ? h0 : h1, b = up ? l1 : h0, c = up ? l0 : l1;
+    return ((uint64_t)__funnelshift_l(b, a, sh) << 32) | __funnelshift_l(c, b, sh);
+}
+
 // 32 bases starting at base `pos` of a sequence of `nwords` words, first base in the top bits.
 // Bases past the last word read as 0; callers cap comparisons by the remaining length.
-// (lo >> 1) >> (63 - sh) is lo >> (64 - sh) for sh > 0 and 0 for sh == 0: no branch for lanes to diverge on.
 __device__ __forceinline__ uint64_t window32(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
     const uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
     const uint64_t hi = wi < nwords ? __ldg(w + wi) : 0ull;
     const uint64_t lo = (wi + 1 < nwords) ? __ldg(w + wi + 1) : 0ull;
-    return (hi << sh) | ((lo >> 1) >> (63 - sh));
+    return join_window(hi, lo, sh);
 }
 
 // ---- per-call description handed to the kernels ----

@@ -144,13 +144,12 @@ __device__ __forceinline__ typename FmtT<FMT>::H hist_word(int mv, bool ins_ext,
 }
 
 // 32 bases starting at base pos of a sequence of nwords words in global memory, for pos inside the sequence
-// (so word pos / 32 exists); the word after it reads as 0 past the end.  (lo >> 1) >> (63 - sh) is
-// lo >> (64 - sh) for sh > 0 and 0 for sh == 0, with no branch.
+// (so word pos / 32 exists); the word after it reads as 0 past the end.
 __device__ __forceinline__ uint64_t window_in(const uint64_t* __restrict__ w, uint32_t nwords, uint32_t pos) {
     const uint32_t wi = pos >> 5, sh = 2 * (pos & 31);
     const uint64_t hi = __ldg(w + wi);
     const uint64_t lo = wi + 1 < nwords ? __ldg(w + wi + 1) : 0ull;
-    return (hi << sh) | ((lo >> 1) >> (63 - sh));
+    return join_window(hi, lo, sh);
 }
 
 // dynamic shared memory of staged launches: copies of the pairs' packed sequences, one slot per group, then
@@ -161,7 +160,7 @@ extern __shared__ uint64_t s_seq[];
 // both loads stay inside it without a check
 __device__ __forceinline__ uint64_t window_shared(uint32_t off, uint32_t pos) {
     const uint32_t wi = off + (pos >> 5), sh = 2 * (pos & 31);
-    return (s_seq[wi] << sh) | ((s_seq[wi + 1] >> 1) >> (63 - sh));
+    return join_window(s_seq[wi], s_seq[wi + 1], sh);
 }
 
 // the extend's view of one pair: global memory, or the group's copies in shared memory
@@ -379,6 +378,10 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         if (gl == 0 && FMT != kFmtBound) st.pairs += 1;
     }
 
+    // reach = (S - s) / E for the current score s, kept by a remainder instead of a division per score
+    int reach = 0, rrem = 0;
+    if (status == kRun) { reach = S / E; rrem = S - reach * E; }
+
     // the extend's view of the pair: with STAGE, the group's copy in shared memory (a spare zero word after
     // each sequence), read at shared-memory latency
     PairSeqs<STAGE> seqs;
@@ -441,6 +444,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     int s = 0;
     while (grp.any_running(status == kRun)) {
         ++s;
+        if (--rrem < 0) { rrem += E; --reach; }
         bool run = status == kRun;
         if (run && s > S) { status = kRejected; run = false; }
         int lo = 0, hi = -1, w = 0;
@@ -468,7 +472,6 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 // an alignment of score <= S.  The sources of every entry kept lie within the same bound, so each
                 // kept entry has its exact value, and the traceback only reads entries on optimal paths (a prefix
                 // of cost c at diagonal k has c + E |k - kend| <= optimum <= S).
-                const int reach = (S - s) / E;
                 lo = max(lo, kend - reach); hi = min(hi, kend + reach);
             }
             w = lo <= hi ? hi - lo + 1 : 0;
