@@ -136,7 +136,7 @@ struct WfaPlan {
     uint32_t live_w;     // compact forms: entries per live-ring slot (a power of 2 above the widest wavefront)
     uint32_t live_slots; // compact forms: live-ring slots (a power of 2 above the farthest source score)
     int runs_cap;        // CIGAR runs staged per pair
-    size_t meta_bytes;   // per-score (lo, hi, base, width) records, int4 each
+    size_t meta_bytes;   // per-score (lo, count, base, width) records, int4 each
     size_t runs_bytes;   // run staging
     int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
     int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end

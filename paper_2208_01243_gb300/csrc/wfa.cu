@@ -76,7 +76,7 @@ __device__ __forceinline__ Wf load_wf(const int4* rec, int s, int mask) {
     Wf f;
     if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
     const int4 q = rec[s & mask];
-    f.lo = q.x; f.cnt = q.y >= q.x ? q.y - q.x + 1 : 0; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
     return f;
 }
 
@@ -84,7 +84,7 @@ __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     Wf f;
     if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
     const int4 q = reinterpret_cast<const int4*>(meta)[s];
-    f.lo = q.x; f.cnt = q.y >= q.x ? q.y - q.x + 1 : 0; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
     return f;
 }
 
@@ -430,8 +430,8 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             e0[0] = (V)m0; e0[1] = (V)kNeg; e0[2] = (V)kNeg; e0[3] = 0;
             if constexpr (FMT != kFmtBound) hc[0] = hist_word<FMT>(m0, false, false);
         }
-        reinterpret_cast<int4*>(meta)[0] = make_int4(0, 0, 0, 1);
-        if (kRing && ring) ring[0] = make_int4(0, 0, 0, 1);
+        reinterpret_cast<int4*>(meta)[0] = make_int4(0, 1, 0, 1);
+        if (kRing && ring) ring[0] = make_int4(0, 1, 0, 1);
         found0 = (kend == 0 && m0 >= m);
     }
     found0 = grp.bcast(found0);
@@ -565,7 +565,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         }
         if (run) {
             if (gl == 0) {
-                const int4 rec = vlo <= vhi ? make_int4(vlo, vhi, base, w) : make_int4(1, 0, 0, 0);
+                const int4 rec = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, base, w) : make_int4(0, 0, 0, 0);
                 reinterpret_cast<int4*>(meta)[s] = rec;
                 if (kRing && ring) ring[s & mask] = rec;
             }
