@@ -345,13 +345,17 @@ def run_ours(args, w, algo):
                                   out["flags"], scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=True)
         groups, counts = aim.aim_batch_info(plan)
         first_pass, full_pass, n_compact = aim.aim_batch_passes(plan)
+        bound_pass, n_bound = aim.aim_batch_bound_passes(plan)
 
         def step(src=None):
             aim.aim_batch_run(plan)
-        # kernels per replay: 2 pack and 3 bucketing launches, then one alignment launch per distinct lanes-per-pair
-        # value; a compact first pass adds the second pass's count/scan/scatter and its alignment launches
+        # kernels per replay: 2 pack and 3 bucketing launches, then one alignment launch per group of buckets sharing
+        # lanes per pair and bound-pass lanes, plus one bound-pass launch per group that has one; a compact first pass
+        # instead adds the second pass's count/scan/scatter and its alignment launches
         first_eff = [f or g for f, g in zip(first_pass, full_pass)]
-        launches_per_step = 5 + (len(set(first_eff)) + 3 + len(set(full_pass)) if n_compact else len(set(full_pass)))
+        keys = set(zip(full_pass, bound_pass))
+        launches_per_step = 5 + (len(set(first_eff)) + 3 + len(set(full_pass)) if n_compact
+                                 else len(keys) + sum(1 for _, b in keys if b))
     else:
         def step(src=None):
             src = src or d
@@ -462,6 +466,8 @@ def run_ours(args, w, algo):
                  "batched_lanes_per_bucket": {str(k): g for k, (g, c) in enumerate(zip(groups, counts)) if c},
                  "batched_compact_first_pass": {str(k): [f, g] for k, (f, g, c) in
                                                 enumerate(zip(first_pass, full_pass, counts)) if c and f},
+                 "batched_bound_pass_lanes": {str(k): b for k, (b, c) in enumerate(zip(bound_pass, counts))
+                                              if c and b},
                  "batched_pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c}}
         del gd
 

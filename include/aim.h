@@ -205,6 +205,12 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
  * in the context for later calls of the same shape (algorithm, costs,
  * thresholds, max_length, chunk size), whose first call pays for planning;
  * they are freed by aim_destroy or replaced by a call of another shape.
+ * Each chunk's byte ranges are found, and its cigar_offsets checked, when its
+ * turn comes, overlapping the device work of the chunks before it; the slots
+ * are sized from the first chunk (with a quarter of headroom) and grow when a
+ * later chunk needs more, once the earlier chunks' results are in host memory.
+ * A decreasing cigar_offsets entry returns AIM_ERR_ARG; the chunks before the
+ * one holding it have then been aligned and their results written.
  * Nothing else may use the context during the call.  Returns once every
  * result is in host memory; results equal aim_align_batch_ascii's bit for bit.
  */

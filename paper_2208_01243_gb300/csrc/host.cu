@@ -187,51 +187,72 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
         !out_scores || !out_flags || ((out_cigars == nullptr) != (cigar_offsets == nullptr)))
         return AIM_ERR_ARG;
     if (max_edits_per_pair && max_edits < 0) return AIM_ERR_ARG;
-    for (uint32_t i = 0; cigar_offsets && i < num_pairs; ++i)
-        if (cigar_offsets[i + 1] < cigar_offsets[i]) return AIM_ERR_ARG;   // capacities are differences
     DeviceGuardImpl guard(ctx->device);
     if (!guard.ok) return AIM_ERR_CUDA;
 
-    // chunks: C pairs (default: an eighth of the batch, at least 65,536 pairs), and the largest byte and run
-    // ranges any chunk needs
+    // chunks: C pairs (default: an eighth of the batch, at least 65,536 pairs).  Each chunk's byte ranges are
+    // found (and its CIGAR offsets checked) when its turn comes, so that host work overlaps the device work of
+    // the chunks before it; the slots are sized from the first chunk with a quarter of headroom and grow (after
+    // the device has finished with them) if a later chunk needs more.
     uint32_t C = chunk_pairs ? chunk_pairs : std::max<uint32_t>((num_pairs + 7) / 8, 65536u);
     C = std::min(C, num_pairs);
     const uint32_t nchunks = (num_pairs + C - 1) / C;
-    uint64_t rc = 0, tc = 0, cc = 0;
-    std::vector<uint64_t> ranges(4 * (size_t)nchunks);   // per chunk: read bytes [lo, hi), target bytes [lo, hi)
-    for (uint32_t j = 0; j < nchunks; ++j) {
+    const bool wfa_batched = algo == AIM_ALGO_WFA_AFFINE;
+    auto chunk_ranges = [&](uint32_t j, uint64_t r[4]) -> bool {
         const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C);
-        uint64_t* r = &ranges[4 * (size_t)j];
+        for (uint32_t i = c0; cigar_offsets && i < c1; ++i)
+            if (cigar_offsets[i + 1] < cigar_offsets[i]) return false;   // capacities are differences
         byte_range(read_char_offsets, read_lengths, c0, c1, &r[0], &r[1]);
         byte_range(target_char_offsets, target_lengths, c0, c1, &r[2], &r[3]);
-        rc = std::max(rc, r[1] - r[0]);
-        tc = std::max(tc, r[3] - r[2]);
-        if (cigar_offsets) cc = std::max(cc, cigar_offsets[c1] - cigar_offsets[c0]);
-    }
-    const bool wfa_batched = algo == AIM_ALGO_WFA_AFFINE;
+        return true;
+    };
+    auto headroom = [](uint64_t x) { return x + x / 4; };
+    uint64_t r0[4];
+    if (!chunk_ranges(0, r0)) return AIM_ERR_ARG;
     HostPipe* hp = static_cast<HostPipe*>(ctx->host_pipe);
-    if (!same_shape(hp, algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C,
-                    rc, tc, cc)) {
-        destroy_pipe(hp);
+    auto rebuild = [&](uint64_t rc, uint64_t tc, uint64_t cc) -> int {
+        destroy_pipe(hp);   // waits for the device to finish with the old slots
         ctx->host_pipe = nullptr;
-        cudaError_t e;
-        hp = make_pipe(algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C, rc,
-                       tc, cc, &e);
-        if (!hp) return e == cudaErrorMemoryAllocation ? AIM_ERR_NOMEM : cuda_status(e);
+        cudaError_t err;
+        hp = make_pipe(algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C,
+                       headroom(rc), headroom(tc), headroom(cc), &err);
+        if (!hp) return err == cudaErrorMemoryAllocation ? AIM_ERR_NOMEM : cuda_status(err);
         ctx->host_pipe = hp;
+        return AIM_OK;
+    };
+    {
+        const uint64_t cc0 = cigar_offsets ? cigar_offsets[std::min(num_pairs, C)] - cigar_offsets[0] : 0;
+        if (!same_shape(hp, algo, pen, max_edits, max_edits_per_pair != nullptr, out_cigars != nullptr, max_length, C,
+                        r0[1] - r0[0], r0[3] - r0[2], cc0)) {
+            const int st = rebuild(r0[1] - r0[0], r0[3] - r0[2], cc0);
+            if (st != AIM_OK) return st;
+        }
     }
 
     uint64_t h2d = 0, d2h = 0;
     cudaError_t e = cudaSuccess;
     int rc_status = AIM_OK;
     for (uint32_t j = 0; j < nchunks && e == cudaSuccess && rc_status == AIM_OK; ++j) {
-        Slot& s = hp->slot[j & 1];
-        cudaStream_t comp = hp->comp[j & 1];
         const uint32_t c0 = j * C, c1 = std::min(num_pairs, c0 + C), k = c1 - c0;
-        const uint64_t rlo = ranges[4 * (size_t)j], rhi = ranges[4 * (size_t)j + 1];
-        const uint64_t tlo = ranges[4 * (size_t)j + 2], thi = ranges[4 * (size_t)j + 3];
+        uint64_t r[4];
+        if (j == 0) {
+            std::memcpy(r, r0, sizeof(r));
+        } else if (!chunk_ranges(j, r)) {
+            rc_status = AIM_ERR_ARG;
+            break;
+        }
+        const uint64_t rlo = r[0], rhi = r[1], tlo = r[2], thi = r[3];
         const uint64_t cbase = cigar_offsets ? cigar_offsets[c0] : 0;
         const uint64_t cend = cigar_offsets ? cigar_offsets[c1] - cbase : 0;
+        if (rhi - rlo > hp->read_cap || thi - tlo > hp->target_cap || cend > hp->cigar_cap) {
+            // a chunk that needs larger slots: the earlier chunks' results are finished first (their copies out
+            // complete), then the slots are rebuilt (and replanned) with room for this one
+            rc_status = rebuild(std::max(rhi - rlo, hp->read_cap), std::max(thi - tlo, hp->target_cap),
+                                std::max(cend, hp->cigar_cap));
+            if (rc_status != AIM_OK) break;
+        }
+        Slot& s = hp->slot[j & 1];
+        cudaStream_t comp = hp->comp[j & 1];
         const uint32_t padded = wfa_batched ? C : k;
         // copy in straight from the caller's arrays, once the slot's previous alignment has read its inputs
         if (s.used) e = cudaStreamWaitEvent(hp->h2d, s.comp_done, 0);
@@ -301,7 +322,9 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
         if (e == cudaSuccess) e = cudaEventRecord(s.out_done, hp->d2h);
         s.used = true;
     }
-    // every result in host memory before returning (also after an error, so no copy outlives the call)
+    // every result in host memory before returning (also after an error, so no copy outlives the call; a failed
+    // rebuild has already waited for the old slots and left no pipe)
+    if (!hp) return rc_status != AIM_OK ? rc_status : AIM_ERR_CUDA;
     const cudaError_t e1 = cudaStreamSynchronize(hp->h2d);
     cudaError_t e2 = cudaStreamSynchronize(hp->comp[0]);
     if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(hp->comp[1]);

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 AFF = (0, 4, 6, 2)
 
 
-def _host_call(aim, ctx, p, algo, pen, max_edits, cap, per_pair=None, band=-1, chunk=0, pinned=True):
+def _host_call(aim, ctx, p, algo, pen, max_edits, cap, per_pair=None, band=-1, chunk=0, pinned=True, off=None):
     import torch
     n = len(p)
 
@@ -33,7 +33,8 @@ def _host_call(aim, ctx, p, algo, pen, max_edits, cap, per_pair=None, band=-1, c
         a = torch.zeros(size, dtype=tdt, pin_memory=True).numpy()
         return a.view(dtype) if a.dtype != np.dtype(dtype) else a
 
-    off = np.zeros(n + 1, np.uint64); off[1:] = np.cumsum(cap)
+    if off is None:
+        off = np.zeros(n + 1, np.uint64); off[1:] = np.cumsum(cap)
     reads = arr(p.reads); targets = arr(p.targets)
     ro = arr(p.read_off.view(np.int64)).view(np.uint64); to = arr(p.target_off.view(np.int64)).view(np.uint64)
     rl = arr(p.read_len.view(np.int32)).view(np.uint32); tl = arr(p.target_len.view(np.int32)).view(np.uint32)
@@ -80,4 +81,36 @@ def test_host_entry_point_equals_device_entry_point(oracle_lib, gen_lib):
                              cigar_cap=cap3[:500])
     assert_flat_same((got3[0][:500], got3[1][:500], got3[2][:500], got3[3][:int(orc[2][-1])], orc[2]), orc,
                      what="host gotoh vs oracle")
+    al.close()
+
+
+def test_host_slots_grow_for_later_chunks(oracle_lib, gen_lib):
+    """The slots are sized from the first chunk; a later chunk with far longer sequences makes the call finish
+    the earlier chunks, rebuild (and replan) its slots and go on: the results still equal the device entry
+    point's, and a second call of the same shape reuses the grown slots.  A decreasing CIGAR offset in a later
+    chunk is an argument error."""
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2208_01243_gb300 as aim
+    al = aim.Aligner(0, 2 << 30)
+    ps = gen.generate(gen.WFA_150BP, 6_000)
+    pu = gen.generate(gen.WFA_UNEVEN, 9_001)
+    p = gen.concat([ps, pu])
+    me = np.concatenate([np.full(len(ps), 6, np.int32), gen.per_pair_max_edits(gen.WFA_UNEVEN, pu)])
+    cap = runs_capacity(AFF, me)
+    ref = device_flat(p, "wfa", AFF, int(me.max()), cap, per_pair=me, aligner=al)
+    want = (ref[0], ref[1], ref[4], ref[3], ref[2])
+    for rep in range(2):
+        got, _ = _host_call(aim, al.ctx, p, "wfa", AFF, int(me.max()), cap, per_pair=me, chunk=3_000)
+        assert_flat_same(got, want, what=f"host wfa, growing slots, call {rep}")
+    refe = device_flat(p, "edit", (0, 1, 0, 1), 12, runs_capacity((0, 1, 0, 1), np.full(len(p), 12), unit=True),
+                       aligner=al)
+    gote, _ = _host_call(aim, al.ctx, p, "edit", (0, 1, 0, 1), 12,
+                         runs_capacity((0, 1, 0, 1), np.full(len(p), 12), unit=True), chunk=3_000)
+    assert_flat_same(gote, (refe[0], refe[1], refe[4], refe[3], refe[2]), what="host edit, growing slots")
+    off = np.zeros(len(p) + 1, np.uint64); off[1:] = np.cumsum(cap)
+    off[4_500] = off[4_499] - 1 if off[4_499] > 0 else 0   # decreasing entry inside the second chunk
+    off[4_499] += 1
+    with pytest.raises(aim.AimError):
+        _host_call(aim, al.ctx, p, "wfa", AFF, int(me.max()), cap, per_pair=me, chunk=3_000, off=off)
     al.close()
