@@ -149,7 +149,7 @@ struct WfaPlan {
 // the bound pass's pruning: wavefronts of at least kBoundMinLen diagonals keep those within kBoundMaxDist of the
 // diagonal closest to the end
 constexpr int kBoundMinLen = 4;
-constexpr int kBoundMaxDist = 8;
+constexpr int kBoundMaxDist = 3;
 // scratch one pair of a bound pass needs (meta records and the live ring)
 size_t wfa_bound_pair_bytes(const WfaPlan& p);
 // the plan with its history sized for wavefronts at most `width` diagonals wide (a compact first pass)

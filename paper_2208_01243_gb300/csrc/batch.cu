@@ -166,7 +166,7 @@ size_t bucket_pair_bytes(const WfaPlan& plan, int b, int G) {
 }
 
 constexpr int kCompactDiagonalsPerLane = 16;   // first-pass history: wavefronts of about 16 diagonals per lane
-constexpr int kBoundDefaultGroup = 8;          // lanes per pair of a forced bound pass
+constexpr int kBoundDefaultGroup = 4;          // lanes per pair of a forced bound pass
 constexpr float kBoundGain = 0.97f;            // a bound pass must save at least 3 % of the bucket's trial time
 
 // scratch one pair of bucket b gets in a compact first pass with G lanes per pair
