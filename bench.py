@@ -74,6 +74,12 @@ def parse():
     ap.add_argument("--workspace-gb", type=float, default=32.0,
                     help="aligner context workspace and batched-plan scratch (GiB)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving-loop measurement")
+    ap.add_argument("--tune-file", default="",
+                    help="batched plans: take the autotuner's choices from this file if it exists, else tune and "
+                         "write them there (so a profiled run replays the plan of an unprofiled one)")
+    ap.add_argument("--profile-step", action="store_true",
+                    help="time the device-resident steps only (no plain-form comparison, host-buffer run, serving "
+                         "or CPU baseline): the command profile captures run, so the step's launches come last")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per pair for the plain WFA calls (0: library choice)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
     ap.add_argument("--serve-probe-seconds", type=float, default=4.0,
@@ -339,13 +345,27 @@ def run_ours(args, w, algo):
             dist.barrier()
 
     plan = None
+    plan_info = None
     if batched:
+        tuned = bool(args.tune_file) and os.path.exists(args.tune_file)
+        if tuned:
+            aim.aim_tune_import(al.ctx, open(args.tune_file).read())
         plan = aim.aim_batch_plan(al.ctx, d["reads"], d["targets"], d["ro"], d["to"], d["rl"], d["tl"], max_len, pen,
                                   max_edits, d.get("pp"), out["scores"], out["cigars"], coff_d, out["lens"],
-                                  out["flags"], scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=True)
+                                  out["flags"], scratch_bytes=int(args.workspace_gb * (1 << 30)), autotune=not tuned)
+        if args.tune_file and not tuned and rank == 0:
+            with open(args.tune_file, "w") as f:
+                f.write(aim.aim_tune_export(al.ctx))
         groups, counts = aim.aim_batch_info(plan)
         first_pass, full_pass, n_compact = aim.aim_batch_passes(plan)
         bound_pass, n_bound = aim.aim_batch_bound_passes(plan)
+        plan_info = {
+            "lanes_per_bucket": {str(k): g for k, (g, c) in enumerate(zip(groups, counts)) if c},
+            "bound_pass_lanes": {str(k): b for k, (b, c) in enumerate(zip(bound_pass, counts)) if c and b},
+            "compact_first_pass": {str(k): [f, g] for k, (f, g, c) in enumerate(zip(first_pass, full_pass, counts))
+                                   if c and f},
+            "pairs_per_bucket": {str(k): c for k, c in enumerate(counts) if c},
+            "tuned_here": not tuned}
 
         def step(src=None):
             aim.aim_batch_run(plan)
@@ -395,7 +415,7 @@ def run_ours(args, w, algo):
 
     # ---- plain form on the same pairs: one launch per read-length group
     plain = None
-    if batched:
+    if batched and not args.profile_step:
         grp = length_groups(p)
         gd = []
         for idx in grp:
@@ -515,8 +535,10 @@ def run_ours(args, w, algo):
         assert np.array_equal(hres["lens"], res_lens.view(np.uint32)), "host-buffer run counts differ"
         barrier()
         return _dist_max(dt, dev, world), moved
-    e2e_ms, (h2d, d2h) = host_timed(0)
-    serial_ms, _ = host_timed(n_pairs)
+    e2e_ms = serial_ms = None
+    if not args.profile_step:
+        e2e_ms, (h2d, d2h) = host_timed(0)
+        serial_ms, _ = host_timed(n_pairs)
 
     if rank != 0:
         if plan is not None:
@@ -574,7 +596,7 @@ def run_ours(args, w, algo):
                            / launches / (ms / 1e3),
             "rejected_frac": float((res_flags & 1).mean()),
             "roofline": roof,
-            "e2e": {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
+            "e2e": None if e2e_ms is None else {"value": world * n_pairs / (e2e_ms / 1e3), "unit": "alignments/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
                     "form": "aim_align_batch_host: one C-ABI call per step on pinned host buffers (ASCII pairs in, "
                             "scores/flags/CIGARs out); the library pipelines chunks through two device slots so "
@@ -586,6 +608,8 @@ def run_ours(args, w, algo):
             "clocks": clk}
     if plain is not None:
         line["plain"] = plain
+    if plan_info is not None:
+        line["batched_plan"] = plan_info
     t3 = [key for key, ww in gen.TABLE3.items() if ww is w]
     if t3:
         ref = TABLE3_UPMEM[t3[0]]
@@ -599,9 +623,9 @@ def run_ours(args, w, algo):
     al.close()
     del d, out
     torch.cuda.empty_cache()
-    if batched and not args.no_serve and world == 1:
+    if batched and not args.no_serve and not args.profile_step and world == 1:
         line["serving"] = serving(args, local)
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not args.profile_step:
         line["cpu_baseline"] = cpu_baseline(w, algo)
     print(json.dumps(line))
     return 0

@@ -228,7 +228,9 @@ AIM_API int aim_align_batch_host(aim_ctx *ctx, const uint8_t *reads, const uint8
  * 0: the library's choice), for pairs no longer than max_length under the
  * threshold rule above (pen, max_edits; host values): per-score records, CIGAR
  * run staging and the wavefront history, every wavefront as wide as its
- * sources allow.  Groups of 32 lanes or whole blocks on reads longer than
+ * sources allow and no wider than the 2 (S - s) / e + 1 diagonals (scaled
+ * units) that can still end within the limit S, as the exact kernels clamp
+ * it.  Groups of 32 lanes or whole blocks on reads longer than
  * 2,048 bp keep a compact history (2 bytes per wavefront entry up to 16,382
  * bp, 4 beyond, plus a small ring of the last few wavefronts) instead of 8
  * bytes per entry (Section 3.3: the long-read limit comes from memory).  The
@@ -356,6 +358,21 @@ AIM_API int aim_set_batch_compact(aim_ctx *ctx, int mode);
  */
 AIM_API int aim_batch_bound_passes(aim_batch *batch, int *bound_pass /* host[32] */);
 AIM_API int aim_set_batch_bound(aim_ctx *ctx, int mode);
+/*
+ * Autotuner choices, so that a later process can plan exactly as a tuned one
+ * did.  The context caches, per (costs, band, bucket, largest scaled score),
+ * the lanes per pair, the compact first-pass lanes (0: none) and the
+ * bound-pass lanes (0: none) its plans chose; plans made with autotune 0 take
+ * cached choices where present.  aim_tune_export writes the cache as text,
+ * one line "x o e band bucket smax lanes compact bound" per entry, into buf
+ * (host, cap bytes, always NUL-terminated when cap > 0) and returns the
+ * text's length without the NUL (a larger value than cap - 1 means buf was
+ * too small; cap 0 only asks the length), or a negative status.
+ * aim_tune_import adds the entries of such a text (host, NUL-terminated) to
+ * the cache; a malformed line returns AIM_ERR_ARG and imports nothing.
+ */
+AIM_API int64_t aim_tune_export(aim_ctx *ctx, char *buf, size_t cap);
+AIM_API int aim_tune_import(aim_ctx *ctx, const char *text);
 AIM_API int aim_batch_destroy(aim_batch *batch);
 
 /*

@@ -74,6 +74,9 @@ def _lib():
         lib.aim_batch_passes.argtypes = [p, p, p]
         lib.aim_set_batch_bound.argtypes = [p, ctypes.c_int]
         lib.aim_batch_bound_passes.argtypes = [p, p]
+        lib.aim_tune_export.argtypes = [p, ctypes.c_char_p, ctypes.c_size_t]
+        lib.aim_tune_export.restype = ctypes.c_int64
+        lib.aim_tune_import.argtypes = [p, ctypes.c_char_p]
         lib.aim_batch_plan.argtypes = [p, p, p, p, p, p, p, u32, u32, ctypes.POINTER(aim_penalties_t), i32, p, p, p,
                                        p, p, p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(p)]
         lib.aim_batch_run.argtypes = [p, p]
@@ -312,6 +315,21 @@ def aim_batch_bound_passes(plan) -> tuple[list[int], int]:
     if n < 0:
         _check(n, "aim_batch_bound_passes")
     return lanes.tolist(), int(n)
+
+
+def aim_tune_export(ctx) -> str:
+    """The context's autotuner choices as text (one line per cached bucket choice)."""
+    n = _lib().aim_tune_export(ctx, None, 0)
+    if n < 0:
+        _check(int(n), "aim_tune_export")
+    buf = ctypes.create_string_buffer(int(n) + 1)
+    _lib().aim_tune_export(ctx, buf, int(n) + 1)
+    return buf.value.decode()
+
+
+def aim_tune_import(ctx, text: str) -> None:
+    """Add choices exported by aim_tune_export to the context's cache (plans with autotune off use them)."""
+    _check(_lib().aim_tune_import(ctx, text.encode()), "aim_tune_import")
 
 
 def aim_set_genasm_window(ctx, window: int = 64, overlap: int = 24) -> None:

@@ -155,7 +155,9 @@ size_t wfa_bound_pair_bytes(const WfaPlan& p);
 // the plan with its history sized for wavefronts at most `width` diagonals wide (a compact first pass)
 WfaPlan wfa_plan_compact(const WfaPlan& full, int64_t width);
 WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limit);
-size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax);
+// worst-case history entries of one pair: every wavefront as wide as its sources allow and, when clamp (the exact
+// kernels), no wider than the diagonals that can still end within the limit
+size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax, bool clamp);
 // lanes per pair suited to the widest wavefront the plan allows (4, 8, 16, 32 or 256; 1 and 2 are valid too;
 // at least 32 beyond kMaxWfaLength16)
 int wfa_default_group(const WfaPlan& p, uint32_t max_length);

@@ -158,6 +158,8 @@ int align_packed(aim_ctx* ctx, const aim::PairsView& P, int algo, const aim_pena
         if (algo == AIM_ALGO_WFA_ADAPTIVE) {
             plan.adapt_min_len = ctx->adapt_min_len;
             plan.adapt_max_dist = ctx->adapt_max_dist;
+            // the adaptive kernels keep the unclamped wavefronts their pruning rule reads
+            plan.hist_entries = aim::wfa_hist_entries(plan, P.max_length, plan.smax, false);
             // pruning keeps wavefronts narrow: a first pass sized and grouped for a typical pruned width, then
             // a second pass with the full worst-case scratch for any pair that outgrew it
             int64_t width = 4 * ((int64_t)plan.adapt_max_dist + plan.adapt_min_len) + 64;

@@ -47,8 +47,10 @@
 // pass to any bucket it makes faster.
 #include <algorithm>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -678,6 +680,51 @@ int aim_batch_passes(aim_batch* b, int* first_pass, int* full_pass) {
         compact += b->groups1[k] != 0;
     }
     return compact;
+}
+
+int64_t aim_tune_export(aim_ctx* ctx, char* buf, size_t cap) {
+    if (!ctx || (cap && !buf)) return AIM_ERR_ARG;
+    std::string text;
+    if (ctx->tune_cache) {
+        char line[160];
+        for (const auto& kv : aim::tune_cache(ctx)) {
+            const auto& k = kv.first;
+            const auto& c = kv.second;
+            std::snprintf(line, sizeof(line), "%d %d %d %d %d %lld %d %d %d\n", std::get<0>(k), std::get<1>(k),
+                          std::get<2>(k), std::get<3>(k), std::get<4>(k), (long long)std::get<5>(k), std::get<0>(c),
+                          std::get<1>(c), std::get<2>(c));
+            text += line;
+        }
+    }
+    if (cap) {
+        const size_t n = std::min(text.size(), cap - 1);
+        std::memcpy(buf, text.data(), n);
+        buf[n] = 0;
+    }
+    return (int64_t)text.size();
+}
+
+int aim_tune_import(aim_ctx* ctx, const char* text) {
+    if (!ctx || !text) return AIM_ERR_ARG;
+    std::vector<std::pair<aim::TuneKey, aim::TuneChoice>> parsed;
+    const char* p = text;
+    while (*p) {
+        int x, o, e, band, bucket, g, g1, gb, used = 0;
+        long long smax;
+        if (std::sscanf(p, "%d %d %d %d %d %lld %d %d %d%n", &x, &o, &e, &band, &bucket, &smax, &g, &g1, &gb,
+                        &used) != 9)
+            return AIM_ERR_ARG;
+        const auto lanes_ok = [](int v, bool zero) { return (zero && v == 0) || v == 1 || v == 2 || v == 4 ||
+                                                            v == 8 || v == 16 || v == 32 || v == 256; };
+        if (bucket < 0 || bucket >= aim::kBuckets || !lanes_ok(g, false) || !lanes_ok(g1, true) ||
+            !(gb == 0 || gb == 4 || gb == 8 || gb == 16 || gb == 32))
+            return AIM_ERR_ARG;
+        parsed.emplace_back(aim::TuneKey(x, o, e, band, bucket, (int64_t)smax), aim::TuneChoice(g, g1, gb));
+        p += used;
+        while (*p == '\n' || *p == ' ' || *p == '\r' || *p == '\t') ++p;
+    }
+    for (const auto& kv : parsed) aim::tune_cache(ctx)[kv.first] = kv.second;
+    return AIM_OK;
 }
 
 int aim_batch_bound_passes(aim_batch* b, int* bound_pass) {

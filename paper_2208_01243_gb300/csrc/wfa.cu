@@ -1034,7 +1034,7 @@ int gcd_i(int a, int b) {
 }  // namespace
 
 // Worst-case entries of the wavefront history of one pair: every wavefront as wide as its sources allow.
-size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax) {
+size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax, bool clamp) {
     const int64_t klo = p.band >= 0 ? -std::min<int64_t>(max_len, p.band) : -max_len;
     const int64_t khi = p.band >= 0 ? std::min<int64_t>(max_len, p.band) : max_len;
     std::vector<int64_t> lo(smax + 1), hi(smax + 1);
@@ -1049,7 +1049,13 @@ size_t wfa_hist_entries(const WfaPlan& p, int64_t max_len, int64_t smax) {
         take(s - p.x, 0); take(s - p.oe, 1); take(s - p.e, 1);
         l = std::max(l, klo); h = std::min(h, khi);
         lo[s] = l; hi[s] = h;
-        if (l <= h) entries += (size_t)(h - l + 1);
+        if (l <= h) {
+            // exact kernels also clamp each wavefront to the 2 (S - s) / E + 1 diagonals around the end diagonal
+            // that can still end within the limit S <= smax (where they lie depends on the pair; how many does not)
+            int64_t w = h - l + 1;
+            if (clamp) w = std::min<int64_t>(w, 2 * ((smax - s) / std::max(p.e, 1)) + 1);
+            entries += (size_t)w;
+        }
     }
     return entries;
 }
@@ -1066,7 +1072,7 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     if (smax > trivial) smax = trivial;
     p.smax = smax;
     p.max_length = max_length;
-    p.hist_entries = wfa_hist_entries(p, L, smax);
+    p.hist_entries = wfa_hist_entries(p, L, smax, true);   // exact kernels (adaptive plans recompute it)
     // the live ring of the compact forms: a power-of-2 slot count above the farthest source (max(X, OE, E)
     // scores back) and a power-of-2 slot width above the widest wavefront (it grows by at most one diagonal on
     // each side per E score units: 2 smax / E + 3, within the matrix and the band)

@@ -53,7 +53,7 @@ def test_wfa_scratch_per_pair_compact_history():
     assert f8 / c16 > 3.8                       # 8 -> 2 bytes per entry, plus the records and the live ring
     c32 = aim.aim_wfa_scratch_per_pair(20_000, pen, 200, lanes=32)
     f8b = aim.aim_wfa_scratch_per_pair(20_000, pen, 200, lanes=16)
-    assert 1.8 < f8b / c32 < 2.1
+    assert 1.5 < f8b / c32 < 2.1                # 4-byte words against 8-byte entries, plus a 32-bit live ring
     # short reads keep the 8-byte entries whatever the group
     assert aim.aim_wfa_scratch_per_pair(150, pen, 6, lanes=32) == aim.aim_wfa_scratch_per_pair(150, pen, 6, lanes=4)
     # past 32,000 bp only the compact history can hold the offsets: 32 lanes at least, whatever is asked

@@ -133,6 +133,47 @@ def test_bound_pass_gives_the_plain_results(oracle_lib, gen_lib, autotune, band)
     assert np.array_equal(outs2[0][0], plain[0]) and np.array_equal(outs2[0][1], plain[1])
 
 
+def test_tune_choices_export_and_import(gen_lib):
+    """A plan made with autotune off in a context that imported another context's exported choices uses the same
+    lanes, compact and bound passes per bucket, and gives the same results; a malformed text imports nothing."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    p, me = _mixed(4_000, 1_003)
+    n = len(p)
+    cap = p.read_len.astype(np.int64) + p.target_len.astype(np.int64) + 1
+    coff = np.zeros(n + 1, np.int64); coff[1:] = np.cumsum(cap)
+    reads, targets, ro, to, rl, tl, cd, pp = aim.upload(p.reads, p.targets, p.read_off, p.target_off, p.read_len,
+                                                        p.target_len, coff, me.astype(np.int32))
+    ml = int(max(p.read_len.max(), p.target_len.max()))
+    runs = []
+    text = None
+    for autotune in (True, False):
+        al = aim.Aligner(0, 1 << 30)
+        if text is not None:
+            with pytest.raises(aim.AimError):
+                aim.aim_tune_import(al.ctx, "4 6 2 -1 3 200 32 0\n")        # a field short
+            assert aim.aim_tune_export(al.ctx) == ""
+            aim.aim_tune_import(al.ctx, text)
+            assert aim.aim_tune_export(al.ctx) == text
+        out = al.outputs(n, cigar_capacity=torch.from_numpy(cap))
+        out["cigars"].zero_()   # entries past a pair's runs are not written: compare whole buffers from zero
+        plan = aim.aim_batch_plan(al.ctx, reads, targets, ro, to, rl, tl, ml, aim.penalties(4, 6, 2), int(me.max()),
+                                  pp, out["scores"], out["cigars"], out["cigar_offsets"], out["cigar_lens"],
+                                  out["flags"], autotune=autotune)
+        aim.aim_batch_run(plan); torch.cuda.synchronize()
+        runs.append((aim.aim_batch_info(plan)[0], aim.aim_batch_passes(plan)[:2], aim.aim_batch_bound_passes(plan)[0],
+                     out["scores"].cpu().numpy().copy(), out["flags"].cpu().numpy().copy(),
+                     out["cigars"].cpu().numpy().copy()))
+        if autotune:
+            text = aim.aim_tune_export(al.ctx)
+            assert len(text.splitlines()) >= sum(1 for c in aim.aim_batch_info(plan)[1] if c)
+        aim.aim_batch_destroy(plan)
+        al.close()
+    a, b = runs
+    assert a[0] == b[0] and a[1] == b[1] and a[2] == b[2]
+    assert all(np.array_equal(x, y) for x, y in zip(a[3:], b[3:]))
+
+
 def test_batched_replay_sees_new_contents(gen_lib):
     """The plan binds buffers, not data: a replay after the inputs change aligns the new pairs."""
     import torch
