@@ -317,9 +317,8 @@ template <int G, bool ADAPT, bool STAGE, int FMT>
 __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* region, size_t region_bytes, uint32_t q0,
                                                 uint32_t qend, uint32_t lane, Counters& st) {
     static_assert(!STAGE || G <= 32, "sequence staging is per group of a warp");
-    static_assert(FMT == kFmt8 || FMT == kFmtBound || (!ADAPT && !STAGE),
-                  "compact histories are for the exact, unstaged kernels");
-    static_assert(FMT != kFmtBound || (ADAPT && G <= 32), "the bound pass prunes, with groups of up to 32 lanes");
+    static_assert(FMT == kFmt8 || (!ADAPT && !STAGE), "compact histories are for the exact, unstaged kernels");
+    static_assert(FMT != kFmtBound, "bound passes run bound_pass_run");
     using V = typename FmtT<FMT>::V;
     using H = typename FmtT<FMT>::H;
     constexpr int kNeg = FmtT<FMT>::kNeg;
@@ -332,9 +331,9 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     int16_t* hist = reinterpret_cast<int16_t*>(region + a.meta_bytes + a.runs_bytes);
     H* hc = reinterpret_cast<H*>(region + a.meta_bytes + a.runs_bytes);
     V* live = reinterpret_cast<V*>(region + region_bytes - (FMT == kFmt8 ? 0 : a.live_bytes));
-    const size_t hist_cap = FMT == kFmtBound ? ~(size_t)0 >> 1   // no history
-        : FMT == kFmt8 ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
-                       : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
+    const size_t hist_cap = FMT == kFmt8
+        ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
+        : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
     const int center = (int)(a.live_w / 2);
     const int X = a.X, OE = a.OE, E = a.E;
 
@@ -360,13 +359,11 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             status = kRun;
             int64_t S64 = lim / a.g;
             S = (int)(S64 > a.smax ? a.smax : S64);
-            if constexpr (FMT != kFmtBound) {
-                // a bound pass found an alignment of score ub (scaled): the optimum is at most ub, so a limit of ub
-                // rejects nothing the limit S would accept, and the reach clamp below keeps fewer diagonals
-                if (a.bound) {
-                    const int ub = a.bound[pi];
-                    if (ub >= 0 && ub < S) S = ub;
-                }
+            // a bound pass found an alignment of score ub (scaled): the optimum is at most ub, so a limit of ub
+            // rejects nothing the limit S would accept, and the reach clamp below keeps fewer diagonals
+            if (a.bound) {
+                const int ub = a.bound[pi];
+                if (ub >= 0 && ub < S) S = ub;
             }
             Pw = read_words(a.P, pi);
             Tw = target_words(a.P, pi);
@@ -375,7 +372,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             klo = a.band >= 0 ? max(-n, -a.band) : -n;
             khi = a.band >= 0 ? min(m, a.band) : m;
         }
-        if (gl == 0 && FMT != kFmtBound) st.pairs += 1;
+        if (gl == 0) st.pairs += 1;
     }
 
     // reach = (S - s) / E for the current score s, kept by a remainder instead of a division per score
@@ -428,7 +425,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         } else {   // live slot 0 at diagonal 0; history word 0
             V* e0 = live + (size_t)center * kEntryElems;
             e0[0] = (V)m0; e0[1] = (V)kNeg; e0[2] = (V)kNeg; e0[3] = 0;
-            if constexpr (FMT != kFmtBound) hc[0] = hist_word<FMT>(m0, false, false);
+            hc[0] = hist_word<FMT>(m0, false, false);
         }
         reinterpret_cast<int4*>(meta)[0] = make_int4(0, 1, 0, 1);
         if (kRing && ring) ring[0] = make_int4(0, 1, 0, 1);
@@ -466,7 +463,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
             if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
             lo = max(lo, klo); hi = min(hi, khi);
-            if constexpr (!ADAPT || FMT == kFmtBound) {
+            if constexpr (!ADAPT) {
                 // threshold: a path through diagonal k at score s still has to reach the end diagonal, a gap of
                 // |k - kend| bases costing at least E each, so only diagonals within (S - s) / E of kend can lie on
                 // an alignment of score <= S.  The sources of every entry kept lie within the same bound, so each
@@ -523,7 +520,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                                                           ((uint64_t)(uint32_t)del << 32);
                     else
                         *reinterpret_cast<int4*>(e) = make_int4(mv, ins, del, 0);
-                    if constexpr (FMT != kFmtBound) hc[base + k] = hist_word<FMT>(mv, ins_ext, del_ext);
+                    hc[base + k] = hist_word<FMT>(mv, ins_ext, del_ext);
                 }
                 if (k == kend) mv_end = mv;
                 if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
@@ -551,8 +548,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 for (int it = 0; it < iters; ++it) {
                     const int k = lo + gl + it * G;
                     if (prune && k >= vlo && k <= vhi) {
-                        const int h = FMT == kFmt8 ? hist[(size_t)(base + k) * kEntryElems]
-                                                   : (int)live[(size_t)(live_slot + k) * kEntryElems];
+                        const int h = hist[(size_t)(base + k) * kEntryElems];
                         if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
                             klo = min(klo, k);
                             khi = max(khi, k);
@@ -576,6 +572,201 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     }
 
     return Forward{status, final_s, top, pi};
+}
+
+// Bound pass with asynchronous groups: each group of G lanes runs its own pair and, the moment that pair ends,
+// records its bound and claims the next pair, which starts at score 0 while the warp's other groups carry on; a
+// warp never waits for its slowest pair (error rates vary tenfold within a bucket).  Every lane of the warp runs
+// each score step, each group on its own pair and score; the collectives are group-local and only the count of
+// diagonal iterations is warp-wide.  The step is the forward recurrence of the live-ring form with the pruning of
+// WFA-adaptive and the threshold clamp; nothing is kept for a traceback.
+template <int G, bool STAGE>
+__device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t* warp_slot, uint32_t lane,
+                                               Counters& st) {
+    static_assert(G <= 32, "bound passes use groups of a warp");
+    using V = int16_t;
+    constexpr int kNeg = kNeg16;
+    constexpr int P = 32 / G;
+    const Group<G> grp(lane);
+    const int g = grp.index(lane), gl = grp.gl;
+    const uint32_t begin = a.bounds ? a.bounds[b] : 0;
+    const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
+    const uint32_t arena16 = (uint32_t)((a.warp_bytes / P) >> 4);
+    uint8_t* region = warp_slot + ((size_t)g * arena16 << 4);
+    const int* meta = reinterpret_cast<const int*>(region);
+    int4* rec = reinterpret_cast<int4*>(region);
+    V* live = reinterpret_cast<V*>(region + ((size_t)arena16 << 4) - a.live_bytes);
+    const int center = (int)(a.live_w / 2);
+    const uint32_t smask = a.live_slots - 1;
+    const int X = a.X, OE = a.OE, E = a.E;
+    PairSeqs<STAGE> seqs;
+    if constexpr (STAGE) {
+        const uint32_t slot = (threadIdx.x >> 5) * (uint32_t)P + (uint32_t)g;
+        seqs.offP = slot * 2 * a.seq_slot_words;
+        seqs.offT = seqs.offP + a.seq_slot_words;
+    }
+    int status = kIdle;   // kRun: the group's pair is running; otherwise it takes the next one
+    bool more = true;     // the queue may still hold pairs
+    uint32_t pi = 0;
+    int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0, s = 0, reach = 0, rrem = 0;
+    for (;;) {
+        const bool need = status != kRun && more;
+        if (__any_sync(kFull, need)) {
+            uint32_t pos = 0;
+            if (need && gl == 0) pos = atomicAdd(a.counters + b, 1u);
+            pos = (uint32_t)grp.bcast((int)pos);
+            bool fresh = false;   // the group starts a pair now
+            if (need) {
+                if (pos >= end - begin || end <= begin) {
+                    more = false;
+                } else {
+                    pi = a.order ? a.order[begin + pos] : begin + pos;
+                    n = (int)a.P.read_len[pi];
+                    m = (int)a.P.target_len[pi];
+                    const int64_t lim = pair_limit(a.L, pi);
+                    kend = m - n;
+                    const bool usable = !pair_bad(a.P, pi) && (uint32_t)n <= a.P.max_length &&
+                                        (uint32_t)m <= a.P.max_length && lim != -2 &&
+                                        (a.band < 0 || (kend <= a.band && -kend <= a.band));
+                    if (!usable) {
+                        if (gl == 0) a.bound[pi] = -1;   // the exact pass reports the pair
+                    } else {
+                        const int64_t S64 = lim / a.g;
+                        S = (int)(S64 > a.smax ? a.smax : S64);
+                        klo = a.band >= 0 ? max(-n, -a.band) : -n;
+                        khi = a.band >= 0 ? min(m, a.band) : m;
+                        reach = S / E; rrem = S - reach * E;
+                        s = 0;
+                        fresh = true;
+                    }
+                }
+            }
+            const uint64_t* Pw = fresh ? read_words(a.P, pi) : nullptr;
+            const uint64_t* Tw = fresh ? target_words(a.P, pi) : nullptr;
+            const uint32_t nwP = (uint32_t)(n + 31) >> 5, nwT = (uint32_t)(m + 31) >> 5;
+            if constexpr (STAGE) {
+                if (fresh) {
+                    for (uint32_t j = (uint32_t)gl; j < nwP; j += (uint32_t)G) s_seq[seqs.offP + j] = __ldg(Pw + j);
+                    for (uint32_t j = (uint32_t)gl; j < nwT; j += (uint32_t)G) s_seq[seqs.offT + j] = __ldg(Tw + j);
+                    if (gl == 0) { s_seq[seqs.offP + nwP] = 0; s_seq[seqs.offT + nwT] = 0; }
+                }
+                __syncwarp();
+            } else if (fresh) {
+                seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
+            }
+            // score 0: diagonal 0 only (live slot 0)
+            int found0 = 0;
+            if (fresh && gl == 0) {
+                uint32_t w0 = 0;
+                const int m0 = extend<STAGE>(seqs, n, m, 0, 0, w0);
+                st.windows += w0;
+                ++st.cells;
+                *reinterpret_cast<uint64_t*>(live + (size_t)center * kEntryElems) =
+                    (uint64_t)(uint16_t)m0 | ((uint64_t)(uint16_t)kNeg << 16) | ((uint64_t)(uint16_t)kNeg << 32);
+                rec[0] = make_int4(0, 1, 0, 1);
+                found0 = kend == 0 && m0 >= m;
+            }
+            found0 = grp.bcast(found0);
+            if (fresh) {
+                if (found0) {
+                    if (gl == 0) a.bound[pi] = 0;
+                } else {
+                    status = kRun;
+                }
+            }
+            __syncwarp();
+        }
+        if (!__any_sync(kFull, status == kRun)) {
+            if (__any_sync(kFull, more)) continue;   // groups whose pair could not run claim again
+            break;
+        }
+        // one score step of every running group
+        bool run = status == kRun;
+        if (run) {
+            ++s;
+            if (--rrem < 0) { rrem += E; --reach; }
+            if (s > S) { status = kRejected; run = false; }
+        }
+        int lo = 0, hi = -1, w = 0;
+        Wf fx{0, 0, 0, 0}, fo{0, 0, 0, 0}, fe{0, 0, 0, 0};
+        if (run) {
+            fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+            fx.w = (int)(((uint32_t)(s - X) & smask) * a.live_w) + center;
+            fo.w = (int)(((uint32_t)(s - OE) & smask) * a.live_w) + center;
+            fe.w = (int)(((uint32_t)(s - E) & smask) * a.live_w) + center;
+            lo = 1 << 30; hi = -(1 << 30);
+            if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
+            if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
+            if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
+            lo = max(lo, klo); hi = min(hi, khi);
+            lo = max(lo, kend - reach); hi = min(hi, kend + reach);   // the threshold clamp
+            w = lo <= hi ? hi - lo + 1 : 0;
+            if (w && (lo + center < 0 || hi + center >= (int)a.live_w)) { status = kCap; run = false; w = 0; hi = lo - 1; }
+        }
+        const int iters = grp.iterations(w);
+        int mv_end = kNeg;
+        int vlo = 1 << 30, vhi = -(1 << 30);
+        const int live_slot = (int)(((uint32_t)s & smask) * a.live_w) + center;
+        uint32_t n_windows = 0;
+        int dmin = 1 << 30, dmax = -(1 << 30);
+        for (int it = 0; it < iters; ++it) {
+            const int k = lo + gl + it * G;
+            if (k <= hi) {
+                const unsigned hmax = (unsigned)min(m, n + k);
+                int ins = max(live_get<kFmtBound>(live, fo, 0, k + 1), live_get<kFmtBound>(live, fe, 1, k + 1));
+                int del = max(live_get<kFmtBound>(live, fo, 0, k - 1), live_get<kFmtBound>(live, fe, 2, k - 1)) + 1;
+                int mis = live_get<kFmtBound>(live, fx, 0, k) + 1;
+                if ((unsigned)ins > hmax) ins = kNeg;
+                if ((unsigned)del > hmax) del = kNeg;
+                if ((unsigned)mis > hmax) mis = kNeg;
+                const int f0 = max(mis, max(ins, del));
+                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);
+                *reinterpret_cast<uint64_t*>(live + (size_t)(live_slot + k) * kEntryElems) =
+                    (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
+                if (k == kend) mv_end = mv;
+                if (f0 >= 0) { vlo = min(vlo, k); vhi = max(vhi, k); }
+                if (mv >= 0) {
+                    const int dist = max(n - (mv - k), m - mv);
+                    dmin = min(dmin, dist);
+                    dmax = max(dmax, dist);
+                }
+            }
+        }
+        if (gl == 0) st.cells += (unsigned)w;
+        st.windows += n_windows;
+        grp.min_max(vlo, vhi);
+        const bool group_hit = grp.group_any(mv_end >= m);
+        // pruning as in WFA-adaptive: a wavefront of at least adapt_min_len diagonals keeps those within
+        // adapt_max_dist of the closest distance to the end
+        grp.min_max(dmin, dmax);
+        const bool prune = run && !group_hit && vlo <= vhi && vhi - vlo + 1 >= a.adapt_min_len &&
+                           dmax - dmin > a.adapt_max_dist;
+        if (__any_sync(kFull, prune)) {
+            int plo = 1 << 30, phi = -(1 << 30);
+            for (int it = 0; it < iters; ++it) {
+                const int k = lo + gl + it * G;
+                if (prune && k >= vlo && k <= vhi) {
+                    const int h = live[(size_t)(live_slot + k) * kEntryElems];
+                    if (h >= 0 && max(n - (h - k), m - h) - dmin <= a.adapt_max_dist) {
+                        plo = min(plo, k);
+                        phi = max(phi, k);
+                    }
+                }
+            }
+            grp.min_max(plo, phi);
+            if (prune) { vlo = plo; vhi = phi; }
+        }
+        if (run) {
+            if (gl == 0) rec[s] = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, 0, w) : make_int4(0, 0, 0, 0);
+            if (group_hit) status = kDone;
+        }
+        // a pair that ended in this step: its bound (the score at which it reached the end), or none
+        if (status == kDone || status == kRejected || status == kCap) {
+            if (gl == 0) a.bound[pi] = status == kDone ? s : -1;
+            status = kIdle;
+        }
+        __syncwarp();
+    }
 }
 
 // Traceback of one finished pair by one lane, from its region as the forward pass left it.  Returns the
@@ -851,21 +1042,9 @@ __device__ __forceinline__ void run_bucket(const WfaArgs& a, int b, uint8_t* war
     const uint32_t begin = a.bounds ? a.bounds[b] : 0;
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     if constexpr (FMT == kFmtBound) {
-        // bound pass: each group runs its pairs one after another in the same region (meta records, then the
-        // live ring at its end) and records the score each reached the end at (scaled), or -1: no bound
-        constexpr int P = 32 / G;
-        const Group<G> grp(lane);
-        const uint32_t arena16 = (uint32_t)((a.warp_bytes / P) >> 4);
-        uint8_t* region = warp_slot + ((size_t)grp.index(lane) * arena16 << 4);
-        for (;;) {
-            uint32_t pos = 0;
-            if (lane == 0) pos = atomicAdd(a.counters + b, (uint32_t)P);
-            pos = __shfl_sync(kFull, pos, 0);
-            if (pos >= end - begin || end <= begin) break;
-            const Forward f =
-                forward_pair<G, ADAPT, STAGE, FMT>(a, region, (size_t)arena16 << 4, begin + pos, end, lane, st);
-            if (f.status != kIdle && grp.gl == 0) a.bound[f.pi] = f.status == kDone ? f.final_s : -1;
-        }
+        // bound pass: asynchronous groups, each in its own region (meta records, then the live ring at its end)
+        (void)begin; (void)end;
+        bound_pass_run<G, STAGE>(a, b, warp_slot, lane, st);
     } else if constexpr (G > 32) {
         // the whole block takes one pair at a time in its arena (its warps' scratch regions); finished pairs
         // wait there, up to one per warp, and the first lane of warp w traces back the w-th
