@@ -193,7 +193,7 @@ AIM_API int aim_align_batch_ascii(aim_ctx *ctx, const uint8_t *reads, const uint
  *   to out_cigars + cigar_offsets[i] (entries past its run count are written as
  *   zero).  Pinned (page-locked) host buffers let the copies overlap the
  *   kernels; pageable ones work but copy synchronously.
- *   chunk_pairs   pairs per chunk (0: an eighth of the batch, at least 65,536)
+ *   chunk_pairs   pairs per chunk (0: a quarter of the batch, at least 65,536)
  *   bytes_moved   optional host[2]: bytes copied host-to-device and device-to-host
  * The batch goes through the device in chunks, two device slots in turn: while
  * one chunk aligns, the next one's inputs copy in and the previous one's
