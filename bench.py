@@ -181,8 +181,11 @@ def traffic_record(kernel: str, workload: str):
         return None
     if not rec:
         return None
-    src = os.path.join(ROOT, "paper_2208_01243_gb300", "csrc", rec["source"])
-    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != rec["source_sha"]:
+    # the record holds one hash over the kernel's sources (its .cu file and the shared header), in order
+    h = hashlib.sha256()
+    for name in rec["sources"]:
+        h.update(open(os.path.join(ROOT, "paper_2208_01243_gb300", "csrc", name), "rb").read())
+    if h.hexdigest()[:16] != rec["sources_sha"]:
         return None
     return rec
 

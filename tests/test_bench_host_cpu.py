@@ -56,12 +56,18 @@ def test_traffic_record_follows_the_source_hash(tmp_path, monkeypatch):
     src_dir.mkdir(parents=True)
     (tmp_path / "profiles").mkdir()
     src = src_dir / "k.cu"
+    hdr = src_dir / "h.cuh"
     src.write_bytes(b"__global__ void k() {}\n")
-    sha = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
-    rec = {"k:w": {"source": "k.cu", "source_sha": sha, "dram_bytes_per_launch": 123, "how": "test"}}
+    hdr.write_bytes(b"// shared\n")
+    sha = hashlib.sha256(src.read_bytes() + hdr.read_bytes()).hexdigest()[:16]
+    rec = {"k:w": {"sources": ["k.cu", "h.cuh"], "sources_sha": sha, "dram_bytes_per_launch": 123, "how": "test"}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.traffic_record("k", "w")["dram_bytes_per_launch"] == 123
     assert bench.traffic_record("k", "other") is None
+    hdr.write_bytes(b"// shared, changed\n")          # a change to the shared header voids the record too
+    assert bench.traffic_record("k", "w") is None
+    hdr.write_bytes(b"// shared\n")
+    assert bench.traffic_record("k", "w")["dram_bytes_per_launch"] == 123
     src.write_bytes(b"__global__ void k() { /* changed */ }\n")
     assert bench.traffic_record("k", "w") is None
