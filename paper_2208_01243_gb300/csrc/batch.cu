@@ -391,7 +391,7 @@ int autotune(aim_batch* b) {
         }
         // a bound pass, then the exact pass clamped at each pair's bound (only where no compact pass was chosen)
         int best_gb = 0;
-        if (best_g1 == 0 && b->ctx->batch_bound != 2 && b->max_length <= kMaxWfaLength16 && best_g <= 32) {
+        if (best_g1 == 0 && b->ctx->batch_bound != 2 && b->max_length <= kMaxWfaLength16) {
             WfaPlan bp = b->plan, ep = b->plan;
             bp.bound = ep.bound = b->bound;
             bp.bound_pass = 1;
@@ -401,7 +401,7 @@ int autotune(aim_batch* b) {
                 best_gb = kBoundDefaultGroup;   // forced: the default lanes, no trials
             } else {
                 for (int Gb : {4, 8, 16, 32}) {
-                    if (Gb > std::max(best_g, 4) || wfa_warp_bytes(Gb, bpb) * min_warps > b->scratch_bytes) continue;
+                    if (wfa_warp_bytes(Gb, bpb) * min_warps > b->scratch_bytes) continue;
                     float ms1 = 0.f, ms2 = 0.f;
                     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
                         e = trial(b, bp, tb, Gb, wfa_warp_bytes(Gb, bpb), t0, t1, &ms1);
@@ -537,8 +537,7 @@ int batch_plan_impl(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, 
             }
             if (ctx->batch_bound == 2) b->bound1[k] = 0;
             if (ctx->batch_bound == 1)   // bound passes run 4 to 32 lanes per pair, whatever the exact pass uses
-                b->bound1[k] = b->max_length <= kMaxWfaLength16 && b->groups[k] <= 32 && !b->groups1[k]
-                                   ? kBoundDefaultGroup : 0;
+                b->bound1[k] = b->max_length <= kMaxWfaLength16 && !b->groups1[k] ? kBoundDefaultGroup : 0;
         }
     }
     // buckets empty at planning keep one pair per warp, so their worst case does not shrink the grid
