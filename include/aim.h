@@ -386,7 +386,10 @@ AIM_API int aim_batch_destroy(aim_batch *batch);
  * warp); an admitted request gets one scratch grant of up to 1/16 of the
  * budget, split between its jobs, and runs on its own streams (copy in, pack,
  * one launch per job side by side, copy out), so its jobs and the requests
- * that arrive while others run overlap on the device.  Results are those of
+ * that arrive while others run overlap on the device.  Jobs of the heaviest
+ * work classes (work class >= 5, wavefronts over 256 diagonals; reads up to
+ * 32,000 bp) run a bound pass first, as the batched form's tuner chooses for
+ * such buckets.  Results are those of
  * aim_align_batch_ascii for the same pairs, independent of what else runs.
  * aim_server_create allocates the arenas and starts the worker thread.
  */

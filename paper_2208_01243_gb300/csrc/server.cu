@@ -106,6 +106,7 @@ struct Request {
         uint32_t begin, count;
         WfaPlan plan;
         int group;
+        int bound_group;     // lanes per pair of a bound pass before the exact one (0: none)
         size_t warp_bytes;
         size_t warps;        // wanted
         size_t slice_off, slice_bytes;   // its part of the request's scratch grant
@@ -131,8 +132,8 @@ struct Request {
 
 // Byte layout of one request inside the device I/O region (and its pinned staging twin).
 struct IoLayout {
-    size_t reads, targets, roff, toff, rl, tl, me, coff, order, packed_r, packed_t, bad_r, bad_t, counter, scores, flags,
-        lens, cigars, total, in_bytes;
+    size_t reads, targets, roff, toff, rl, tl, me, coff, order, packed_r, packed_t, bad_r, bad_t, counter, bound, scores,
+        flags, lens, cigars, total, in_bytes;
     uint64_t stride;
 };
 
@@ -162,7 +163,8 @@ IoLayout layout_of(const Request& r) {
     L.packed_t = take((size_t)r.n * L.stride * 8);
     L.bad_r = take(r.n);
     L.bad_t = take(r.n);
-    L.counter = take(32 * sizeof(uint32_t));
+    L.counter = take(64 * sizeof(uint32_t));   // per job: the exact pass's claim counter, then the bound pass's
+    L.bound = take(r.n * 4);                    // per pair: the bound pass's score bound
     L.total = o;
     (void)out_end;
     return L;
@@ -304,15 +306,32 @@ int launch_request(aim_server* s, Request* r) {
         uint32_t* counter = reinterpret_cast<uint32_t*>(d + L.counter) + j % 32;
         e = cudaStreamWaitEvent(js, r->events[0], 0);
         if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, sizeof(uint32_t), js);
+        if (e == cudaSuccess && job.bound_group) e = cudaMemsetAsync(counter + 32, 0, sizeof(uint32_t), js);
         if (e != cudaSuccess) break;
         PairsView P{reinterpret_cast<const uint64_t*>(d + L.packed_r), reinterpret_cast<const uint64_t*>(d + L.packed_t),
                     nullptr, nullptr, reinterpret_cast<const uint32_t*>(d + L.rl),
                     reinterpret_cast<const uint32_t*>(d + L.tl), d + L.bad_r, d + L.bad_t, job.count, r->max_len};
         P.stride = L.stride;
+        uint8_t* slice = s->dev_scratch + r->scratch_off + job.slice_off;
+        WfaPlan exact = job.plan;
         int warps = 0;
-        e = launch_wfa_buckets(job.plan, P, lim, O, order + job.begin, nullptr, &job.group, 1, job.warp_bytes,
-                               s->dev_scratch + r->scratch_off + job.slice_off, job.slice_bytes, counter, s->num_sms,
-                               js, &warps);
+        if (job.bound_group) {
+            // a bound pass in the job's scratch slice first (the exact pass then reuses the slice); if not one
+            // block of it fits, the exact pass runs alone
+            WfaPlan bp = job.plan;
+            bp.bound = reinterpret_cast<int32_t*>(d + L.bound);
+            bp.bound_pass = 1;
+            int bg = job.bound_group;
+            const size_t bwb = wfa_warp_bytes(bg, wfa_bound_pair_bytes(job.plan));
+            if (8 * bwb <= job.slice_bytes) {
+                e = launch_wfa_buckets(bp, P, lim, O, order + job.begin, nullptr, &bg, 1, bwb, slice, job.slice_bytes,
+                                       counter + 32, s->num_sms, js, &warps);
+                if (e == cudaSuccess && warps > 0) exact.bound = bp.bound;
+            }
+            if (e != cudaSuccess) break;
+        }
+        e = launch_wfa_buckets(exact, P, lim, O, order + job.begin, nullptr, &job.group, 1, job.warp_bytes, slice,
+                               job.slice_bytes, counter, s->num_sms, js, &warps);
         if (e == cudaSuccess && warps == 0) e = cudaErrorMemoryAllocation;
         if (e == cudaSuccess) e = cudaEventRecord(r->events[1 + j], js);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(st, r->events[1 + j], 0);
@@ -532,6 +551,11 @@ int aim_server_submit(aim_server* s, const aim_request* q, uint64_t* ticket) {
             job.group = 32;
             job.warp_bytes = wfa_pair_bytes(job.plan, 32);
         }
+        // a bound pass before the exact one for the heaviest classes (work class >= 5, wavefronts over 256
+        // diagonals), where the batched form's tuner keeps one: 4 lanes per pair before groups of up to 32 lanes,
+        // 16 before whole blocks.  Results are the exact pass's either way.
+        const int key = keyed[i].first, kc = 7 - key / 4, wc = 3 - key % 4;
+        job.bound_group = kc >= 5 && wc == 3 && r->max_len <= kMaxWfaLength16 ? (job.group > 32 ? 16 : 4) : 0;
         // warps wanted: every pair in flight at once (a 256-lane group uses 8 warps), within the device's capacity
         const size_t want = job.group > 32 ? (size_t)job.count * (job.group / 32)
                                            : (job.count + (32 / job.group) - 1) / (size_t)(32 / job.group);
