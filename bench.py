@@ -82,7 +82,7 @@ def parse():
                          "or CPU baseline): the command profile captures run, so the step's launches come last")
     ap.add_argument("--lanes", type=int, default=0, help="lanes per pair for the plain WFA calls (0: library choice)")
     ap.add_argument("--serve-seconds", type=float, default=6.0, help="offered-load duration per load level")
-    ap.add_argument("--serve-probe-seconds", type=float, default=4.0,
+    ap.add_argument("--serve-probe-seconds", type=float, default=8.0,
                     help="duration of each open-loop rate tried while searching the serving peak")
     ap.add_argument("--serve-budget-gb", type=float, default=160.0, help="serving wavefront-state budget (GiB)")
     return ap.parse_args()
@@ -666,7 +666,10 @@ def serving(args, local):
 
     def run(arrivals, sizes):
         """Submit at the given times; returns latencies (s, submission order), pairs, wall time (first submission to
-        last completion) and queue samples (s since start, requests queued or running)."""
+        last completion) and queue samples (s since start, requests queued or running).  Every run draws its
+        requests' pairs from the start of the pool, so a run's requests are the same from one bench run to the next
+        (the largest of them, up to 4096 pairs of reads up to 10 kbp, set the p99)."""
+        cursor[0] = 0
         t0 = time.perf_counter()
         tickets, queue = [], []
         for a, k in zip(arrivals, sizes):
@@ -709,7 +712,12 @@ def serving(args, local):
         first, last = float(np.median(lat[:q])), float(np.median(lat[-q:]))
         sustained = pairs / wall
         rate = float(sz.sum()) / float(arr[-1])
-        bounded = last <= 2.0 * first + 0.02 and sustained >= 0.95 * rate
+        # the queue (sampled at submissions) must not grow either: its mean over the last quarter of the run
+        # within 2x that of the first quarter + 4 requests
+        qn = len(queue) // 4
+        q_first = float(np.mean([c for _, c in queue[:qn]])) if qn else 0.0
+        q_last = float(np.mean([c for _, c in queue[-qn:]])) if qn else 0.0
+        bounded = (last <= 2.0 * first + 0.02 and sustained >= 0.95 * rate and q_last <= 2.0 * q_first + 4)
         trials.append({"offered_pairs_per_s": rate, "fraction_of_closed_loop": frac, "bounded": bool(bounded),
                        "sustained_alignments_per_s": sustained, "p50_first_quarter_ms": first * 1e3,
                        "p50_last_quarter_ms": last * 1e3, "max_queue": int(max(x[1] for x in queue))})
@@ -739,9 +747,10 @@ def serving(args, local):
     return {"workload": "serve_100_10000bp_1_10pct: Poisson requests of 1-4096 pairs (log-uniform), reads "
                         "100-10,000 bp (log-uniform), 1-10 % edits, WFA 4/6/2, thresholds ceil(0.1*len)",
             "wavefront_budget_gib": args.serve_budget_gb, "peak_alignments_per_s": peak,
-            "peak_rule": "highest open-loop Poisson rate (falling fractions of the closed-loop throughput) whose "
-                         "median latency in the last quarter of the run stays within 2x that of the first quarter "
-                         "+ 20 ms and whose sustained throughput is >= 95 % of the offered rate",
+            "peak_rule": "highest open-loop Poisson rate (falling fractions of the closed-loop throughput, "
+                         f"{args.serve_probe_seconds:g} s each) whose median latency and mean queue length in the last "
+                         "quarter of the run stay within 2x those of the first quarter (+ 20 ms, + 4 requests) and "
+                         "whose sustained throughput is >= 95 % of the offered rate",
             "closed_loop_alignments_per_s": closed, "peak_search": trials, "mean_pairs_per_request": mean_req,
             "loads": levels, "failed": st["failed"],
             "latency": "server clock from submission to results in host memory (includes queueing, copies)"}

@@ -410,8 +410,8 @@ typedef struct {
 /* pen: costs and band for every request (max_score must be < 0: thresholds are per pair). */
 AIM_API int aim_server_create(aim_ctx *ctx, const aim_penalties_t *pen, size_t wavefront_budget_bytes,
                               size_t io_budget_bytes, aim_server **out);
-/* Copies the request's inputs and queues it; the output buffers must stay valid until it completes (CIGAR
- * entries past a pair's run count are written as zero).
+/* Copies the request's inputs and queues it; the output buffers must stay valid until it completes (only each
+ * pair's first cigar_lens[i] CIGAR entries are written; entries past them keep what the caller left there).
  * AIM_ERR_NOMEM: one pair's wavefront scratch or the request's I/O exceeds the server's budgets. */
 AIM_API int aim_server_submit(aim_server *server, const aim_request *request, uint64_t *ticket);
 /* *done = 1 once the request's results are in its output buffers; then the ticket is released and

@@ -279,8 +279,6 @@ int launch_request(aim_server* s, Request* r) {
     cudaStream_t st = r->stream;
     cudaError_t e = cudaMemcpyAsync(d, h, L.in_bytes, cudaMemcpyHostToDevice, st);
     // the whole CIGAR region is copied back: runs past each pair's count read as zero, not as an earlier request's
-    if (e == cudaSuccess && r->out_cigars && r->cigar_total)
-        e = cudaMemsetAsync(d + L.cigars, 0, r->cigar_total * 4, st);
     if (e == cudaSuccess)
         e = launch_pack(d + L.reads, reinterpret_cast<const uint64_t*>(d + L.roff),
                         reinterpret_cast<const uint32_t*>(d + L.rl), r->n, reinterpret_cast<uint64_t*>(d + L.packed_r),
@@ -352,7 +350,17 @@ void finish(aim_server* s, Request* r) {
     std::memcpy(r->out_scores, h + L.scores, r->n * 4);
     std::memcpy(r->out_flags, h + L.flags, r->n);
     if (r->out_lens) std::memcpy(r->out_lens, h + L.lens, r->n * 4);
-    if (r->out_cigars) std::memcpy(r->out_cigars, h + L.cigars, r->cigar_total * 4);
+    if (r->out_cigars) {
+        // each pair's runs only (a few hundred bytes), not the request's whole run capacity: the worker thread that
+        // does this also admits and completes the other requests
+        const uint32_t* lens = reinterpret_cast<const uint32_t*>(h + L.lens);
+        const uint32_t* runs = reinterpret_cast<const uint32_t*>(h + L.cigars);
+        for (uint32_t i = 0; i < r->n; ++i) {
+            const uint64_t at = r->coff[i], cap = r->coff[i + 1] - at;
+            const uint64_t cnt = std::min<uint64_t>(lens[i], cap);
+            if (cnt) std::memcpy(r->out_cigars + at, runs + at, cnt * 4);
+        }
+    }
 }
 
 void worker_loop(aim_server* s) {
