@@ -334,6 +334,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     const size_t hist_cap = FMT == kFmt8
         ? (region_bytes - a.meta_bytes - a.runs_bytes) / (kEntryElems * sizeof(int16_t))
         : (region_bytes - a.meta_bytes - a.runs_bytes - a.live_bytes) / sizeof(H);
+    const int hist_cap32 = (int)(hist_cap < (size_t)INT32_MAX ? hist_cap : (size_t)INT32_MAX);
     const int center = (int)(a.live_w / 2);
     const int X = a.X, OE = a.OE, E = a.E;
 
@@ -412,14 +413,13 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         }
     }
 
-    // score 0: diagonal 0 only
+    // score 0: diagonal 0 only.  The pair's entries (top) and extend windows are added to the launch's counters
+    // once, at its end.
+    uint32_t pair_windows = 0;
     int top = 0, final_s = 0;
     int found0 = 0;
     if (status == kRun && gl == 0) {
-        uint32_t w0 = 0;
-        const int m0 = extend<STAGE>(seqs, n, m, 0, 0, w0);
-        st.windows += w0;
-        ++st.cells;
+        const int m0 = extend<STAGE>(seqs, n, m, 0, 0, pair_windows);
         if constexpr (FMT == kFmt8) {
             hist[0] = (int16_t)m0; hist[1] = kNeg16; hist[2] = kNeg16; hist[3] = 0;
         } else {   // live slot 0 at diagonal 0; history word 0
@@ -472,7 +472,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 lo = max(lo, kend - reach); hi = min(hi, kend + reach);
             }
             w = lo <= hi ? hi - lo + 1 : 0;
-            if (w && ((size_t)top + (size_t)w > hist_cap ||
+            if (w && (top + w > hist_cap32 ||
                       (FMT != kFmt8 && (lo + center < 0 || hi + center >= (int)a.live_w)))) {
                 status = kCap; run = false; w = 0; hi = lo - 1;
             }
@@ -482,7 +482,6 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         int vlo = 1 << 30, vhi = -(1 << 30);   // trimmed range: diagonals holding a valid entry
         const int base = top - lo;
         const int live_slot = FMT == kFmt8 ? 0 : (int)(((uint32_t)s & (a.live_slots - 1)) * a.live_w) + center;
-        uint32_t n_windows = 0;
         int dmin = 1 << 30, dmax = -(1 << 30);   // WFA-adaptive: distances of the new entries to the end cell
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
@@ -508,7 +507,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 if ((unsigned)del > hmax) del = kNeg;
                 if ((unsigned)mis > hmax) mis = kNeg;
                 const int f0 = max(mis, max(ins, del));   // >= 0 iff any candidate is valid
-                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);   // f0 stays negative if invalid
+                const int mv = extend<STAGE>(seqs, n, m, k, f0, pair_windows);   // f0 stays negative if invalid
                 if constexpr (FMT == kFmt8) {
                     *reinterpret_cast<uint64_t*>(hist + (size_t)(base + k) * kEntryElems) =
                         (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
@@ -531,8 +530,6 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 }
             }
         }
-        if (gl == 0) st.cells += (unsigned)w;   // the wavefront's entries, computed by the group's lanes
-        st.windows += n_windows;
         grp.min_max(vlo, vhi);   // group-wide trimmed range
         const bool group_hit = grp.group_any(mv_end >= m);
         if constexpr (ADAPT) {
@@ -571,6 +568,8 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         grp.sync();
     }
 
+    if (gl == 0) st.cells += (unsigned)top;   // the pair's entries, computed by the group's lanes
+    st.windows += pair_windows;
     return Forward{status, final_s, top, pi};
 }
 
