@@ -259,7 +259,10 @@ struct Group<G, false> {
             }
         }
     }
-    __device__ bool group_any(bool x) const { return (__ballot_sync(kFull, x) & gmask) != 0; }
+    __device__ bool group_any(bool x) const {
+        if constexpr (G == 32) return __any_sync(kFull, x);
+        else return (__ballot_sync(kFull, x) & gmask) != 0;
+    }
     __device__ int bcast(int x) const { return __shfl_sync(kFull, x, leader); }
     __device__ void sync() const { __syncwarp(); }
 };
@@ -605,6 +608,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
         seqs.offT = seqs.offP + a.seq_slot_words;
     }
     int status = kIdle;   // kRun: the group's pair is running; otherwise it takes the next one
+    uint32_t p_cells = 0, p_windows = 0;   // the running pair's entries and windows, added to st when it ends
     bool more = true;     // the queue may still hold pairs
     uint32_t pi = 0;
     int n = 0, m = 0, S = 0, kend = 0, klo = 0, khi = 0, s = 0, reach = 0, rrem = 0;
@@ -656,10 +660,8 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
             // score 0: diagonal 0 only (live slot 0)
             int found0 = 0;
             if (fresh && gl == 0) {
-                uint32_t w0 = 0;
-                const int m0 = extend<STAGE>(seqs, n, m, 0, 0, w0);
-                st.windows += w0;
-                ++st.cells;
+                const int m0 = extend<STAGE>(seqs, n, m, 0, 0, p_windows);
+                ++p_cells;
                 *reinterpret_cast<uint64_t*>(live + (size_t)center * kEntryElems) =
                     (uint64_t)(uint16_t)m0 | ((uint64_t)(uint16_t)kNeg << 16) | ((uint64_t)(uint16_t)kNeg << 32);
                 rec[0] = make_int4(0, 1, 0, 1);
@@ -669,6 +671,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
             if (fresh) {
                 if (found0) {
                     if (gl == 0) a.bound[pi] = 0;
+                    st.cells += p_cells; st.windows += p_windows; p_cells = p_windows = 0;
                 } else {
                     status = kRun;
                 }
@@ -706,7 +709,6 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
         int mv_end = kNeg;
         int vlo = 1 << 30, vhi = -(1 << 30);
         const int live_slot = (int)(((uint32_t)s & smask) * a.live_w) + center;
-        uint32_t n_windows = 0;
         int dmin = 1 << 30, dmax = -(1 << 30);
         for (int it = 0; it < iters; ++it) {
             const int k = lo + gl + it * G;
@@ -719,7 +721,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
                 if ((unsigned)del > hmax) del = kNeg;
                 if ((unsigned)mis > hmax) mis = kNeg;
                 const int f0 = max(mis, max(ins, del));
-                const int mv = extend<STAGE>(seqs, n, m, k, f0, n_windows);
+                const int mv = extend<STAGE>(seqs, n, m, k, f0, p_windows);
                 *reinterpret_cast<uint64_t*>(live + (size_t)(live_slot + k) * kEntryElems) =
                     (uint64_t)(uint16_t)mv | ((uint64_t)(uint16_t)ins << 16) | ((uint64_t)(uint32_t)del << 32);
                 if (k == kend) mv_end = mv;
@@ -731,8 +733,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
                 }
             }
         }
-        if (gl == 0) st.cells += (unsigned)w;
-        st.windows += n_windows;
+        if (gl == 0) p_cells += (unsigned)w;
         grp.min_max(vlo, vhi);
         const bool group_hit = grp.group_any(mv_end >= m);
         // pruning as in WFA-adaptive: a wavefront of at least adapt_min_len diagonals keeps those within
@@ -762,6 +763,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
         // a pair that ended in this step: its bound (the score at which it reached the end), or none
         if (status == kDone || status == kRejected || status == kCap) {
             if (gl == 0) a.bound[pi] = status == kDone ? s : -1;
+            st.cells += p_cells; st.windows += p_windows; p_cells = p_windows = 0;
             status = kIdle;
         }
         __syncwarp();
