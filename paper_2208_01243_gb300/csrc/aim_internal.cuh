@@ -136,7 +136,9 @@ struct WfaPlan {
     uint32_t live_w;     // compact forms: entries per live-ring slot (a power of 2 above the widest wavefront)
     uint32_t live_slots; // compact forms: live-ring slots (a power of 2 above the farthest source score)
     int runs_cap;        // CIGAR runs staged per pair
-    size_t meta_bytes;   // per-score (lo, count, base, width) records, int4 each
+    int rec_pad;         // empty records before record 0 (max(x, oe, e)): every source record s - x, s - oe,
+                         // s - e of a score s >= 0 can be read without a check
+    size_t meta_bytes;   // those and the per-score (lo, count, base, width) records, int4 each
     size_t runs_bytes;   // run staging
     int adapt_min_len;   // WFA-adaptive: prune wavefronts spanning >= this many diagonals (< 0: exact WFA)
     int adapt_max_dist;  // WFA-adaptive: drop outer diagonals more than this behind the closest to the end
@@ -182,6 +184,7 @@ struct WfaArgs {
     size_t pair_bytes;         // scratch one pair of a G-lane group may need (G <= 32; the rest of the group's
                                // share holds finished pairs awaiting their traceback)
     size_t meta_bytes, runs_bytes;
+    uint32_t rec_pad;          // empty records before record 0 in each pair's region
     uint32_t runs_cap;
     uint32_t nwarps;
     uint32_t seq_slot_words;   // words per sequence copy in shared memory (0: the extend reads global memory)

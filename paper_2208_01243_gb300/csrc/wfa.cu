@@ -88,6 +88,14 @@ __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     return f;
 }
 
+// the same for a score s >= -rec_pad of a pair region whose padding records are written (no check)
+__device__ __forceinline__ Wf load_rec(const int* meta, int s) {
+    const int4 q = reinterpret_cast<const int4*>(meta)[s];
+    Wf f;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
+    return f;
+}
+
 __device__ __forceinline__ int wf_hi(const Wf& f) { return f.lo + f.cnt - 1; }
 
 // component c (0 M, 1 I, 2 D) of wavefront f at diagonal k, or a negative value
@@ -327,7 +335,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
     constexpr int kNeg = FmtT<FMT>::kNeg;
     const Group<G> grp(lane);
     const int g = grp.index(lane), gl = grp.gl;
-    int* meta = reinterpret_cast<int*>(region);
+    int* meta = reinterpret_cast<int*>(region + (size_t)a.rec_pad * sizeof(int4));   // record 0
     // kFmt8: the history holds every wavefront whole and the forward pass reads it back.  Compact forms: the live
     // ring sits at the end of the region (each forward pass of the group uses the same place), the history of
     // compact words after the run staging.
@@ -416,6 +424,10 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         }
     }
 
+    // the empty records before record 0 (the sources of the first scores), written by the group's lanes
+    if (status == kRun)
+        for (int j = gl; j < (int)a.rec_pad; j += G) reinterpret_cast<int4*>(meta)[-1 - j] = make_int4(0, 0, 0, 0);
+
     // score 0: diagonal 0 only.  The pair's entries (top) and extend windows are added to the launch's counters
     // once, at its end.
     uint32_t pair_windows = 0;
@@ -453,7 +465,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             if constexpr (kRing) {
                 fx = load_wf(src, s - X, mask); fo = load_wf(src, s - OE, mask); fe = load_wf(src, s - E, mask);
             } else {
-                fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+                fx = load_rec(meta, s - X); fo = load_rec(meta, s - OE); fe = load_rec(meta, s - E);
             }
             if constexpr (FMT != kFmt8) {   // Wf.w becomes the entry of diagonal 0 in the source's live slot
                 const uint32_t sm = a.live_slots - 1;
@@ -595,8 +607,8 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
     const uint32_t end = a.bounds ? a.bounds[b + 1] : a.P.num_pairs;
     const uint32_t arena16 = (uint32_t)((a.warp_bytes / P) >> 4);
     uint8_t* region = warp_slot + ((size_t)g * arena16 << 4);
-    const int* meta = reinterpret_cast<const int*>(region);
-    int4* rec = reinterpret_cast<int4*>(region);
+    const int* meta = reinterpret_cast<const int*>(region + (size_t)a.rec_pad * sizeof(int4));   // record 0
+    int4* rec = reinterpret_cast<int4*>(region + (size_t)a.rec_pad * sizeof(int4));
     V* live = reinterpret_cast<V*>(region + ((size_t)arena16 << 4) - a.live_bytes);
     const int center = (int)(a.live_w / 2);
     const uint32_t smask = a.live_slots - 1;
@@ -657,6 +669,8 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
             } else if (fresh) {
                 seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
             }
+            if (fresh)   // the empty records before record 0
+                for (int j = gl; j < (int)a.rec_pad; j += G) rec[-1 - j] = make_int4(0, 0, 0, 0);
             // score 0: diagonal 0 only (live slot 0)
             int found0 = 0;
             if (fresh && gl == 0) {
@@ -692,7 +706,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
         int lo = 0, hi = -1, w = 0;
         Wf fx{0, 0, 0, 0}, fo{0, 0, 0, 0}, fe{0, 0, 0, 0};
         if (run) {
-            fx = load_wf(meta, s - X); fo = load_wf(meta, s - OE); fe = load_wf(meta, s - E);
+            fx = load_rec(meta, s - X); fo = load_rec(meta, s - OE); fe = load_rec(meta, s - E);
             fx.w = (int)(((uint32_t)(s - X) & smask) * a.live_w) + center;
             fo.w = (int)(((uint32_t)(s - OE) & smask) * a.live_w) + center;
             fe.w = (int)(((uint32_t)(s - E) & smask) * a.live_w) + center;
@@ -775,7 +789,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
 // expected) or the runs overflow the staging area.
 template <bool ADAPT>
 __device__ uint32_t traceback(const WfaArgs& a, uint8_t* region, uint32_t pi, int final_s, bool& ok) {
-    const int* meta = reinterpret_cast<const int*>(region);
+    const int* meta = reinterpret_cast<const int*>(region + (size_t)a.rec_pad * sizeof(int4));
     uint32_t* staged = reinterpret_cast<uint32_t*>(region + a.meta_bytes);
     const int16_t* hist = reinterpret_cast<const int16_t*>(region + a.meta_bytes + a.runs_bytes);
     const int n = (int)a.P.read_len[pi], m = (int)a.P.target_len[pi];
@@ -889,7 +903,7 @@ __device__ __noinline__ uint32_t traceback_compact(const WfaArgs& a, uint8_t* re
     constexpr int B = FmtT<FMT>::kBits;
     constexpr uint32_t kField = (1u << B) - 1;
     constexpr int kNeg = FmtT<FMT>::kNeg;
-    const int* meta = reinterpret_cast<const int*>(region);
+    const int* meta = reinterpret_cast<const int*>(region + (size_t)a.rec_pad * sizeof(int4));
     uint32_t* staged = reinterpret_cast<uint32_t*>(region + a.meta_bytes);
     const H* hc = reinterpret_cast<const H*>(region + a.meta_bytes + a.runs_bytes);
     const int n = (int)a.P.read_len[pi], m = (int)a.P.target_len[pi];
@@ -1267,7 +1281,8 @@ WfaPlan plan_wfa(const Costs& c, int band, uint32_t max_length, int64_t max_limi
     int64_t runs = 2 * L + 1;
     if (minc > 0) runs = std::min<int64_t>(runs, 2 * (smax / minc) + 1);
     p.runs_cap = (int)runs;
-    p.meta_bytes = align_up((size_t)(smax + 1) * 4 * sizeof(int), 16);
+    p.rec_pad = std::max(std::max(p.x, p.oe), p.e);
+    p.meta_bytes = align_up((size_t)(smax + 1 + p.rec_pad) * 4 * sizeof(int), 16);
     p.runs_bytes = align_up((size_t)p.runs_cap * sizeof(uint32_t), 16);
     p.adapt_min_len = -1;
     p.adapt_max_dist = 0;
@@ -1330,6 +1345,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
     a.P = P; a.L = L; a.O = O;
     a.scratch = scratch; a.warp_bytes = warp_bytes;
     a.meta_bytes = plan.meta_bytes; a.runs_bytes = plan.runs_bytes; a.runs_cap = (uint32_t)plan.runs_cap;
+    a.rec_pad = (uint32_t)plan.rec_pad;
     a.order = order; a.bounds = bounds; a.counters = counters; a.nbuckets = nbuckets;
     // a bound pass prunes with its own parameters and writes plan.bound; exact passes read it when it is set
     const bool bound_pass = plan.bound_pass != 0;
