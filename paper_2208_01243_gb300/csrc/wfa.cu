@@ -67,24 +67,30 @@ namespace {
 
 struct Wf {
     int lo, cnt, base, w;   // diagonals lo .. lo+cnt-1 (cnt == 0: empty); component c of diagonal k at element
-                            // (base + k) * kEntryElems + c (base: first entry, already offset by -lo)
+                            // (base + k) * kEntryElems + c (base: first entry, already offset by -lo); w: set by
+                            // the compact forms to the live-slot entry of diagonal 0
+    int hi;                 // lo + cnt - 1, stored in the record (an empty record has lo > hi, far apart, so a
+                            // union of source ranges needs no test for empty ones)
 };
+// a score record (lo, count, base, hi) and the empty one
+constexpr int kEmptyLo = 1 << 29, kEmptyHi = -(1 << 29);
+__device__ __forceinline__ int4 empty_rec() { return make_int4(kEmptyLo, 0, 0, kEmptyHi); }
 
 // record of score s: element s & mask of rec (mask -1: the group's records in scratch; R-1: its ring of the
 // last R scores in shared memory)
 __device__ __forceinline__ Wf load_wf(const int4* rec, int s, int mask) {
     Wf f;
-    if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
+    if (s < 0) { f.lo = kEmptyLo; f.cnt = 0; f.base = 0; f.w = 0; f.hi = kEmptyHi; return f; }
     const int4 q = rec[s & mask];
-    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = 0; f.hi = q.w;
     return f;
 }
 
 __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
     Wf f;
-    if (s < 0) { f.lo = 0; f.cnt = 0; f.base = 0; f.w = 0; return f; }
+    if (s < 0) { f.lo = kEmptyLo; f.cnt = 0; f.base = 0; f.w = 0; f.hi = kEmptyHi; return f; }
     const int4 q = reinterpret_cast<const int4*>(meta)[s];
-    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = 0; f.hi = q.w;
     return f;
 }
 
@@ -92,11 +98,9 @@ __device__ __forceinline__ Wf load_wf(const int* meta, int s) {
 __device__ __forceinline__ Wf load_rec(const int* meta, int s) {
     const int4 q = reinterpret_cast<const int4*>(meta)[s];
     Wf f;
-    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = q.w;
+    f.lo = q.x; f.cnt = q.y; f.base = q.z; f.w = 0; f.hi = q.w;
     return f;
 }
-
-__device__ __forceinline__ int wf_hi(const Wf& f) { return f.lo + f.cnt - 1; }
 
 // component c (0 M, 1 I, 2 D) of wavefront f at diagonal k, or a negative value
 __device__ __forceinline__ int wf_get(const int16_t* hist, const Wf& f, int c, int k) {
@@ -426,7 +430,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
 
     // the empty records before record 0 (the sources of the first scores), written by the group's lanes
     if (status == kRun)
-        for (int j = gl; j < (int)a.rec_pad; j += G) reinterpret_cast<int4*>(meta)[-1 - j] = make_int4(0, 0, 0, 0);
+        for (int j = gl; j < (int)a.rec_pad; j += G) reinterpret_cast<int4*>(meta)[-1 - j] = empty_rec();
 
     // score 0: diagonal 0 only.  The pair's entries (top) and extend windows are added to the launch's counters
     // once, at its end.
@@ -442,8 +446,8 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
             e0[0] = (V)m0; e0[1] = (V)kNeg; e0[2] = (V)kNeg; e0[3] = 0;
             hc[0] = hist_word<FMT>(m0, false, false);
         }
-        reinterpret_cast<int4*>(meta)[0] = make_int4(0, 1, 0, 1);
-        if (kRing && ring) ring[0] = make_int4(0, 1, 0, 1);
+        reinterpret_cast<int4*>(meta)[0] = make_int4(0, 1, 0, 0);
+        if (kRing && ring) ring[0] = make_int4(0, 1, 0, 0);
         found0 = (kend == 0 && m0 >= m);
     }
     found0 = grp.bcast(found0);
@@ -473,10 +477,9 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
                 fo.w = (int)(((uint32_t)(s - OE) & sm) * a.live_w) + center;
                 fe.w = (int)(((uint32_t)(s - E) & sm) * a.live_w) + center;
             }
-            lo = 1 << 30; hi = -(1 << 30);
-            if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
-            if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
-            if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
+            // the union of the sources' ranges, the gap sources one diagonal wider (an empty one is neutral)
+            lo = min(fx.lo, min(fo.lo, fe.lo) - 1);
+            hi = max(fx.hi, max(fo.hi, fe.hi) + 1);
             lo = max(lo, klo); hi = min(hi, khi);
             if constexpr (!ADAPT) {
                 // threshold: a path through diagonal k at score s still has to reach the end diagonal, a gap of
@@ -573,7 +576,7 @@ __device__ __forceinline__ Forward forward_pair(const WfaArgs& a, uint8_t* regio
         }
         if (run) {
             if (gl == 0) {
-                const int4 rec = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, base, w) : make_int4(0, 0, 0, 0);
+                const int4 rec = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, base, vhi) : empty_rec();
                 reinterpret_cast<int4*>(meta)[s] = rec;
                 if (kRing && ring) ring[s & mask] = rec;
             }
@@ -670,7 +673,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
                 seqs.P = Pw; seqs.T = Tw; seqs.nwP = nwP; seqs.nwT = nwT;
             }
             if (fresh)   // the empty records before record 0
-                for (int j = gl; j < (int)a.rec_pad; j += G) rec[-1 - j] = make_int4(0, 0, 0, 0);
+                for (int j = gl; j < (int)a.rec_pad; j += G) rec[-1 - j] = empty_rec();
             // score 0: diagonal 0 only (live slot 0)
             int found0 = 0;
             if (fresh && gl == 0) {
@@ -678,7 +681,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
                 ++p_cells;
                 *reinterpret_cast<uint64_t*>(live + (size_t)center * kEntryElems) =
                     (uint64_t)(uint16_t)m0 | ((uint64_t)(uint16_t)kNeg << 16) | ((uint64_t)(uint16_t)kNeg << 32);
-                rec[0] = make_int4(0, 1, 0, 1);
+                rec[0] = make_int4(0, 1, 0, 0);
                 found0 = kend == 0 && m0 >= m;
             }
             found0 = grp.bcast(found0);
@@ -710,10 +713,9 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
             fx.w = (int)(((uint32_t)(s - X) & smask) * a.live_w) + center;
             fo.w = (int)(((uint32_t)(s - OE) & smask) * a.live_w) + center;
             fe.w = (int)(((uint32_t)(s - E) & smask) * a.live_w) + center;
-            lo = 1 << 30; hi = -(1 << 30);
-            if (fx.cnt) { lo = min(lo, fx.lo); hi = max(hi, wf_hi(fx)); }
-            if (fo.cnt) { lo = min(lo, fo.lo - 1); hi = max(hi, wf_hi(fo) + 1); }
-            if (fe.cnt) { lo = min(lo, fe.lo - 1); hi = max(hi, wf_hi(fe) + 1); }
+            // the union of the sources' ranges, the gap sources one diagonal wider (an empty one is neutral)
+            lo = min(fx.lo, min(fo.lo, fe.lo) - 1);
+            hi = max(fx.hi, max(fo.hi, fe.hi) + 1);
             lo = max(lo, klo); hi = min(hi, khi);
             lo = max(lo, kend - reach); hi = min(hi, kend + reach);   // the threshold clamp
             w = lo <= hi ? hi - lo + 1 : 0;
@@ -771,7 +773,7 @@ __device__ __forceinline__ void bound_pass_run(const WfaArgs& a, int b, uint8_t*
             if (prune) { vlo = plo; vhi = phi; }
         }
         if (run) {
-            if (gl == 0) rec[s] = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, 0, w) : make_int4(0, 0, 0, 0);
+            if (gl == 0) rec[s] = vlo <= vhi ? make_int4(vlo, vhi - vlo + 1, 0, vhi) : empty_rec();
             if (group_hit) status = kDone;
         }
         // a pair that ended in this step: its bound (the score at which it reached the end), or none
