@@ -73,7 +73,9 @@ enum {
     AIM_ERR_INPUT = -2,       /* bad input data detected synchronously */
     AIM_ERR_NOMEM = -3,       /* workspace too small even for one pair in flight */
     AIM_ERR_CUDA = -4,        /* a CUDA call failed; aim_last_cuda_error() has the code */
-    AIM_ERR_UNSUPPORTED = -5  /* valid but not supported (e.g. a band wider than 127 for the DP) */
+    AIM_ERR_UNSUPPORTED = -5, /* valid but not supported (e.g. a band wider than 127 for the DP) */
+    AIM_ERR_CANCELLED = -6,   /* serving: the request was cancelled before it was admitted */
+    AIM_ERR_BUSY = -7         /* serving: the request is already admitted (it completes as usual) */
 };
 
 /* per-pair flags (out_flags) */
@@ -419,9 +421,19 @@ AIM_API int aim_server_submit(aim_server *server, const aim_request *request, ui
 AIM_API int aim_server_poll(aim_server *server, uint64_t ticket, int *done, uint64_t *latency_ns);
 /* Blocks until the request completes (then as aim_server_poll with done = 1). */
 AIM_API int aim_server_wait(aim_server *server, uint64_t ticket, uint64_t *latency_ns);
-/* out[6]: submitted, completed, pairs completed, failed, queued now, running now. */
+/* out[6]: submitted, completed, pairs completed, failed (cancelled ones included), queued now, running now. */
 AIM_API int aim_server_stats(aim_server *server, uint64_t *out);
-/* Finishes every queued and running request, then frees the server. */
+/* paused = 1: admit no further request (queued ones wait; running ones complete); 0: admit again. */
+AIM_API int aim_server_pause(aim_server *server, int paused);
+/* Cancels a request that is still queued: it leaves the queue at once and its ticket completes with
+ * AIM_ERR_CANCELLED (poll/wait return that status; its output buffers are not touched).  AIM_ERR_BUSY: it was
+ * already admitted and completes as usual.  AIM_ERR_ARG: unknown or already released ticket. */
+AIM_API int aim_server_cancel(aim_server *server, uint64_t ticket);
+/* Host-side fault injection, for tests of the failure path: the countdown-th request admitted from now on
+ * (1: the next one) fails at launch as if a CUDA call had failed.  None of its work is enqueued, its arenas are
+ * released, its ticket completes with AIM_ERR_CUDA, and the server carries on with the others.  0 disarms. */
+AIM_API int aim_server_inject_failure(aim_server *server, uint32_t countdown);
+/* Finishes every queued and running request (resuming a paused server), then frees the server. */
 AIM_API int aim_server_destroy(aim_server *server);
 
 /*

@@ -16,6 +16,7 @@ import torch
 from .build import LIB
 
 AIM_OK, AIM_ERR_ARG, AIM_ERR_INPUT, AIM_ERR_NOMEM, AIM_ERR_CUDA, AIM_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
+AIM_ERR_CANCELLED, AIM_ERR_BUSY = -6, -7
 AIM_F_REJECTED, AIM_F_CIGAR_OVERFLOW, AIM_F_BAD_PAIR, AIM_F_STEP_CAP = 1, 2, 4, 8
 AIM_ALGO_EDIT_NW, AIM_ALGO_GOTOH_BANDED, AIM_ALGO_WFA_AFFINE, AIM_ALGO_WFA_ADAPTIVE, AIM_ALGO_GENASM = 0, 1, 2, 3, 4
 ALGO = {"edit": AIM_ALGO_EDIT_NW, "gotoh": AIM_ALGO_GOTOH_BANDED, "wfa": AIM_ALGO_WFA_AFFINE,
@@ -88,6 +89,9 @@ def _lib():
         lib.aim_server_wait.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64)]
         lib.aim_server_stats.argtypes = [p, p]
         lib.aim_server_destroy.argtypes = [p]
+        lib.aim_server_pause.argtypes = [p, ctypes.c_int]
+        lib.aim_server_cancel.argtypes = [p, ctypes.c_uint64]
+        lib.aim_server_inject_failure.argtypes = [p, u32]
         lib.aim_batch_info.argtypes = [p, p, p]
         lib.aim_batch_destroy.argtypes = [p]
         lib.aim_stats_reset.argtypes = [p, p]
@@ -281,6 +285,25 @@ def aim_server_stats(server) -> dict:
     o = np.zeros(6, np.uint64)
     _check(_lib().aim_server_stats(server, ctypes.c_void_p(o.ctypes.data)), "aim_server_stats")
     return dict(zip(["submitted", "completed", "pairs_completed", "failed", "queued", "running"], map(int, o)))
+
+
+def aim_server_pause(server, paused: bool = True) -> None:
+    _check(_lib().aim_server_pause(server, 1 if paused else 0), "aim_server_pause")
+
+
+def aim_server_cancel(server, ticket: int) -> bool:
+    """True: the queued request was cancelled (its ticket completes with AIM_ERR_CANCELLED); False: it was already
+    admitted and completes as usual."""
+    rc = _lib().aim_server_cancel(server, ticket)
+    if rc == AIM_ERR_BUSY:
+        return False
+    _check(rc, "aim_server_cancel")
+    return True
+
+
+def aim_server_inject_failure(server, countdown: int = 1) -> None:
+    """Host-side fault injection: the countdown-th request admitted from now fails at launch (0 disarms)."""
+    _check(_lib().aim_server_inject_failure(server, int(countdown)), "aim_server_inject_failure")
 
 
 def aim_server_destroy(server) -> None:

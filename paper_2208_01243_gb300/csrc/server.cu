@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace aim {
 namespace {
@@ -195,6 +196,8 @@ struct aim_server {
     std::unordered_map<uint64_t, std::unique_ptr<aim::Request>> tickets;
     uint64_t next_ticket;
     bool stop;
+    bool paused;                // admit nothing while set
+    uint32_t inject_countdown;  // > 0: the request admitted when it reaches 0 fails at launch (tests)
     std::thread worker;
     uint64_t n_submitted, n_completed, pairs_completed, n_failed;
 };
@@ -264,6 +267,7 @@ void release(aim_server* s, Request* r) {
 
 // Enqueue the request's work on its stream (no lock needed: its arena ranges are its own).
 int launch_request(aim_server* s, Request* r) {
+    aim::Range range("aim_server_launch");
     const IoLayout L = layout_of(*r);
     uint8_t* h = s->host_stage + r->host_off;
     uint8_t* d = s->dev_io + r->io_off;
@@ -345,6 +349,7 @@ int launch_request(aim_server* s, Request* r) {
 }
 
 void finish(aim_server* s, Request* r) {
+    aim::Range range("aim_server_finish");
     const IoLayout L = layout_of(*r);
     const uint8_t* h = s->host_stage + r->host_off;
     std::memcpy(r->out_scores, h + L.scores, r->n * 4);
@@ -382,7 +387,7 @@ void worker_loop(aim_server* s) {
             s->cv_done.notify_all();
         }
         // admissions, in arrival order
-        while (!s->queue.empty()) {
+        while (!s->paused && !s->queue.empty()) {
             Request* r = s->queue.front();
             if (s->free_streams.size() < r->jobs.size() + 1) break;   // a request holds its own streams
             if (!try_admit(s, r)) break;
@@ -402,8 +407,9 @@ void worker_loop(aim_server* s) {
                 r->events.push_back(ev);
             }
             s->running.push_back(r);
+            const bool injected = s->inject_countdown > 0 && --s->inject_countdown == 0;
             lock.unlock();
-            const int rc = launch_request(s, r);
+            const int rc = injected ? AIM_ERR_CUDA : launch_request(s, r);
             lock.lock();
             if (rc != AIM_OK) {   // the request fails as a whole; its ticket completes with an error status
                 lock.unlock();
@@ -445,7 +451,7 @@ int aim_server_create(aim_ctx* ctx, const aim_penalties_t* pen, size_t wavefront
     s->costs = Costs{pen->mismatch, pen->gap_open, pen->gap_extend};
     s->num_sms = ctx->num_sms;
     s->warps_cap = ctx->num_sms * 32;
-    s->next_stream = 0; s->next_ticket = 1; s->stop = false;
+    s->next_stream = 0; s->next_ticket = 1; s->stop = false; s->paused = false; s->inject_countdown = 0;
     s->n_submitted = s->n_completed = s->pairs_completed = s->n_failed = 0;
     if (!wavefront_budget_bytes) wavefront_budget_bytes = (size_t)4 << 30;
     if (!io_budget_bytes) io_budget_bytes = (size_t)1 << 30;
@@ -475,6 +481,7 @@ int aim_server_create(aim_ctx* ctx, const aim_penalties_t* pen, size_t wavefront
 }
 
 int aim_server_submit(aim_server* s, const aim_request* q, uint64_t* ticket) {
+    aim::Range range("aim_server_submit");
     using namespace aim;
     if (!s || !q || !ticket) return AIM_ERR_ARG;
     *ticket = 0;
@@ -629,11 +636,48 @@ int aim_server_stats(aim_server* s, uint64_t* out) {
     return AIM_OK;
 }
 
+int aim_server_pause(aim_server* s, int paused) {
+    if (!s || (paused != 0 && paused != 1)) return AIM_ERR_ARG;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->paused = paused != 0;
+    }
+    s->cv_work.notify_one();
+    return AIM_OK;
+}
+
+int aim_server_cancel(aim_server* s, uint64_t ticket) {
+    if (!s) return AIM_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    auto it = s->tickets.find(ticket);
+    if (it == s->tickets.end()) return AIM_ERR_ARG;
+    aim::Request* r = it->second.get();
+    auto q = std::find(s->queue.begin(), s->queue.end(), r);
+    if (q == s->queue.end()) return AIM_ERR_BUSY;   // admitted (running or done): it completes as usual
+    s->queue.erase(q);
+    r->status = AIM_ERR_CANCELLED;
+    r->t_done = aim::Clock::now();
+    r->done = true;
+    ++s->n_completed;
+    ++s->n_failed;
+    s->cv_done.notify_all();
+    s->cv_work.notify_one();   // the requests behind it may fit now
+    return AIM_OK;
+}
+
+int aim_server_inject_failure(aim_server* s, uint32_t countdown) {
+    if (!s) return AIM_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->inject_countdown = countdown;
+    return AIM_OK;
+}
+
 int aim_server_destroy(aim_server* s) {
     if (!s) return AIM_OK;
     {
         std::lock_guard<std::mutex> lock(s->mu);
         s->stop = true;
+        s->paused = false;   // everything queued is finished
     }
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();

@@ -92,3 +92,79 @@ def test_request_larger_than_the_budget_is_refused(gen_lib):
     assert ei.value.status == aim.AIM_ERR_NOMEM
     aim.aim_server_destroy(srv)
     aim.aim_destroy(ctx)
+
+
+def _same_as_plain(o):
+    plain = device_results(o["pairs"], "wfa", AFF, int(o["me"].max()), per_pair=o["me"])
+    assert np.array_equal(plain[0], o["scores"]) and np.array_equal(plain[1], o["flags"])
+    assert all(np.array_equal(a, b) for a, b in zip(plain[2], _runs(o)))
+
+
+def test_pause_cancel_and_an_injected_launch_failure(gen_lib):
+    """Host-side failure paths: a paused server admits nothing; a queued request is cancelled and its outputs stay
+    untouched; a request made to fail at launch (injected on the host, no GPU fault) completes with AIM_ERR_CUDA
+    while the requests around it, and a later one, give the plain entry point's results."""
+    import time
+    import paper_2208_01243_gb300 as aim
+    pool, reqs = _requests(n_req=6, seed=12)
+    ctx = aim.aim_create(0, 64 << 20)
+    srv = aim.aim_server_create(ctx, aim.penalties(4, 6, 2), 96 << 20, 256 << 20)
+    aim.aim_server_pause(srv, True)
+    subs = [_submit(aim, srv, pool, idx, me) for idx, me in reqs[:4]]
+    time.sleep(0.05)
+    st = aim.aim_server_stats(srv)
+    assert (st["queued"], st["running"], st["completed"]) == (4, 0, 0)
+    t1, o1 = subs[1]
+    assert aim.aim_server_cancel(srv, t1)
+    with pytest.raises(aim.AimError) as ei:
+        aim.aim_server_wait(srv, t1)
+    assert ei.value.status == aim.AIM_ERR_CANCELLED
+    assert (o1["scores"] == -7).all() and (o1["flags"] == 255).all() and not o1["lens"].any()
+    with pytest.raises(aim.AimError) as ei:   # the ticket is released
+        aim.aim_server_cancel(srv, t1)
+    assert ei.value.status == aim.AIM_ERR_ARG
+    # admission order from here: requests 0, 2, 3; the second of them fails at launch
+    aim.aim_server_inject_failure(srv, 2)
+    aim.aim_server_pause(srv, False)
+    aim.aim_server_wait(srv, subs[0][0])
+    with pytest.raises(aim.AimError) as ei:
+        aim.aim_server_wait(srv, subs[2][0])
+    assert ei.value.status == aim.AIM_ERR_CUDA
+    aim.aim_server_wait(srv, subs[3][0])
+    _same_as_plain(subs[0][1])
+    _same_as_plain(subs[3][1])
+    # the server carries on; an admitted request cannot be cancelled
+    t4, o4 = _submit(aim, srv, pool, *reqs[4])
+    for _ in range(2000):
+        if aim.aim_server_stats(srv)["completed"] == 5:
+            break
+        time.sleep(0.005)
+    assert not aim.aim_server_cancel(srv, t4)
+    aim.aim_server_wait(srv, t4)
+    _same_as_plain(o4)
+    st = aim.aim_server_stats(srv)
+    assert (st["submitted"], st["completed"], st["failed"], st["queued"], st["running"]) == (5, 5, 2, 0, 0)
+    aim.aim_server_destroy(srv)
+    aim.aim_destroy(ctx)
+
+
+def test_device_allocation_failures_leave_the_device_usable(gen_lib):
+    """Budgets twice the device's memory: the allocation fails, the call returns AIM_ERR_NOMEM, and work runs
+    afterwards."""
+    import torch
+    import paper_2208_01243_gb300 as aim
+    too_much = 2 * torch.cuda.mem_get_info(0)[1]
+    with pytest.raises(aim.AimError) as ei:
+        aim.aim_create(0, too_much)
+    assert ei.value.status == aim.AIM_ERR_NOMEM
+    ctx = aim.aim_create(0, 64 << 20)
+    with pytest.raises(aim.AimError) as ei:
+        aim.aim_server_create(ctx, aim.penalties(4, 6, 2), too_much, 64 << 20)
+    assert ei.value.status == aim.AIM_ERR_NOMEM
+    pool, reqs = _requests(n_req=1, seed=13)
+    srv = aim.aim_server_create(ctx, aim.penalties(4, 6, 2), 96 << 20, 256 << 20)
+    t, o = _submit(aim, srv, pool, *reqs[0])
+    aim.aim_server_wait(srv, t)
+    aim.aim_server_destroy(srv)
+    aim.aim_destroy(ctx)
+    _same_as_plain(o)
