@@ -6,6 +6,7 @@
 #include <new>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace aim {
 struct KernelTimes {
@@ -240,6 +241,8 @@ const char* aim_status_string(int status) {
         case AIM_ERR_NOMEM: return "workspace too small";
         case AIM_ERR_CUDA: return "CUDA error";
         case AIM_ERR_UNSUPPORTED: return "unsupported";
+        case AIM_ERR_CANCELLED: return "cancelled";
+        case AIM_ERR_BUSY: return "already admitted";
         default: return "unknown status";
     }
 }
@@ -405,6 +408,7 @@ int aim_timing_read(aim_ctx* ctx, int kind, double* total_ms, int* launches) {
 int aim_pack_2bit(aim_ctx* ctx, const uint8_t* ascii, const uint64_t* char_offsets, const uint32_t* lengths,
                   uint32_t count, uint64_t* packed, const uint64_t* word_offsets, uint8_t* bad,
                   aim_stream_t stream) {
+    aim::Range range("aim_pack_2bit");
     if (!ctx) return AIM_ERR_ARG;
     if (count == 0) return AIM_OK;
     if (!ascii || !char_offsets || !lengths || !packed || !word_offsets) return AIM_ERR_ARG;
@@ -422,6 +426,7 @@ int aim_align_batch(aim_ctx* ctx, const uint64_t* packed_reads, const uint64_t* 
                     const aim_penalties_t* pen, int32_t max_edits, const int32_t* max_edits_per_pair,
                     int32_t* out_scores, uint32_t* out_cigars, const uint64_t* cigar_offsets,
                     uint32_t* out_cigar_lens, uint8_t* out_flags, aim_stream_t stream) {
+    aim::Range range("aim_align_batch");
     if (!common_args_ok(ctx, read_lengths, target_lengths, num_pairs, algo, pen, out_scores, out_cigars,
                         cigar_offsets, out_flags))
         return AIM_ERR_ARG;
@@ -442,6 +447,7 @@ int aim_align_batch_ascii(aim_ctx* ctx, const uint8_t* reads, const uint8_t* tar
                           const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
                           const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags,
                           aim_stream_t stream) {
+    aim::Range range("aim_align_batch_ascii");
     if (!common_args_ok(ctx, read_lengths, target_lengths, num_pairs, algo, pen, out_scores, out_cigars,
                         cigar_offsets, out_flags))
         return AIM_ERR_ARG;

@@ -56,6 +56,7 @@
 #include <vector>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace aim {
 namespace {
@@ -637,6 +638,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
                    const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
                    const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags, size_t scratch_bytes,
                    int autotune, aim_batch** out) {
+    aim::Range range("aim_batch_plan");
     return aim::batch_plan_impl(ctx, reads, targets, read_char_offsets, target_char_offsets, read_lengths,
                                 target_lengths, num_pairs, max_length, pen, max_edits, max_edits_per_pair, out_scores,
                                 out_cigars, cigar_offsets, out_cigar_lens, out_flags, scratch_bytes, autotune, nullptr,
@@ -644,6 +646,7 @@ int aim_batch_plan(aim_ctx* ctx, const uint8_t* reads, const uint8_t* targets, c
 }
 
 int aim_batch_run(aim_batch* b, aim_stream_t stream) {
+    aim::Range range("aim_batch_run");
     using namespace aim;
     if (!b) return AIM_ERR_ARG;
     DeviceGuardImpl guard(b->ctx->device);

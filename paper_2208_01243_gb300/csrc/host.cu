@@ -32,6 +32,7 @@
 #include <vector>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace aim {
 namespace {
@@ -179,6 +180,7 @@ extern "C" int aim_align_batch_host(aim_ctx* ctx, const uint8_t* reads, const ui
                                     const int32_t* max_edits_per_pair, int32_t* out_scores, uint32_t* out_cigars,
                                     const uint64_t* cigar_offsets, uint32_t* out_cigar_lens, uint8_t* out_flags,
                                     uint32_t chunk_pairs, uint64_t* bytes_moved) {
+    aim::Range range("aim_align_batch_host");
     using namespace aim;
     if (bytes_moved) bytes_moved[0] = bytes_moved[1] = 0;
     if (!ctx || !pen || algo < AIM_ALGO_EDIT_NW || algo > AIM_ALGO_GENASM) return AIM_ERR_ARG;

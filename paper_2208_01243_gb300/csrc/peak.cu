@@ -15,6 +15,7 @@
 #include <cstdint>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace aim {
 namespace {
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(256) int_peak_kernel(int iters, int c1, int c2
 }  // namespace aim
 
 extern "C" int aim_measure_int_peak(int device, double* ops_per_s, double* kernel_ms, double* per_mix) {
+    aim::Range range("aim_measure_int_peak");
     using namespace aim;
     if (!ops_per_s) return AIM_ERR_ARG;
     DeviceGuardImpl guard(device);

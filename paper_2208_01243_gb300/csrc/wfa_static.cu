@@ -26,6 +26,7 @@
 #include <mutex>
 
 #include "aim_internal.cuh"
+#include "ranges.h"
 
 namespace {
 
@@ -80,6 +81,7 @@ extern "C" int aim_wfa_align_static(const uint64_t* packed_reads, const uint64_t
                                     int32_t max_edits, const int32_t* max_edits_per_pair, int32_t* out_scores,
                                     uint32_t* out_cigars, const uint64_t* cigar_offsets, uint32_t* out_cigar_lens,
                                     uint8_t* out_flags, aim_stream_t stream) {
+    aim::Range range("aim_wfa_align_static");
     if (!pen || pen->match != 0 || pen->mismatch < 1 || pen->gap_open < 0 || pen->gap_extend < 1 ||
         pen->mismatch > (1 << 20) || pen->gap_open > (1 << 20) || pen->gap_extend > (1 << 20))
         return AIM_ERR_ARG;
