@@ -3,8 +3,9 @@
 // Fixed slots (every sequence at word i * stride, the form the ASCII entry points use): one thread per output
 // word.  It reads the word's 32 bytes as aligned 4-byte loads (each load holds at least one byte of the word, so
 // none crosses into another page), lines them up with funnel shifts, and converts four bytes at a time:
-// ((c >> 1) ^ (c >> 2)) & 3 maps A, C, G, T (0x41, 0x43, 0x47, 0x54) to 0, 1, 2, 3; a 4-byte compare against the
-// four letters flags anything else; one multiply gathers the four 2-bit codes into a byte, first base on top.
+// ((c >> 1) ^ (c >> 2)) & 3 maps A, C, G, T (0x41, 0x43, 0x47, 0x54) to 0, 1, 2, 3; a byte whose code's letter
+// (looked up for four bytes by one byte permute) is not the byte itself flags the pair; one multiply gathers the
+// four 2-bit codes into a byte, first base on top.  The slot of a thread comes from a multiply, not a division.
 //
 // Explicit word offsets (aim_pack_2bit): one warp per sequence; each lane converts one byte per 32-base word
 // and the warp ORs the lanes' 2-bit codes together (two 32-bit halves).  Lane w%32 keeps word w and the warp
@@ -65,14 +66,32 @@ __global__ void __launch_bounds__(256) pack_kernel(const uint8_t* __restrict__ a
 }
 
 // four ASCII bytes (first in the low byte) -> their 2-bit codes, first base in bits 7..6; *bad: a byte in `keep`
-// (0xff per byte to look at) that is not A, C, G or T
+// (0xff per byte to look at) that is not A, C, G or T.  Every byte c gets the code ((c >> 1) ^ (c >> 2)) & 3,
+// and c is one of the four letters exactly when it equals the letter of its code, "ACGT"[code]: one byte
+// permute looks the four letters up, with the codes as its selector nibbles.
 __device__ __forceinline__ uint32_t pack4(uint32_t x, uint32_t keep, bool& bad) {
-    const uint32_t ok = __vcmpeq4(x, 0x41414141u) | __vcmpeq4(x, 0x43434343u) | __vcmpeq4(x, 0x47474747u) |
-                        __vcmpeq4(x, 0x54545454u);
-    bad |= (~ok & keep) != 0;
-    const uint32_t codes = ((x >> 1) ^ (x >> 2)) & 0x03030303u & keep;
+    const uint32_t codes = ((x >> 1) ^ (x >> 2)) & 0x03030303u;   // byte k: code of byte k
+    const uint32_t pairs = codes | (codes >> 4);                   // byte 0: c0 | c1 << 4; byte 2: c2 | c3 << 4
+    const uint32_t sel = __byte_perm(pairs, 0u, 0x4420u);          // nibble k: c_k
+    const uint32_t letters = __byte_perm(0x54474341u, 0u, sel);    // byte k: "ACGT"[c_k]
+    bad |= ((letters ^ x) & keep) != 0;
     // byte k holds code k; times 2^30 + 2^20 + 2^10 + 1 puts code k at bits 30-2k..31-2k with no carries
-    return (codes * 0x40100401u) >> 24;
+    return ((codes & keep) * 0x40100401u) >> 24;
+}
+
+// g / d for any 32-bit g, by a multiply: with s = ceil(log2 d) and M = ceil(2^(32+s) / d) = 2^32 + m (d <= 2^s
+// puts M in [2^32, 2^33)), g * M / 2^(32+s) = g / d + g (M d - 2^(32+s)) / (d 2^(32+s)), and the second term
+// is below 1 / d since M d - 2^(32+s) < d <= 2^s and g < 2^32: its floor is g / d rounded down.
+struct Divider {
+    uint32_t m, s;
+    __device__ uint32_t div(uint32_t g) const { return (uint32_t)(((uint64_t)__umulhi(g, m) + g) >> s); }
+};
+
+Divider make_divider(uint32_t d) {
+    uint32_t s = 0;
+    while (((uint64_t)1 << s) < d) ++s;
+    const uint64_t M = (((uint64_t)1 << (32 + s)) + d - 1) / d;
+    return Divider{(uint32_t)(M - ((uint64_t)1 << 32)), s};
 }
 
 template <bool WIDE>
@@ -80,11 +99,11 @@ __global__ void __launch_bounds__(256) pack_words_kernel(const uint8_t* __restri
                                                          const uint64_t* __restrict__ char_off,
                                                          const uint32_t* __restrict__ len, uint32_t count,
                                                          uint64_t* __restrict__ packed, uint32_t stride,
-                                                         uint8_t* __restrict__ bad) {
+                                                         Divider by_stride, uint8_t* __restrict__ bad) {
     using Index = typename std::conditional<WIDE, uint64_t, uint32_t>::type;
     const Index total = (Index)count * stride;
     for (Index g = (Index)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += (Index)gridDim.x * blockDim.x) {
-        const uint32_t i = (uint32_t)(g / stride);
+        const uint32_t i = WIDE ? (uint32_t)(g / stride) : by_stride.div((uint32_t)g);
         const uint32_t w = (uint32_t)(g - (Index)i * stride);
         const uint32_t L = __ldg(len + i);
         const uint32_t nw = (L + 31) >> 5;
@@ -137,12 +156,13 @@ cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const ui
         uint64_t blocks = (total + 255) / 256;
         const uint64_t cap = (uint64_t)sms * 32;   // grid-stride beyond 32 blocks of 256 per SM
         if (blocks > cap) blocks = cap;
+        const Divider by_stride = make_divider((uint32_t)word_stride);
         if (total <= 0xffffffffull)
             pack_words_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(ascii, char_off, len, count, packed,
-                                                                        (uint32_t)word_stride, bad);
+                                                                        (uint32_t)word_stride, by_stride, bad);
         else
             pack_words_kernel<true><<<(unsigned)blocks, 256, 0, st>>>(ascii, char_off, len, count, packed,
-                                                                       (uint32_t)word_stride, bad);
+                                                                       (uint32_t)word_stride, by_stride, bad);
         return cudaGetLastError();
     }
     const uint32_t warps_needed = count;

@@ -270,6 +270,33 @@ def test_ascii_path_odd_buffer_addresses_and_bad_bytes(aligner, oracle_lib, shif
         assert list(cg[off[i]:off[i] + ln[i]]) == runs, i
 
 
+def test_packer_flags_every_non_acgt_byte(aligner, oracle_lib):
+    """Every byte value other than A, C, G and T (lowercase letters, N, NUL, 0xff ...) flags its pair, at any
+    position of a word and of a 4-byte group; the pairs without one align as the oracle does."""
+    rng = np.random.default_rng(77)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    reads, targets, bad = [], [], []
+    for v in range(256):
+        if v in acgt:
+            continue
+        for planted in (True, False):
+            L = int(rng.integers(1, 80))
+            r = bytearray(rng.choice(acgt, L).tobytes())
+            t = bytearray(r)
+            t[int(rng.integers(L))] = int(rng.choice(acgt))
+            if planted:
+                (r if v % 2 else t)[int(rng.integers(L))] = v
+            reads.append(bytes(r)); targets.append(bytes(t)); bad.append(planted)
+    p = gen.from_strings(reads, targets)
+    s, f, runs, _ = device_results(p, "edit", oracle.UNIT, 80, aligner=aligner)
+    for i in range(len(p)):
+        if bad[i]:
+            assert (s[i], f[i]) == (-1, oracle.F_BAD_PAIR), i
+        else:
+            sc, fl, rr = oracle.align(p.read(i), p.target(i), oracle.UNIT)
+            assert (s[i], f[i], list(runs[i])) == (sc, fl, list(rr)), i
+
+
 def test_results_independent_of_batch_composition(aligner, gen_lib):
     """Each pair's result is the same alone, in a shuffled batch and with a small workspace."""
     p = gen.generate(gen.WFA_UNEVEN, 600)
