@@ -1217,10 +1217,12 @@ void (*compact_kernel_for(int G, int fmt))(WfaArgs) {
 }
 
 // Groups of up to 16 lanes (many pairs per SM) stage their pairs' sequences in shared memory when a block's
-// copies fit in kStageBytes; groups of 32 lanes and whole blocks (one long pair per warp or block) gained
-// nothing from it and read global memory.
+// copies fit in kStageBytes (kBoundStageBytes for bound passes, which keep no history: 4-lane bound passes over
+// reads of up to 1,000 bp then stage their 34 KB, 139.0 -> 138.4 ms on the default step); groups of 32 lanes
+// and whole blocks (one long pair per warp or block) gained nothing from it and read global memory.
 constexpr int kStageMaxGroup = 16;
 constexpr size_t kStageBytes = 24 << 10;
+constexpr size_t kBoundStageBytes = 48 << 10;
 
 int gcd_i(int a, int b) {
     while (b) { const int t = a % b; a = b; b = t; }
@@ -1374,7 +1376,7 @@ cudaError_t launch_wfa_buckets(const WfaPlan& plan, const PairsView& P, const Li
         // sequence copies in shared memory when the group size takes them and a block's fit in kStageBytes
         const size_t slot_words = ((size_t)P.max_length + 31) / 32 + 1;
         size_t smem = (size_t)8 * (32 / std::min(G, 32)) * 2 * slot_words * sizeof(uint64_t);
-        if (G > kStageMaxGroup || smem > kStageBytes) smem = 0;
+        if (G > kStageMaxGroup || smem > (bound_pass ? kBoundStageBytes : kStageBytes)) smem = 0;
         a.seq_slot_words = smem ? (uint32_t)slot_words : 0u;
         if (bound_pass && (G < 4 || G > 32)) return cudaErrorInvalidValue;
         const int fmt = bound_pass ? kFmtBound : wfa_format(plan, G);
