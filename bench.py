@@ -702,10 +702,17 @@ def serving(args, local):
     closed = pairs / wall
     mean_req = float(sizes.mean())
 
+    def warm(rate_pairs, seed):
+        # 1.5 s of the same offered load, not measured, before each probe and level: some runs showed a transient
+        # of about a second at their start (the queue grew, then drained), whatever the load
+        arr, sz = offered(rate_pairs, 1.5, seed)
+        run(arr, sz)
+
     # open-loop peak: the highest offered rate at which the queue stays bounded
     trials = []
     peak = None
     for j, frac in enumerate((0.95, 0.9, 0.85, 0.8, 0.75, 0.7, 0.6, 0.5)):
+        warm(frac * closed, 900 + j)
         arr, sz = offered(frac * closed, args.serve_probe_seconds, 700 + j)
         lat, pairs, wall, queue = run(arr, sz)
         q = len(lat) // 4
@@ -728,6 +735,7 @@ def serving(args, local):
         peak = trials[-1]["offered_pairs_per_s"]
     levels = {}
     for frac in (0.5, 0.8, 0.95):
+        warm(frac * peak, 800 + int(frac * 100))
         arr, sz = offered(frac * peak, args.serve_seconds, 600 + int(frac * 100))
         lat, pairs, wall, queue = run(arr, sz)
         # queue length over time: requests queued or running, sampled at submissions, as (s, count) every ~0.25 s
@@ -750,7 +758,8 @@ def serving(args, local):
             "peak_rule": "highest open-loop Poisson rate (falling fractions of the closed-loop throughput, "
                          f"{args.serve_probe_seconds:g} s each) whose median latency and mean queue length in the last "
                          "quarter of the run stay within 2x those of the first quarter (+ 20 ms, + 4 requests) and "
-                         "whose sustained throughput is >= 95 % of the offered rate",
+                         "whose sustained throughput is >= 95 % of the offered rate; each probe and load level follows "
+                         "1.5 s of the same offered load that is not measured",
             "closed_loop_alignments_per_s": closed, "peak_search": trials, "mean_pairs_per_request": mean_req,
             "loads": levels, "failed": st["failed"],
             "latency": "server clock from submission to results in host memory (includes queueing, copies)"}
