@@ -87,7 +87,7 @@ struct Divider {
     __device__ uint32_t div(uint32_t g) const { return (uint32_t)(((uint64_t)__umulhi(g, m) + g) >> s); }
 };
 
-Divider make_divider(uint32_t d) {
+Divider make_divider(uint32_t d) {   // 1 <= d <= 2^31
     uint32_t s = 0;
     while (((uint64_t)1 << s) < d) ++s;
     const uint64_t M = (((uint64_t)1 << (32 + s)) + d - 1) / d;
@@ -156,8 +156,10 @@ cudaError_t launch_pack(const uint8_t* ascii, const uint64_t* char_off, const ui
         uint64_t blocks = (total + 255) / 256;
         const uint64_t cap = (uint64_t)sms * 32;   // grid-stride beyond 32 blocks of 256 per SM
         if (blocks > cap) blocks = cap;
-        const Divider by_stride = make_divider((uint32_t)word_stride);
-        if (total <= 0xffffffffull)
+        // the reciprocal needs 2^(32+s) in 64 bits (a stride up to 2^31); anything wider divides
+        const bool narrow = total <= 0xffffffffull && word_stride <= ((uint64_t)1 << 31);
+        const Divider by_stride = narrow ? make_divider((uint32_t)word_stride) : Divider{0u, 0u};
+        if (narrow)
             pack_words_kernel<false><<<(unsigned)blocks, 256, 0, st>>>(ascii, char_off, len, count, packed,
                                                                         (uint32_t)word_stride, by_stride, bad);
         else
