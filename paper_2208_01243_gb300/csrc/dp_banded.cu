@@ -25,6 +25,11 @@
 // remaining prefix must have.  Unit cost has one state, so three bits
 // (diagonal, up, left) say which neighbours reach H(v,h).
 //
+// Base comparisons: a lane's cells on one diagonal read consecutive bases of
+// both sequences, so every 64 anti-diagonals the warp builds, per diagonal, a
+// 32-bit mask of the next 32 cells' mismatches from two 32-base windows
+// (XOR, fold each 2-bit field, gather the bits); a cell then tests one bit.
+//
 // Early exit (threshold): costs never decrease along a path and every path
 // touches one of any two consecutive anti-diagonals, so once every cell of
 // two consecutive anti-diagonals exceeds the limit the pair is rejected.
@@ -59,6 +64,29 @@ struct DpArgs {
 
 __device__ __forceinline__ int32_t cap_inf(int32_t v) { return v > kInf ? kInf : v; }
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
+
+// Mismatch bits of 32 consecutive cells of one diagonal: bit j is set when read base iv + j differs from target
+// base ih + j.  The XOR of the two 32-base windows has a nonzero 2-bit field where the bases differ; those fields
+// fold onto their low bits, the even bits are gathered into 32 (bit 31 - j for base j) and reversed.  Bases past
+// a sequence's end read as 0; the sweep never asks for them.
+// 32 bases from base `pos` of a sequence, first base in the top bits; positions before 0 or past the end read 0
+__device__ __forceinline__ uint64_t window_from(const uint64_t* w, uint32_t nwords, int pos) {
+    if (pos >= 0) return window32(w, nwords, (uint32_t)pos);
+    if (pos <= -32) return 0ull;
+    return window32(w, nwords, 0u) >> (2 * -pos);
+}
+
+__device__ __forceinline__ uint32_t mismatch_mask(const uint64_t* Pw, uint32_t nwP, int iv, const uint64_t* Tw,
+                                                  uint32_t nwT, int ih) {
+    const uint64_t x = window_from(Pw, nwP, iv) ^ window_from(Tw, nwT, ih);
+    uint64_t f = (x | (x >> 1)) & 0x5555555555555555ull;
+    f = (f | (f >> 1)) & 0x3333333333333333ull;
+    f = (f | (f >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+    f = (f | (f >> 4)) & 0x00FF00FF00FF00FFull;
+    f = (f | (f >> 8)) & 0x0000FFFF0000FFFFull;
+    f = (f | (f >> 16)) & 0x00000000FFFFFFFFull;
+    return __brev((uint32_t)f);
+}
 
 // finished pairs awaiting their traceback, one record per slot of a warp: pair, score, tight end states
 __shared__ int4 s_dp_pend[256];
@@ -194,11 +222,13 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
         const uint64_t* Tw = live ? target_words(a.P, pi) : nullptr;
 
         // per slot (parity p, block r): the latest cell of that diagonal, the anti-diagonal range where the
-        // diagonal holds cells of this pair, and the packed words its cells read (advanced, not reloaded)
+        // diagonal holds cells of this pair, and the mismatch bits of the diagonal's next cells (mm: up to 32
+        // cells from read base mi0, refreshed for the whole warp every 64 anti-diagonals)
         int32_t Ms[2][R], Is[2][R], Ds[2][R];
         int dlo[2][R], dhi[2][R];
-        uint64_t pw[2][R], tw[2][R];
-        int pwi[2][R], twi[2][R];
+        uint32_t mm[2][R];
+        int mi0[2][R];
+        const uint32_t nwP = (n + 31) >> 5, nwT = (m + 31) >> 5;
 #pragma unroll
         for (int pp = 0; pp < 2; ++pp)
 #pragma unroll
@@ -208,8 +238,8 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
                 // cell (v,h) of diagonal k lies on anti-diagonal d = 2v + k: v >= 0, h >= 0, v <= n, h <= m
                 dlo[pp][r] = live && q <= 2 * b ? (k < 0 ? -k : k) : (1 << 30);
                 dhi[pp][r] = min(2 * (int)n + k, 2 * (int)m - k);
-                pwi[pp][r] = twi[pp][r] = -1;
-                pw[pp][r] = tw[pp][r] = 0;
+                mi0[pp][r] = -(1 << 30);
+                mm[pp][r] = 0;
             }
         {   // seed: cell (0,0) on diagonal k = 0, q = b
             const int i0 = b >> 1, p0s = b & 1;
@@ -277,12 +307,8 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
                     const int v = (d - k) >> 1, h = (d + k) >> 1;
                     uint32_t bits = 0;
                     if (v >= 1 && h >= 1) {
-                        const int iv = v - 1, ih = h - 1;
-                        if ((iv >> 5) != pwi[P][r]) { pwi[P][r] = iv >> 5; pw[P][r] = __ldg(Pw + (iv >> 5)); }
-                        if ((ih >> 5) != twi[P][r]) { twi[P][r] = ih >> 5; tw[P][r] = __ldg(Tw + (ih >> 5)); }
-                        const uint32_t pb = (uint32_t)(pw[P][r] >> (62 - 2 * (iv & 31))) & 3u;
-                        const uint32_t tb = (uint32_t)(tw[P][r] >> (62 - 2 * (ih & 31))) & 3u;
-                        const int32_t delta = pb == tb ? 0 : x;
+                        // this cell's bit of the diagonal's mask (refreshed for the whole warp every 64 steps)
+                        const int32_t delta = (mm[P][r] >> (v - 1 - mi0[P][r])) & 1u ? x : 0;
                         if (UNIT) {
                             Mv = cap_inf(dM + delta);
                         } else {
@@ -331,16 +357,34 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
             if constexpr (SUB == 1) return __all_sync(kFull, over);
             else return (__ballot_sync(kFull, over) & seg) == seg;
         };
+        // the mismatch masks of every slot for the anti-diagonals dr .. dr + 63: slot (p, r) holds the cells on
+        // anti-diagonals of its diagonal's parity, at most 32 of them in 64 steps, from read base mi0 on.  The
+        // whole warp refreshes at the same steps, so no lane waits on another's loads.
+        int covered = 0;   // last anti-diagonal the masks cover
+        auto refresh = [&](const int dr) {
+#pragma unroll
+            for (int pp = 0; pp < 2; ++pp)
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int k = 2 * (GS * r + sl) + pp - b;
+                    const int d1 = dr + ((dr - k) & 1);   // first anti-diagonal >= dr holding a cell of k
+                    mi0[pp][r] = ((d1 - k) >> 1) - 1;
+                    mm[pp][r] = live ? mismatch_mask(Pw, nwP, mi0[pp][r], Tw, nwT, mi0[pp][r] + k) : 0u;
+                }
+            covered = dr + 63;
+        };
         using P0 = std::integral_constant<int, 0>;
         using P1 = std::integral_constant<int, 1>;
         if constexpr (SUB == 1) {
             bool rejected = false;
             int d = 1;
+            if (d <= dend) refresh(d);
             if (d <= dend && ((d + b) & 1)) {   // start on parity 1 so the loop below alternates 0, 1
                 prev_over = step(d, P1{});
                 ++d;
             }
             for (; d <= dend; d += 2) {
+                if (d + 1 > covered) refresh(d);
                 bool o = step(d, P0{});
                 if (o && prev_over) { rejected = true; break; }
                 prev_over = o;
@@ -370,11 +414,13 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
                 prev_over = o;
             };
             int d = 1;
+            if (d <= dmax) refresh(d);
             if (d <= dmax && ((d + b) & 1)) {
                 rejects(step(d, P1{}), d);
                 ++d;
             }
             for (; d <= dmax; d += 2) {
+                if (d + 1 > covered) refresh(d);
                 rejects(step(d, P0{}), d);
                 if (!__any_sync(kFull, live)) break;
                 if (d + 1 > dmax) break;
