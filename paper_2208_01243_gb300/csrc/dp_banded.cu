@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
     const int32_t x = UNIT ? 1 : a.c.x;
     const int32_t oe = UNIT ? 1 : a.c.o + a.c.e;
     const int32_t e = UNIT ? 1 : a.c.e;
-    unsigned long long st_cells = 0, st_pairs = 0;
+    // this lane's cells and pairs over the launch, in 32 bits (a lane sweeps one cell per block and step: 2^32
+    // of them would take minutes)
+    uint32_t st_cells = 0, st_pairs = 0;
 
     for (;;) {
         uint32_t p0 = 0;
@@ -467,8 +469,8 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
         }
     }
     dp_finish<UNIT, RW>(a, warp_slots, pend, npend, lane);
-    warp_stat_add(a.O.stats, 2, st_cells, lane);
-    warp_stat_add(a.O.stats, 3, st_pairs, lane);
+    warp_stat_add(a.O.stats, 2, (unsigned long long)st_cells, lane);
+    warp_stat_add(a.O.stats, 3, (unsigned long long)st_pairs, lane);
 }
 
 template <bool UNIT, int R, int SUB>
