@@ -65,10 +65,6 @@ struct DpArgs {
 __device__ __forceinline__ int32_t cap_inf(int32_t v) { return v > kInf ? kInf : v; }
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
 
-// Mismatch bits of 32 consecutive cells of one diagonal: bit j is set when read base iv + j differs from target
-// base ih + j.  The XOR of the two 32-base windows has a nonzero 2-bit field where the bases differ; those fields
-// fold onto their low bits, the even bits are gathered into 32 (bit 31 - j for base j) and reversed.  Bases past
-// a sequence's end read as 0; the sweep never asks for them.
 // 32 bases from base `pos` of a sequence, first base in the top bits; positions before 0 or past the end read 0
 __device__ __forceinline__ uint64_t window_from(const uint64_t* w, uint32_t nwords, int pos) {
     if (pos >= 0) return window32(w, nwords, (uint32_t)pos);
@@ -76,6 +72,10 @@ __device__ __forceinline__ uint64_t window_from(const uint64_t* w, uint32_t nwor
     return window32(w, nwords, 0u) >> (2 * -pos);
 }
 
+// Mismatch bits of 32 consecutive cells of one diagonal: bit j is set when read base iv + j differs from target
+// base ih + j.  The XOR of the two 32-base windows has a nonzero 2-bit field where the bases differ; those fields
+// fold onto their low bits, the even bits are gathered into 32 (bit 31 - j for base j) and reversed.  Bases past
+// a sequence's end read as 0; the sweep never asks for them.
 __device__ __forceinline__ uint32_t mismatch_mask(const uint64_t* Pw, uint32_t nwP, int iv, const uint64_t* Tw,
                                                   uint32_t nwT, int ih) {
     const uint64_t x = window_from(Pw, nwP, iv) ^ window_from(Tw, nwT, ih);
