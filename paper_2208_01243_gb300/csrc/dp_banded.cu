@@ -63,6 +63,13 @@ struct DpArgs {
 };
 
 __device__ __forceinline__ int32_t cap_inf(int32_t v) { return v > kInf ? kInf : v; }
+
+// A new value is at most its predecessor's plus the largest cost, so after d anti-diagonals every value is at
+// most kInf + d * (largest cost).  When that stays within int32 for the whole sweep (the host checks), values
+// need no cap: an unreachable cell then holds some value above kInf instead of kInf itself, which every test
+// reads the same way (above any limit; its trace bits are never read).
+template <bool CAP>
+__device__ __forceinline__ int32_t capped(int32_t v) { return CAP ? cap_inf(v) : v; }
 __device__ __forceinline__ int32_t min3(int32_t a, int32_t b, int32_t c) { return min(min(a, b), c); }
 
 // 32 bases from base `pos` of a sequence, first base in the top bits; positions before 0 or past the end read 0
@@ -161,7 +168,7 @@ __device__ __forceinline__ void dp_finish(const DpArgs& a, uint8_t* warp_slots, 
 }
 
 // 4 blocks of 256 per SM (64 registers) with one lane block, 2 with two
-template <bool UNIT, int R, int SUB>
+template <bool UNIT, int R, int SUB, bool CAP>
 __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(DpArgs a) {
     static_assert(SUB == 1 || R == 1, "several pairs per warp only for one lane block");
     using TB = typename std::conditional<UNIT, uint8_t, uint16_t>::type;
@@ -312,31 +319,31 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
                         // this cell's bit of the diagonal's mask (refreshed for the whole warp every 64 steps)
                         const int32_t delta = (mm[P][r] >> (v - 1 - mi0[P][r])) & 1u ? x : 0;
                         if (UNIT) {
-                            Mv = cap_inf(dM + delta);
+                            Mv = capped<CAP>(dM + delta);
                         } else {
                             // the mismatch cost is common to the three predecessors: compare them with their
                             // minimum.  (Bits of an unreachable cell are never read: the traceback walks reachable
                             // cells only, so no test of the value against infinity is needed.)
                             const int32_t mn = min3(dM, dI, dD);
-                            Mv = cap_inf(mn + delta);
+                            Mv = capped<CAP>(mn + delta);
                             bits |= (dM == mn ? 1u : 0u) | (dI == mn ? 2u : 0u) | (dD == mn ? 4u : 0u);
                         }
                     }
                     if (v >= 1) {
                         if (UNIT) {
-                            Iv = cap_inf(uM + 1);
+                            Iv = capped<CAP>(uM + 1);
                         } else {
                             const int32_t a0 = uM + oe, a1 = uD + oe, a2 = uI + e, mn = min3(a0, a1, a2);
-                            Iv = cap_inf(mn);
+                            Iv = capped<CAP>(mn);
                             bits |= (a0 == mn ? 8u : 0u) | (a1 == mn ? 16u : 0u) | (a2 == mn ? 32u : 0u);
                         }
                     }
                     if (h >= 1) {
                         if (UNIT) {
-                            Dv = cap_inf(lM + 1);
+                            Dv = capped<CAP>(lM + 1);
                         } else {
                             const int32_t a0 = lM + oe, a1 = lI + oe, a2 = lD + e, mn = min3(a0, a1, a2);
-                            Dv = cap_inf(mn);
+                            Dv = capped<CAP>(mn);
                             bits |= (a0 == mn ? 64u : 0u) | (a1 == mn ? 128u : 0u) | (a2 == mn ? 256u : 0u);
                         }
                     }
@@ -473,10 +480,10 @@ __global__ void __launch_bounds__(256, R == 1 ? 4 : R == 2 ? 2 : 1) dp_kernel(Dp
     warp_stat_add(a.O.stats, 3, (unsigned long long)st_pairs, lane);
 }
 
-template <bool UNIT, int R, int SUB>
+template <bool UNIT, int R, int SUB, bool CAP>
 cudaError_t launch_t(const DpArgs& args0, int num_sms, cudaStream_t st, int* warps_used, size_t scratch_bytes) {
     int bps = 0;
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dp_kernel<UNIT, R, SUB>, 256, 0);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, dp_kernel<UNIT, R, SUB, CAP>, 256, 0);
     if (err != cudaSuccess) return err;
     if (bps < 1) bps = 1;
     size_t warps = (size_t)num_sms * bps * 8;
@@ -491,9 +498,26 @@ cudaError_t launch_t(const DpArgs& args0, int num_sms, cudaStream_t st, int* war
     const size_t per_warp = scratch_bytes / warps / args0.slot_bytes;
     a.defer = (uint32_t)((per_warp > 32 ? 32 : per_warp) / SUB * SUB);
     const unsigned blocks = (unsigned)((warps + 7) / 8);
-    dp_kernel<UNIT, R, SUB><<<blocks, 256, 0, st>>>(a);
+    dp_kernel<UNIT, R, SUB, CAP><<<blocks, 256, 0, st>>>(a);
     *warps_used = (int)warps;
     return cudaGetLastError();
+}
+
+template <bool CAP>
+cudaError_t launch_dp_t(const DpPlan& plan, const DpArgs& a, int num_sms, cudaStream_t st, int* warps_used,
+                        size_t scratch_bytes) {
+    if (plan.unit) {
+        if (plan.pairs_per_warp == 4) return launch_t<true, 1, 4, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.pairs_per_warp == 2) return launch_t<true, 1, 2, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.blocks == 1) return launch_t<true, 1, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+        if (plan.blocks == 2) return launch_t<true, 2, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+        return launch_t<true, 4, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+    }
+    if (plan.pairs_per_warp == 4) return launch_t<false, 1, 4, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.pairs_per_warp == 2) return launch_t<false, 1, 2, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.blocks == 1) return launch_t<false, 1, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+    if (plan.blocks == 2) return launch_t<false, 2, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
+    return launch_t<false, 4, 1, CAP>(a, num_sms, st, warps_used, scratch_bytes);
 }
 
 }  // namespace
@@ -531,18 +555,11 @@ cudaError_t launch_dp(const DpPlan& plan, const Costs& c, const PairsView& P, co
     a.runs_cap = (uint32_t)cap;
     a.trace_bytes = plan.slot_bytes;
     a.slot_bytes = align_up(plan.slot_bytes + (size_t)cap * 4, 128);
-    if (plan.unit) {
-        if (plan.pairs_per_warp == 4) return launch_t<true, 1, 4>(a, num_sms, st, warps_used, scratch_bytes);
-        if (plan.pairs_per_warp == 2) return launch_t<true, 1, 2>(a, num_sms, st, warps_used, scratch_bytes);
-        if (plan.blocks == 1) return launch_t<true, 1, 1>(a, num_sms, st, warps_used, scratch_bytes);
-        if (plan.blocks == 2) return launch_t<true, 2, 1>(a, num_sms, st, warps_used, scratch_bytes);
-        return launch_t<true, 4, 1>(a, num_sms, st, warps_used, scratch_bytes);
-    }
-    if (plan.pairs_per_warp == 4) return launch_t<false, 1, 4>(a, num_sms, st, warps_used, scratch_bytes);
-    if (plan.pairs_per_warp == 2) return launch_t<false, 1, 2>(a, num_sms, st, warps_used, scratch_bytes);
-    if (plan.blocks == 1) return launch_t<false, 1, 1>(a, num_sms, st, warps_used, scratch_bytes);
-    if (plan.blocks == 2) return launch_t<false, 2, 1>(a, num_sms, st, warps_used, scratch_bytes);
-    return launch_t<false, 4, 1>(a, num_sms, st, warps_used, scratch_bytes);
+    // values need no cap when kInf + (anti-diagonals + 1) * (largest cost) fits int32
+    const int64_t maxc = plan.unit ? 1 : std::max<int64_t>(std::max<int64_t>(c.x, (int64_t)c.o + c.e), c.e);
+    const bool need_cap = (2 * (int64_t)P.max_length + 2) * maxc >= (int64_t)INT32_MAX - kInf - maxc;
+    return need_cap ? launch_dp_t<true>(plan, a, num_sms, st, warps_used, scratch_bytes)
+                    : launch_dp_t<false>(plan, a, num_sms, st, warps_used, scratch_bytes);
 }
 
 }  // namespace aim

@@ -297,6 +297,29 @@ def test_packer_flags_every_non_acgt_byte(aligner, oracle_lib):
             assert (s[i], f[i], list(runs[i])) == (sc, fl, list(rr)), i
 
 
+def test_dp_huge_costs_keep_the_value_cap(aligner, oracle_lib):
+    """Costs of 2^20 over reads of up to 1,000 bp could take DP values past int32 without the cap at infinity, so
+    the host picks the capped kernel instance there; results match the oracle."""
+    rng = np.random.default_rng(91)
+    acgt = np.frombuffer(b"ACGT", np.uint8)
+    big = 1 << 20
+    pen = (0, big, big, big)
+    reads, targets = [], []
+    for _ in range(64):
+        L = int(rng.integers(900, 1001))
+        r = rng.choice(acgt, L)
+        t = r.copy()
+        for _ in range(int(rng.integers(0, 4))):   # up to three substitutions
+            j = int(rng.integers(L))
+            t[j] = acgt[(int(np.flatnonzero(acgt == t[j])[0]) + 1) % 4]
+        reads.append(r.tobytes()); targets.append(t.tobytes())
+    p = gen.from_strings(reads, targets)
+    s, f, runs, _ = device_results(p, "gotoh", pen, 3, aligner=aligner)
+    for i in range(len(p)):
+        sc, fl, rr = oracle.align(p.read(i), p.target(i), pen, limit=oracle.limit_for(pen, 3))
+        assert (s[i], f[i], list(runs[i])) == (sc, fl, list(rr)), i
+
+
 def test_results_independent_of_batch_composition(aligner, gen_lib):
     """Each pair's result is the same alone, in a shuffled batch and with a small workspace."""
     p = gen.generate(gen.WFA_UNEVEN, 600)
